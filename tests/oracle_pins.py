@@ -1,0 +1,311 @@
+"""Pins for the FP64 oracle: checks against what the mathematics fixes, not
+against the oracle itself. Each pin takes an `oracle.Oracle` and raises
+AssertionError when the oracle disagrees. They are run on the real oracle
+(test_oracle_pins.py) and on copies with planted mistakes
+(test_oracle_mutants.py), where at least one pin must fail.
+
+What pins what:
+  fir_delta          FIR tap order and indexing, DFT sign and channel order
+                     (a unit impulse reproduces the taps, closed form)
+  tone               FIR + DFT: a channel-centred tone lands in its channel
+                     with amplitude A*sum(h); leakage = DFT of the folded taps
+  dft_vs_numpy       naive DFT + reordering vs numpy.fft + fftshift
+  point_source       delay correction: closed-form phase -2 pi f_k (tau_i - tau_j)
+                     before, zero after; amplitude S A_p A_q (sum h)^2
+  bandpass           bandpass weights undo a per-station ripple exactly
+  delay_ramp         linear delay interpolation over the block: a tone whose
+                     delay drifts linearly is left with a phase constant in time
+  correlate_einsum   correlation vs numpy.einsum of Y Y^H
+  hermitian          autos: XX, YY real and >= 0, YX = conj(XY)
+  linearity          sums over two halves of the block add up to the whole
+  gradient_fd        vjp vs central finite differences of the loss
+  gradient_truth     zero loss and zero gradient at the true parameters
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import synth
+
+FS = synth.SAMPLE_RATE_HZ
+
+
+def cplx(a):
+    return a[..., 0] + 1j * a[..., 1]
+
+
+def bidx(i, j):
+    return j * (j + 1) // 2 + i
+
+
+def _random_taps(rng, T, C):
+    return rng.uniform(-1.0, 1.0, size=T * C)
+
+
+def pin_fir_delta(o):
+    """A unit impulse at sample s0*C + c0 gives u_s[c0] = A h[(s0 - s) C + c0]
+    for 0 <= s0 - s < T and nothing else; its DFT is u * exp(-2 pi i c0 m / C)."""
+    rng = np.random.default_rng(1)
+    C, T, S = 8, 4, 10
+    L = (S + T - 1) * C
+    taps = _random_taps(rng, T, C)
+    A = 1000
+    for s0, c0, p0, comp in [(3, 0, 0, 0), (7, 5, 1, 0), (12, 3, 0, 1), (0, 7, 1, 1)]:
+        raw = np.zeros((1, 1, L, 2, 2), np.int16)
+        raw[0, 0, s0 * C + c0, p0, comp] = A
+        chan = cplx(o.channelize(synth.CI16, raw, T, C, S, taps))[0, 0]   # [P][S][C]
+        amp = A * (1j if comp else 1.0)
+        exp = np.zeros((S, C), complex)
+        for s in range(S):
+            k = s0 - s
+            if 0 <= k < T:
+                u = amp * taps[k * C + c0]
+                for kout in range(C):
+                    m = (kout - C // 2) % C
+                    exp[s, kout] = u * np.exp(-2j * np.pi * c0 * m / C)
+        assert np.allclose(chan[p0], exp, rtol=0, atol=1e-9), "delta response"
+        assert np.all(chan[1 - p0] == 0), "other polarisation untouched"
+
+
+def pin_tone(o):
+    """Tone exp(i(2 pi m t / C + th)): X_s[k] = A e^{i th} sum_c H_c e^{-2 pi i c (k'-m)/C}
+    with H_c = sum_k h[kC + c] and k' = k - C/2; exactly A e^{i th} sum(h) in
+    channel m + C/2. Quantisation error bound: sum|h| * 0.5 * sqrt(2)."""
+    rng = np.random.default_rng(2)
+    C, T, S = 16, 4, 6
+    L = (S + T - 1) * C
+    taps = synth.kaiser_sinc_taps(T, C) * (1 + 0.1 * rng.uniform(-1, 1, T * C))
+    H = taps.reshape(T, C).sum(0)
+    A, th = 8000.0, 0.7
+    bound = 0.5 * np.sqrt(2) * np.abs(taps).sum() + 1e-9
+    for m in (-3, 0, 5, -8):
+        t = np.arange(L)
+        z = A * np.exp(1j * (2 * np.pi * ((m * t) % C) / C + th))
+        raw = np.zeros((1, 1, L, 2, 2), np.int16)
+        raw[0, 0, :, 0] = synth.quantise(z, synth.CI16)
+        chan = cplx(o.channelize(synth.CI16, raw, T, C, S, taps))[0, 0, 0]    # [S][C]
+        FH = np.fft.fft(H)
+        exp = np.empty(C, complex)
+        for k in range(C):
+            mp = (k - C // 2) % C
+            exp[k] = A * np.exp(1j * th) * FH[(mp - m) % C]
+        assert np.max(np.abs(chan - exp[None, :])) <= bound, "tone response"
+        assert abs(chan[0, m + C // 2] - A * np.exp(1j * th) * taps.sum()) <= bound
+
+
+def pin_dft_vs_numpy(o):
+    """Naive DFT + reordering equals numpy.fft.fft + fftshift of the FIR output."""
+    rng = np.random.default_rng(3)
+    for C, T, S, fmt in [(16, 16, 5, synth.CI16), (64, 4, 3, synth.CI8), (4, 2, 7, synth.CI16)]:
+        L = (S + T - 1) * C
+        lim = synth.FORMAT_MAX[fmt]
+        raw = rng.integers(-lim, lim + 1, size=(1, 2, L, 2, 2)).astype(synth.FORMAT_DTYPE[fmt])
+        taps = _random_taps(rng, T, C)
+        chan = cplx(o.channelize(fmt, raw, T, C, S, taps))          # [1][N][P][S][C]
+        x = cplx(raw.astype(np.float64))[0]                          # [N][L][P]
+        h = taps.reshape(T, C)
+        for n in range(2):
+            for p in range(2):
+                xr = x[n, :, p].reshape(S + T - 1, C)
+                u = sum(h[k][None, :] * xr[k:k + S] for k in range(T))
+                X = np.fft.fftshift(np.fft.fft(u, axis=-1), axes=-1)
+                assert np.allclose(chan[0, n, p], X, rtol=1e-12, atol=1e-9), "DFT vs numpy"
+
+
+def _point_source_setup(seed, N=4, C=16, T=4, S=12, SB=2, A=4000.0, ripple=None):
+    rng = np.random.default_rng(seed)
+    tau = rng.uniform(-5e-6, 5e-6, N)
+    k0 = 11
+    tone = synth.Tone(amp=A, channel=k0, delays=tau, ripple=ripple)
+    blk = synth.make_block(seed, synth.CI16, SB, N, C, S, n_taps=T, sigma=0.0, tones=[tone])
+    return blk, tau, k0
+
+
+def pin_point_source(o):
+    """Before correction V_ij^pq(k0) = S A_p A_q (sum h)^2 e^{i(p-q)pi/3}
+    e^{-2 pi i f_k0 (tau_i - tau_j)}; after correction the delay phase is gone."""
+    blk, tau, k0 = _point_source_setup(4)
+    A, N, S, C = 4000.0, blk.n_stations, blk.n_spectra, blk.n_channels
+    chan = o.channelize(blk.fmt, blk.raw, blk.n_taps, C, S, blk.taps)
+    zero = np.zeros(N)
+    v0 = cplx(o.correlate(o.correct(chan, FS, blk.centres, zero, zero)))
+    v1 = cplx(o.correlate(o.correct(chan, FS, blk.centres, tau, tau)))
+    sh = blk.taps.sum()
+    for sb in range(blk.n_subbands):
+        f = blk.centres[sb] + (k0 - C // 2) * FS / C
+        for j in range(N):
+            for i in range(j + 1):
+                for p in range(2):
+                    for q in range(2):
+                        amp = S * A * A * (1 - .25 * p) * (1 - .25 * q) * sh * sh
+                        pol = np.exp(1j * (p - q) * np.pi / 3)
+                        e0 = amp * pol * np.exp(-2j * np.pi * f * (tau[i] - tau[j]))
+                        e1 = amp * pol
+                        got0 = v0[sb, k0, bidx(i, j), 2 * p + q]
+                        got1 = v1[sb, k0, bidx(i, j), 2 * p + q]
+                        assert abs(got0 - e0) <= 2e-3 * abs(e0), "uncorrected phase"
+                        assert abs(got1 - e1) <= 2e-3 * abs(e1), "corrected phase"
+
+
+def pin_bandpass(o):
+    """A tone scaled by ripple r[n][k] comes back to amplitude A_p sum(h) per
+    station once corrected with bandpass weights 1/r."""
+    rng = np.random.default_rng(5)
+    N, C = 4, 16
+    ripple = synth.bandpass_ripple(rng, N, C, depth=0.2)
+    blk, tau, k0 = _point_source_setup(5, N=N, C=C, ripple=ripple)
+    A = 4000.0
+    chan = o.channelize(blk.fmt, blk.raw, blk.n_taps, C, blk.n_spectra, blk.taps)
+    corr = cplx(o.correct(chan, FS, blk.centres, tau, tau, bandpass=1.0 / ripple))
+    sh = blk.taps.sum()
+    for p in range(2):
+        exp = A * (1 - .25 * p) * sh * np.exp(1j * p * np.pi / 3)
+        got = corr[:, k0, :, :, p]
+        assert np.max(np.abs(got - exp)) <= 1e-3 * abs(exp), "bandpass restores amplitude"
+    # gains multiply in: a gain of 2i on (station 1, pol 0) scales that sample by 2i
+    g = np.zeros((N, 2, 2)); g[..., 0] = 1.0; g[1, 0] = (0.0, 2.0)
+    corr_g = cplx(o.correct(chan, FS, blk.centres, tau, tau, bandpass=1.0 / ripple, gains=g))
+    assert np.allclose(corr_g[:, :, :, 1, 0], 2j * corr[:, :, :, 1, 0], rtol=1e-12, atol=1e-9)
+    assert np.allclose(corr_g[:, :, :, 0, :], corr[:, :, :, 0, :], rtol=1e-12, atol=1e-9)
+
+
+def pin_delay_ramp(o):
+    """A tone whose delay drifts linearly, tau(t) = tb + (te - tb) t / (S C), is
+    corrected with tau_begin = tb, tau_end = te. The residual phase must be the
+    same for every spectrum (only the fixed offset of the FIR window centre is
+    left), which fixes the interpolation tau(s) = tb + (te - tb) s / S."""
+    C, T, S, N = 16, 4, 16, 2
+    L = (S + T - 1) * C
+    k0 = 9
+    m = k0 - C // 2
+    centres = np.array([150e6])
+    f = centres[0] + m * FS / C
+    tb = np.array([1.3e-6, -2.2e-6])
+    te = tb + np.array([3.0e-9, -1.7e-8])          # several turns of phase over the block
+    A = 12000.0
+    t = np.arange(L)
+    raw = np.zeros((1, N, L, 2, 2), np.int16)
+    for n in range(N):
+        tau_t = tb[n] + (te[n] - tb[n]) * t / (S * C)
+        z = A * np.exp(1j * 2 * np.pi * ((m * t) % C) / C) * np.exp(-2j * np.pi * f * tau_t)
+        for p in range(2):
+            raw[0, n, :, p] = synth.quantise(z, synth.CI16)
+    taps = synth.kaiser_sinc_taps(T, C)
+    chan = o.channelize(synth.CI16, raw, T, C, S, taps)
+    corr = cplx(o.correct(chan, FS, centres, tb, te))
+    for n in range(N):
+        ph = np.unwrap(np.angle(corr[0, k0, :, n, 0]))
+        assert np.ptp(ph) < 2e-2, f"residual phase drifts over the block ({np.ptp(ph)})"
+
+
+def pin_correlate_einsum(o):
+    """Correlation equals numpy.einsum Y Y^H on the station-pair triangle."""
+    rng = np.random.default_rng(6)
+    SB, C, S, N = 2, 3, 9, 5
+    corr = rng.standard_normal((SB, C, S, N, 2, 2))
+    vis = cplx(o.correlate(corr))
+    Y = cplx(corr).reshape(SB, C, S, N * 2)
+    full = np.einsum("aksi,aksj->akij", Y, np.conj(Y))
+    for j in range(N):
+        for i in range(j + 1):
+            for p in range(2):
+                for q in range(2):
+                    assert np.allclose(vis[:, :, bidx(i, j), 2 * p + q],
+                                       full[:, :, 2 * i + p, 2 * j + q], rtol=1e-12, atol=1e-12)
+
+
+def pin_hermitian(o):
+    """Autocorrelations: XX and YY real and non-negative, YX = conj(XY)."""
+    rng = np.random.default_rng(7)
+    SB, C, S, N = 1, 4, 7, 6
+    corr = rng.standard_normal((SB, C, S, N, 2, 2))
+    vis = cplx(o.correlate(corr))
+    for i in range(N):
+        v = vis[:, :, bidx(i, i)]
+        assert np.all(np.abs(v[..., 0].imag) < 1e-12) and np.all(v[..., 0].real >= 0)
+        assert np.all(np.abs(v[..., 3].imag) < 1e-12) and np.all(v[..., 3].real >= 0)
+        assert np.allclose(v[..., 2], np.conj(v[..., 1]), rtol=1e-12, atol=1e-12)
+
+
+def pin_linearity(o):
+    """Integration is a sum over time: two halves add up to the whole block."""
+    rng = np.random.default_rng(8)
+    corr = rng.standard_normal((1, 3, 10, 4, 2, 2))
+    v = o.correlate(corr)
+    va = o.correlate(np.ascontiguousarray(corr[:, :, :4]))
+    vb = o.correlate(np.ascontiguousarray(corr[:, :, 4:]))
+    assert np.allclose(v, va + vb, rtol=1e-12, atol=1e-12)
+
+
+def _grad_problem(seed, SB=2, N=3, C=4, S=8):
+    rng = np.random.default_rng(seed)
+    chan = synth.channelised_noise(seed, SB, N, 2, C, S)
+    centres = synth.subband_centres(SB)
+    gains = synth.random_gains(rng, N)
+    tau = rng.uniform(-50e-9, 50e-9, N)
+    bandpass = rng.uniform(0.8, 1.2, (N, C))
+    B = N * (N + 1) // 2
+    w = rng.uniform(0.5, 1.5, (SB, C, B, 4))
+    M = rng.standard_normal((SB, C, B, 4)) + 1j * rng.standard_normal((SB, C, B, 4))
+    return chan, centres, gains, tau, bandpass, w, M
+
+
+def _loss(o, chan, centres, gains, tau, bandpass, w, M):
+    V = cplx(o.correlate(o.correct(chan, FS, centres, tau, tau, bandpass=bandpass, gains=gains)))
+    return float(np.sum(w * np.abs(V - M) ** 2)), V
+
+
+def pin_gradient_fd(o):
+    """vjp against central finite differences of L = sum w |V - M|^2
+    (step 1e-3 on gain components, 1e-3 ns on delays)."""
+    chan, centres, gains, tau, bandpass, w, M = _grad_problem(9)
+    L0, V = _loss(o, chan, centres, gains, tau, bandpass, w, M)
+    G = 2 * w * (V - M)
+    gg, gt = o.vjp(chan, FS, centres, tau, np.stack([G.real, G.imag], -1),
+                   bandpass=bandpass, gains=gains)
+    h = 1e-3
+    fd_g = np.zeros_like(gains)
+    for idx in np.ndindex(gains.shape):
+        gp, gm = gains.copy(), gains.copy()
+        gp[idx] += h
+        gm[idx] -= h
+        fd_g[idx] = (_loss(o, chan, centres, gp, tau, bandpass, w, M)[0]
+                     - _loss(o, chan, centres, gm, tau, bandpass, w, M)[0]) / (2 * h)
+    ht = 1e-12
+    fd_t = np.zeros_like(tau)
+    for n in range(len(tau)):
+        tp, tm = tau.copy(), tau.copy()
+        tp[n] += ht
+        tm[n] -= ht
+        fd_t[n] = (_loss(o, chan, centres, gains, tp, bandpass, w, M)[0]
+                   - _loss(o, chan, centres, gains, tm, bandpass, w, M)[0]) / (2 * ht)
+    assert np.linalg.norm(gg - fd_g) <= 1e-5 * np.linalg.norm(fd_g), "gain gradient vs FD"
+    assert np.linalg.norm(gt - fd_t) <= 1e-4 * np.linalg.norm(fd_t), "delay gradient vs FD"
+
+
+def pin_gradient_truth(o):
+    """With M = V(true) the loss is zero and so is its gradient."""
+    chan, centres, gains, tau, bandpass, w, _ = _grad_problem(10)
+    _, V = _loss(o, chan, centres, gains, tau, bandpass, w, 0.0)
+    gg, gt = o.vjp(chan, FS, centres, tau, np.zeros(V.shape + (2,)), bandpass=bandpass,
+                   gains=gains)
+    assert np.all(gg == 0) and np.all(gt == 0)
+    L, _ = _loss(o, chan, centres, gains, tau, bandpass, w, V)
+    assert L == 0.0
+    # non-trivial check of the same point: moving the gains makes L > 0
+    L2, _ = _loss(o, chan, centres, gains * 1.01, tau, bandpass, w, V)
+    assert L2 > 0
+
+
+def pin_fx_chain(o):
+    """The whole-chain entry equals its three steps run one after another."""
+    blk, tau, _ = _point_source_setup(11, N=3, C=8, S=5, SB=1)
+    chan = o.channelize(blk.fmt, blk.raw, blk.n_taps, 8, 5, blk.taps)
+    v = o.correlate(o.correct(chan, FS, blk.centres, tau, tau * 1.5))
+    v2 = o.fx(blk.fmt, blk.raw, blk.n_taps, 8, 5, blk.taps, FS, blk.centres, tau, tau * 1.5)
+    assert np.array_equal(v, v2)
+
+
+ALL_PINS = [pin_fir_delta, pin_tone, pin_dft_vs_numpy, pin_point_source, pin_bandpass,
+            pin_delay_ramp, pin_correlate_einsum, pin_hermitian, pin_linearity,
+            pin_gradient_fd, pin_gradient_truth, pin_fx_chain]
