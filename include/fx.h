@@ -1,0 +1,155 @@
+/*
+ * fx.h -- C ABI of the GB300 FX correlator library (libfx_gb300.so).
+ *
+ * The hot path of the Cobalt correlator pipeline (arXiv 1801.04834,
+ * Sec. "Signal processing with GPU kernels"), per subband:
+ *   fx_channelize  polyphase filter bank: T-tap FIR per channel + C-point FFT
+ *   fx_correct     fine delay compensation + bandpass correction (+ gains),
+ *                  transposing to the per-channel, all-stations layout
+ *   fx_correlate   X-stage: all station pairs x 4 polarisation products,
+ *                  integrated over the block
+ *
+ * Conventions for every call:
+ *   - Pointers prefixed d_ are device pointers (cudaMalloc'd or torch tensors),
+ *     h_ are host pointers. The caller owns every buffer it passes in; the
+ *     library owns only what fx_create allocates (taps, twiddles, subband
+ *     frequencies, the phase-table and status workspaces).
+ *   - Complex values are interleaved (re, im) pairs of the stated real type.
+ *   - Calls are asynchronous and stream-ordered on `stream` (NULL = legacy
+ *     default stream). They never synchronise the device, so they can be
+ *     captured in a CUDA graph. An error from earlier asynchronous work is
+ *     reported by a later call that checks for it.
+ *   - Return values are fx_status codes; nothing throws across the ABI.
+ *     fx_last_error() returns a message for the last failure on this thread.
+ *   - A handle is not thread-safe: use one handle per host thread / stream.
+ *   - Nothing is allocated on the device after fx_create returns.
+ *
+ * Layouts (row-major; N stations, P = 2 polarisations, I = N*P inputs with
+ * input index i = n*P + p, SB subbands, C channels, T taps, S spectra):
+ *   raw   [SB][N][L][P]      complex int16 or int8, L = (S + T - 1) * C samples
+ *   chan  [SB][N][P][S][C]   complex float
+ *   corr  FX_F32:            [SB][C][S][I] complex float
+ *         FX_F16, FX_BF16:   [SB][C][2][I_pad][S_pad] half / bfloat16,
+ *                            plane 0 real parts, plane 1 imaginary parts
+ *         FX_F16_SPLIT:      [SB][C][4][I_pad][S_pad] half, planes hi.re,
+ *                            hi.im, lo.re, lo.im (value = hi + lo)
+ *         I_pad = I rounded up to 16, S_pad = S rounded up to 64; the padding
+ *         is written as zeros by fx_correct.
+ *   vis   [SB][C][B][4]      complex float, B = N(N+1)/2 baselines,
+ *                            b = j(j+1)/2 + i for stations i <= j, products
+ *                            (p,q) in the order XX, XY, YX, YY (index 2p+q):
+ *                            V = sum_s Y[i,p] * conj(Y[j,q]).
+ */
+#ifndef FX_GB300_H
+#define FX_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t, spelled without the CUDA headers. */
+typedef struct CUstream_st *fx_stream;
+
+typedef enum {
+    FX_OK = 0,
+    FX_ERR_INVALID = -1,     /* bad argument, NULL pointer, size mismatch */
+    FX_ERR_CUDA = -2,        /* a CUDA runtime call or kernel launch failed */
+    FX_ERR_NOMEM = -3,       /* device or host allocation failed in fx_create */
+    FX_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+    FX_ERR_UNSUPPORTED = -5  /* valid request this build does not implement */
+} fx_status;
+
+typedef enum { FX_CI16 = 0, FX_CI8 = 1 } fx_format;
+
+/* Arithmetic type of the corrected samples and of the X-stage operands. The
+ * FIR and FFT always run in FP32; the X-stage always accumulates in FP32. */
+typedef enum { FX_F32 = 0, FX_F16 = 1, FX_BF16 = 2, FX_F16_SPLIT = 3 } fx_precision;
+
+typedef struct {
+    int n_stations;              /* N >= 1 (antenna fields) */
+    int n_pols;                  /* P, must be 2 */
+    int n_subbands;              /* SB >= 1 */
+    int n_channels;              /* C in {16, 64, 256} */
+    int n_taps;                  /* T in {4, 8, 16} */
+    int n_spectra;               /* S >= 1, spectra integrated per block */
+    int format;                  /* fx_format of the raw samples */
+    int precision;               /* fx_precision of corr and of the X-stage */
+    double sample_rate_hz;       /* subband width / complex sample rate, > 0 */
+    const double *h_subband_centre_hz; /* [SB] sky frequency of each subband centre */
+    const float *h_taps;         /* [T*C] prototype filter, tap k of channel c at
+                                    k*C + c; copied at fx_create */
+    float operand_scale;         /* power of two multiplied into FP16/BF16
+                                    operands and divided out of vis; 0 means 1 */
+    unsigned flags;              /* reserved, must be 0 */
+} fx_params;
+
+typedef struct fx_handle fx_handle;
+
+/* Buffer sizes and padded dimensions implied by a handle's parameters. */
+typedef struct {
+    size_t raw_bytes;            /* input of fx_channelize */
+    size_t chan_bytes;           /* output of fx_channelize */
+    size_t corr_bytes;           /* output of fx_correct (depends on precision) */
+    size_t vis_bytes;            /* output of fx_correlate */
+    int n_inputs;                /* I = N * P */
+    int n_inputs_pad;            /* I_pad of the planar layouts */
+    int n_spectra_pad;           /* S_pad of the planar layouts */
+    int n_baselines;             /* B = N (N + 1) / 2 */
+    int corr_planes;             /* 0 for FX_F32, else 2 or 4 */
+} fx_sizes;
+
+/* Validate params, copy taps and subband frequencies to the device, build the
+ * FFT twiddle table (host FP64, stored FP32) and allocate the workspaces.
+ * Uses the current CUDA device. On failure *out is NULL. */
+fx_status fx_create(const fx_params *params, fx_handle **out);
+
+/* Free everything fx_create allocated. Synchronises the device first. NULL is
+ * a no-op. */
+void fx_destroy(fx_handle *h);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *fx_last_error(void);
+
+fx_status fx_query_sizes(const fx_handle *h, fx_sizes *out);
+
+/* Polyphase filter bank (Sec. "Signal processing with GPU kernels": FIR and
+ * FFT kernels that channelise each subband; Sec. "Processing steps": fixed
+ * to floating point conversion). d_raw: raw layout, format from params;
+ * d_chan: chan layout, complex float. For spectrum s and channel c the FIR is
+ *   u_s[c] = sum_{k<T} h[k*C + c] * x[(s + k)*C + c],
+ * then X_s[m] = sum_c u_s[c] exp(-2 pi i c m / C) (unnormalised), stored at
+ * channel (m + C/2) mod C, so channel k has sky frequency
+ * f_sb + (k - C/2) * fs / C. The first T-1 spectra' worth of samples in each
+ * block are the FIR history carried over from the previous block. */
+fx_status fx_channelize(fx_handle *h, const void *d_raw, float *d_chan, fx_stream stream);
+
+/* Fine delay compensation and bandpass correction with the transposing
+ * write-back (Sec. "Signal processing with GPU kernels"): for station n,
+ *   tau_n(s) = d_delay_begin[n] + (d_delay_end[n] - d_delay_begin[n]) * s / S
+ *   Y = X * bandpass[n][k] * gain[n][p] * exp(+2 pi i f_k tau_n(s)).
+ * The phase at the block ends is formed in FP64 per (station, channel) and
+ * reduced mod 2 pi; the per-sample interpolation, sin/cos and rotation run in
+ * FP32. d_delay_begin, d_delay_end: [N] double seconds (device).
+ * d_bandpass: [N][C] float or NULL (all ones). d_gains: [N][P] complex float
+ * or NULL (all ones). d_chan: chan layout. d_corr: corr layout of the handle's
+ * precision; FP16/BF16 values are multiplied by operand_scale before rounding. */
+fx_status fx_correct(fx_handle *h, const float *d_chan, const double *d_delay_begin,
+                     const double *d_delay_end, const float *d_bandpass,
+                     const float *d_gains, void *d_corr, fx_stream stream);
+
+/* X-stage correlation (Sec. "Signal processing with GPU kernels": the last
+ * kernel correlates all pairs of antenna fields and integrates ~1 s):
+ *   vis[sb][k][b(i,j)][2p+q] = sum_{s<S} Y[i,p] conj(Y[j,q])  for i <= j.
+ * d_corr: corr layout of the handle's precision; d_vis: vis layout. FP32
+ * operands run on the CUDA cores; FP16/BF16/split operands on the tcgen05
+ * tensor cores with FP32 accumulation (split: hi*hi' + hi*lo' + lo*hi'). */
+fx_status fx_correlate(fx_handle *h, const void *d_corr, float *d_vis, fx_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FX_GB300_H */

@@ -1,0 +1,143 @@
+"""Torch-tensor convenience layer over the C ABI (include/fx.h).
+
+`Correlator` owns one fx_handle and calls the same entry points with device
+pointers taken from torch tensors. It checks dtypes, devices, contiguity and
+byte sizes before every call (the C side trusts the sizes implied by the
+handle), allocates outputs when none are given, and launches on torch's
+current CUDA stream. It does no arithmetic of its own.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import FX_CI8, FX_CI16, FX_F16, FX_F16_SPLIT, FX_F32, check
+
+SAMPLE_RATE_HZ = 195312.5
+
+
+def _stream_ptr(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Correlator:
+    """One FX correlator configuration (stations, subbands, channels, taps,
+    spectra per block, sample format, X-stage precision)."""
+
+    def __init__(self, n_stations: int, n_subbands: int, n_channels: int, n_spectra: int,
+                 taps, centres, n_taps: int = 16, fmt: int = FX_CI16, precision: int = FX_F32,
+                 sample_rate_hz: float = SAMPLE_RATE_HZ, operand_scale: float = 0.0, device=None):
+        self.lib = _abi.load()
+        if device is not None:
+            torch.cuda.set_device(device)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.N, self.SB, self.C, self.S, self.T = n_stations, n_subbands, n_channels, n_spectra, n_taps
+        self.fmt, self.precision = fmt, precision
+        taps = np.ascontiguousarray(np.asarray(taps, dtype=np.float32).reshape(-1))
+        centres = np.ascontiguousarray(np.asarray(centres, dtype=np.float64).reshape(-1))
+        if taps.size != n_taps * n_channels:
+            raise ValueError("taps must have n_taps * n_channels entries")
+        if centres.size != n_subbands:
+            raise ValueError("centres must have n_subbands entries")
+        self._taps, self._centres = taps, centres
+        p = _abi.fx_params()
+        p.n_stations, p.n_pols, p.n_subbands = n_stations, 2, n_subbands
+        p.n_channels, p.n_taps, p.n_spectra = n_channels, n_taps, n_spectra
+        p.format, p.precision = fmt, precision
+        p.sample_rate_hz = sample_rate_hz
+        p.h_subband_centre_hz = centres.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        p.h_taps = taps.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        p.operand_scale = operand_scale
+        p.flags = 0
+        h = ctypes.c_void_p()
+        check(self.lib.fx_create(ctypes.byref(p), ctypes.byref(h)), "fx_create")
+        self.handle = h
+        sz = _abi.fx_sizes()
+        check(self.lib.fx_query_sizes(h, ctypes.byref(sz)), "fx_query_sizes")
+        self.sizes = sz
+        self.I, self.I_pad, self.S_pad, self.B = sz.n_inputs, sz.n_inputs_pad, sz.n_spectra_pad, sz.n_baselines
+        self.planes = sz.corr_planes
+
+    # -- shapes -----------------------------------------------------------
+    def raw_shape(self):
+        return (self.SB, self.N, (self.S + self.T - 1) * self.C, 2, 2)
+
+    def chan_shape(self):
+        return (self.SB, self.N, 2, self.S, self.C, 2)
+
+    def corr_shape(self):
+        if self.precision == FX_F32:
+            return (self.SB, self.C, self.S, self.N, 2, 2)
+        return (self.SB, self.C, self.planes, self.I_pad, self.S_pad)
+
+    def corr_dtype(self):
+        return {FX_F32: torch.float32, FX_F16: torch.float16, FX_F16_SPLIT: torch.float16}.get(
+            self.precision, torch.bfloat16)
+
+    def vis_shape(self):
+        return (self.SB, self.C, self.B, 4, 2)
+
+    # -- checks -----------------------------------------------------------
+    def _dev(self, t: torch.Tensor, name: str, dtype, nbytes: int):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+        if t.device != self.device:
+            raise ValueError(f"{name} must be on {self.device} (got {t.device})")
+        if t.dtype != dtype:
+            raise TypeError(f"{name} must be {dtype} (got {t.dtype})")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() * t.element_size() != nbytes:
+            raise ValueError(f"{name} has {t.numel() * t.element_size()} bytes, expected {nbytes}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def _opt(self, t, name, dtype, nbytes):
+        return None if t is None else self._dev(t, name, dtype, nbytes)
+
+    # -- entry points -----------------------------------------------------
+    def channelize(self, raw: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        rdt = torch.int16 if self.fmt == FX_CI16 else torch.int8
+        if out is None:
+            out = torch.empty(self.chan_shape(), dtype=torch.float32, device=self.device)
+        check(self.lib.fx_channelize(self.handle, self._dev(raw, "raw", rdt, self.sizes.raw_bytes),
+                                     self._dev(out, "chan", torch.float32, self.sizes.chan_bytes),
+                                     _stream_ptr(stream)), "fx_channelize")
+        return out
+
+    def correct(self, chan, delay_begin, delay_end, bandpass=None, gains=None, out=None, stream=None):
+        if out is None:
+            out = torch.empty(self.corr_shape(), dtype=self.corr_dtype(), device=self.device)
+        N, C = self.N, self.C
+        check(self.lib.fx_correct(
+            self.handle, self._dev(chan, "chan", torch.float32, self.sizes.chan_bytes),
+            self._dev(delay_begin, "delay_begin", torch.float64, 8 * N),
+            self._dev(delay_end, "delay_end", torch.float64, 8 * N),
+            self._opt(bandpass, "bandpass", torch.float32, 4 * N * C),
+            self._opt(gains, "gains", torch.float32, 16 * N),
+            self._dev(out, "corr", self.corr_dtype(), self.sizes.corr_bytes),
+            _stream_ptr(stream)), "fx_correct")
+        return out
+
+    def correlate(self, corr, out=None, stream=None):
+        if out is None:
+            out = torch.empty(self.vis_shape(), dtype=torch.float32, device=self.device)
+        check(self.lib.fx_correlate(self.handle,
+                                    self._dev(corr, "corr", self.corr_dtype(), self.sizes.corr_bytes),
+                                    self._dev(out, "vis", torch.float32, self.sizes.vis_bytes),
+                                    _stream_ptr(stream)), "fx_correlate")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.fx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,224 @@
+// correct.cu -- fine delay compensation + bandpass correction (+ complex
+// gains) with the transposing write-back to the per-channel layout the
+// X-stage reads.
+//
+// Paper, Sec. "Signal processing with GPU kernels": the residual delays at the
+// start and end of a block give channel-dependent phase angles computed in
+// double precision; within the block the angle is interpolated linearly per
+// sample and the rotation itself is single precision; the delay/bandpass
+// kernel transposes on write-back so that the correlator reads all stations of
+// one channel together. Sec. "Verification and validation": double precision
+// is needed only for the delays.
+//
+// Two kernels per call:
+//   phase_table  FP64, one thread per (subband, station, channel):
+//                phi0 = 2 pi f_k tau_begin reduced mod 2 pi, and the
+//                per-spectrum step 2 pi f_k (tau_end - tau_begin) / S; both
+//                stored as FP32. FP64 work is SB*N*C, not per sample.
+//   correct_*    FP32 per sample: phi = phi0 + s * step, sincos, rotate,
+//                times bandpass * gain, transpose. Memory bound.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "internal.h"
+
+namespace fxi {
+namespace {
+
+__global__ void phase_table_kernel(const double *__restrict__ centres, const double *__restrict__ tau_b,
+                                   const double *__restrict__ tau_e, float2 *__restrict__ table,
+                                   int SB, int N, int C, int S, double fs)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)SB * N * C) return;
+    const int k = (int)(idx % C);
+    const int n = (int)((idx / C) % N);
+    const int sb = (int)(idx / ((long long)C * N));
+    const double two_pi = 6.283185307179586476925286766559;
+    const double f = centres[sb] + (double)(k - C / 2) * fs / (double)C;
+    const double phi0 = two_pi * f * tau_b[n];
+    const double red = phi0 - two_pi * rint(phi0 / two_pi);
+    const double step = two_pi * f * (tau_e[n] - tau_b[n]) / (double)S;
+    table[idx] = make_float2((float)red, (float)step);
+}
+
+// Y = X * bandpass * gain * exp(i (phi0 + s * step))
+__device__ __forceinline__ float2 correct_one(float2 x, float2 ph, int s, float bp, float2 g)
+{
+    float sn, cs;
+    sincosf(fmaf((float)s, ph.y, ph.x), &sn, &cs);
+    const float2 xg = make_float2(fmaf(x.x, g.x, -x.y * g.y), fmaf(x.x, g.y, x.y * g.x));
+    return make_float2(bp * fmaf(xg.x, cs, -xg.y * sn), bp * fmaf(xg.x, sn, xg.y * cs));
+}
+
+// ---- FP32 output [SB][C][S][I] -----------------------------------------
+// CTA = (subband, spectrum s, block of CB channels), all I inputs. Reads are
+// CB-channel runs of one (station, pol, spectrum); writes are I-input runs of
+// one (channel, spectrum); the tile turns the corner in shared memory.
+constexpr int kCB = 32;
+constexpr int kNT = 256;
+
+__global__ void __launch_bounds__(kNT)
+correct_f32_kernel(const float2 *__restrict__ chan, const float2 *__restrict__ table,
+                   const float *__restrict__ bandpass, const float2 *__restrict__ gains,
+                   float2 *__restrict__ corr, int N, int C, int S)
+{
+    extern __shared__ float2 tile[];   // [CB][I + 1]
+    const int I = N * kPols;
+    const int s = blockIdx.x;
+    const int c0 = blockIdx.y * kCB;
+    const int sb = blockIdx.z;
+    const int cb = min(kCB, C - c0);
+    for (int e = threadIdx.x; e < I * cb; e += kNT) {
+        const int c = e % cb, i = e / cb;
+        const int n = i / kPols, p = i % kPols;
+        const int k = c0 + c;
+        const float2 x = chan[((((long long)sb * N + n) * kPols + p) * S + s) * C + k];
+        const float2 ph = table[((long long)sb * N + n) * C + k];
+        const float bp = bandpass ? bandpass[(long long)n * C + k] : 1.f;
+        const float2 g = gains ? gains[i] : make_float2(1.f, 0.f);
+        tile[c * (I + 1) + i] = correct_one(x, ph, s, bp, g);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < I * cb; e += kNT) {
+        const int i = e % I, c = e / I;
+        corr[(((long long)sb * C + c0 + c) * S + s) * I + i] = tile[c * (I + 1) + i];
+    }
+}
+
+// ---- planar 16-bit output [SB][C][planes][I_pad][S_pad] -----------------
+// CTA tile = 8 channels x 64 spectra x 8 inputs. Reads are 8-channel runs
+// (64 B); writes are 64-spectrum rows (128 B) of one (channel, plane, input).
+constexpr int kPT_C = 8, kPT_S = 64, kPT_I = 8;
+constexpr int kPT_ROW = kPT_S + 2;   // float2 pad per (input, channel) row
+
+template <int MODE>  // 1: F16, 2: BF16, 3: F16 split
+__global__ void __launch_bounds__(kNT)
+correct_planar_kernel(const float2 *__restrict__ chan, const float2 *__restrict__ table,
+                      const float *__restrict__ bandpass, const float2 *__restrict__ gains,
+                      void *__restrict__ corr, int N, int C, int S, int I_pad, int S_pad, float scale)
+{
+    __shared__ float2 tile[kPT_I * kPT_C * kPT_ROW];
+    const int I = N * kPols;
+    const int s0 = blockIdx.x * kPT_S;
+    const int i0 = blockIdx.y * kPT_I;
+    const int cblocks = C / kPT_C;
+    const int c0 = (blockIdx.z % cblocks) * kPT_C;
+    const int sb = blockIdx.z / cblocks;
+
+    for (int e = threadIdx.x; e < kPT_I * kPT_S * kPT_C; e += kNT) {
+        const int c = e % kPT_C;
+        const int s = (e / kPT_C) % kPT_S;
+        const int il = e / (kPT_C * kPT_S);
+        const int i = i0 + il, ss = s0 + s, k = c0 + c;
+        float2 y = make_float2(0.f, 0.f);
+        if (i < I && ss < S) {
+            const int n = i / kPols, p = i % kPols;
+            const float2 x = chan[((((long long)sb * N + n) * kPols + p) * S + ss) * C + k];
+            const float2 ph = table[((long long)sb * N + n) * C + k];
+            const float bp = bandpass ? bandpass[(long long)n * C + k] : 1.f;
+            const float2 g = gains ? gains[i] : make_float2(1.f, 0.f);
+            y = correct_one(x, ph, ss, bp, g);
+            y.x *= scale;
+            y.y *= scale;
+        }
+        tile[(il * kPT_C + c) * kPT_ROW + s] = y;
+    }
+    __syncthreads();
+    constexpr int planes = (MODE == 3) ? 4 : 2;
+    const long long plane_stride = (long long)I_pad * S_pad;
+    // task = (input il, channel c, group of 8 spectra)
+    for (int t = threadIdx.x; t < kPT_I * kPT_C * (kPT_S / 8); t += kNT) {
+        const int g8 = t % (kPT_S / 8);
+        const int c = (t / (kPT_S / 8)) % kPT_C;
+        const int il = t / ((kPT_S / 8) * kPT_C);
+        const float2 *src = tile + (il * kPT_C + c) * kPT_ROW + g8 * 8;
+        const long long base = (((long long)sb * C + c0 + c) * planes) * plane_stride +
+                               (long long)(i0 + il) * S_pad + s0 + g8 * 8;
+        unsigned short re_hi[8], im_hi[8], re_lo[8], im_lo[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float2 y = src[q];
+            if constexpr (MODE == 2) {
+                re_hi[q] = __bfloat16_as_ushort(__float2bfloat16_rn(y.x));
+                im_hi[q] = __bfloat16_as_ushort(__float2bfloat16_rn(y.y));
+            } else {
+                const __half hr = __float2half_rn(y.x), hi = __float2half_rn(y.y);
+                re_hi[q] = __half_as_ushort(hr);
+                im_hi[q] = __half_as_ushort(hi);
+                if constexpr (MODE == 3) {
+                    re_lo[q] = __half_as_ushort(__float2half_rn(y.x - __half2float(hr)));
+                    im_lo[q] = __half_as_ushort(__float2half_rn(y.y - __half2float(hi)));
+                }
+            }
+        }
+        unsigned short *out = reinterpret_cast<unsigned short *>(corr);
+        auto store8 = [&](long long off, const unsigned short (&v)[8]) {
+            uint4 w;
+            w.x = v[0] | ((unsigned)v[1] << 16);
+            w.y = v[2] | ((unsigned)v[3] << 16);
+            w.z = v[4] | ((unsigned)v[5] << 16);
+            w.w = v[6] | ((unsigned)v[7] << 16);
+            *reinterpret_cast<uint4 *>(out + off) = w;
+        };
+        store8(base, re_hi);
+        store8(base + plane_stride, im_hi);
+        if constexpr (MODE == 3) {
+            store8(base + 2 * plane_stride, re_lo);
+            store8(base + 3 * plane_stride, im_lo);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_phase_table(const Handle &h, const double *tau_b, const double *tau_e,
+                               cudaStream_t st)
+{
+    const long long n = (long long)h.p.n_subbands * h.p.n_stations * h.p.n_channels;
+    const int threads = 256;
+    const long long blocks = (n + threads - 1) / threads;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    phase_table_kernel<<<(unsigned)blocks, threads, 0, st>>>(h.d_centres, tau_b, tau_e, h.d_phase,
+                                                             h.p.n_subbands, h.p.n_stations,
+                                                             h.p.n_channels, h.p.n_spectra,
+                                                             h.p.sample_rate_hz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_correct(const Handle &h, const float2 *chan, const float *bandpass,
+                           const float2 *gains, void *corr, cudaStream_t st)
+{
+    const int N = h.p.n_stations, C = h.p.n_channels, S = h.p.n_spectra, SB = h.p.n_subbands;
+    if (h.p.precision == FX_F32) {
+        const size_t smem = sizeof(float2) * kCB * (h.I + 1);
+        if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+        cudaError_t e = cudaFuncSetAttribute(correct_f32_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid(S, (C + kCB - 1) / kCB, SB);
+        if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+        correct_f32_kernel<<<grid, kNT, smem, st>>>(chan, h.d_phase, bandpass, gains,
+                                                    reinterpret_cast<float2 *>(corr), N, C, S);
+        return cudaGetLastError();
+    }
+    dim3 grid(h.S_pad / kPT_S, h.I_pad / kPT_I, SB * (C / kPT_C));
+    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+    switch (h.p.precision) {
+    case FX_F16:
+        correct_planar_kernel<1><<<grid, kNT, 0, st>>>(chan, h.d_phase, bandpass, gains, corr, N, C, S,
+                                                       h.I_pad, h.S_pad, h.operand_scale);
+        break;
+    case FX_BF16:
+        correct_planar_kernel<2><<<grid, kNT, 0, st>>>(chan, h.d_phase, bandpass, gains, corr, N, C, S,
+                                                       h.I_pad, h.S_pad, h.operand_scale);
+        break;
+    default:
+        correct_planar_kernel<3><<<grid, kNT, 0, st>>>(chan, h.d_phase, bandpass, gains, corr, N, C, S,
+                                                       h.I_pad, h.S_pad, h.operand_scale);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fxi

@@ -1,0 +1,231 @@
+// fx_api.cu -- the C ABI declared in include/fx.h: parameter validation,
+// handle and workspace ownership, dispatch to the kernels.
+//
+// One wrapper per kernel validates shapes and pointers before launching, in
+// the spirit of the paper's per-kernel wrapper classes that hold execution
+// configuration and buffer sizes (Sec. "Signal processing with GPU kernels").
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+fx_status fail(fx_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+fx_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(FX_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool is_pow2(float x)
+{
+    int e;
+    float m = std::frexp(x, &e);
+    return x > 0.f && m == 0.5f;
+}
+
+}  // namespace
+
+struct fx_handle : fxi::Handle {};
+
+extern "C" const char *fx_last_error(void) { return g_err; }
+
+extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
+{
+    if (!out) return fail(FX_ERR_INVALID, "fx_create: out is NULL");
+    *out = nullptr;
+    if (!pp) return fail(FX_ERR_INVALID, "fx_create: params is NULL");
+    const fx_params &p = *pp;
+    if (p.n_pols != fxi::kPols) return fail(FX_ERR_UNSUPPORTED, "n_pols must be 2 (got %d)", p.n_pols);
+    if (p.n_stations < 1 || p.n_stations > 4096)
+        return fail(FX_ERR_INVALID, "n_stations out of range (%d)", p.n_stations);
+    if (p.n_subbands < 1) return fail(FX_ERR_INVALID, "n_subbands must be >= 1 (got %d)", p.n_subbands);
+    if (p.n_spectra < 1) return fail(FX_ERR_INVALID, "n_spectra must be >= 1 (got %d)", p.n_spectra);
+    if (p.n_taps < 1) return fail(FX_ERR_INVALID, "n_taps must be >= 1 (got %d)", p.n_taps);
+    if (!fxi::ppf_supported(p.n_channels, p.n_taps))
+        return fail(FX_ERR_UNSUPPORTED, "channels %d / taps %d not built (C in {16,64,256}, T in {4,8,16})",
+                    p.n_channels, p.n_taps);
+    if (p.format != FX_CI16 && p.format != FX_CI8) return fail(FX_ERR_INVALID, "bad format %d", p.format);
+    if (p.precision < FX_F32 || p.precision > FX_F16_SPLIT)
+        return fail(FX_ERR_INVALID, "bad precision %d", p.precision);
+    if (!(p.sample_rate_hz > 0)) return fail(FX_ERR_INVALID, "sample_rate_hz must be > 0");
+    if (!p.h_subband_centre_hz) return fail(FX_ERR_INVALID, "h_subband_centre_hz is NULL");
+    if (!p.h_taps) return fail(FX_ERR_INVALID, "h_taps is NULL");
+    if (p.flags != 0) return fail(FX_ERR_INVALID, "flags must be 0");
+    float scale = p.operand_scale == 0.f ? 1.f : p.operand_scale;
+    if (!is_pow2(scale)) return fail(FX_ERR_INVALID, "operand_scale must be a power of two");
+    if (p.precision == FX_F32 && scale != 1.f)
+        return fail(FX_ERR_INVALID, "operand_scale applies to FP16/BF16 only");
+    const long long I = 2LL * p.n_stations;
+    const long long S = p.n_spectra;
+    const long long SB = p.n_subbands;
+    // keep every flattened index within 64-bit and the planar row length within int
+    if (S > (1 << 24)) return fail(FX_ERR_INVALID, "n_spectra too large");
+
+    fx_handle *h = new (std::nothrow) fx_handle();
+    if (!h) return fail(FX_ERR_NOMEM, "host allocation failed");
+    h->p = p;
+    h->p.h_subband_centre_hz = nullptr;
+    h->p.h_taps = nullptr;
+    h->I = (int)I;
+    h->I_pad = (int)((I + 15) / 16 * 16);
+    h->S_pad = (int)((S + 63) / 64 * 64);
+    h->B = p.n_stations * (p.n_stations + 1) / 2;
+    h->operand_scale = scale;
+    cudaGetDevice(&h->device);
+
+    const int C = p.n_channels, T = p.n_taps, N = p.n_stations;
+    std::vector<float2> tw(C);
+    for (int m = 0; m < C; ++m) {
+        const double a = 2.0 * 3.14159265358979323846 * (double)m / (double)C;
+        tw[m] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    }
+    int ntiles = fxi::xf32_build_tiles(N, nullptr);
+    std::vector<int2> tiles(ntiles);
+    fxi::xf32_build_tiles(N, tiles.data());
+    h->xf32_ntiles = ntiles;
+
+    cudaError_t e = cudaSuccess;
+#define FX_TRY(call)                                             \
+    do {                                                         \
+        e = (call);                                              \
+        if (e != cudaSuccess) {                                  \
+            fx_destroy(h);                                       \
+            return e == cudaErrorMemoryAllocation                \
+                       ? fail(FX_ERR_NOMEM, "%s: %s", #call, cudaGetErrorString(e)) \
+                       : cuda_fail(e, #call);                    \
+        }                                                        \
+    } while (0)
+    FX_TRY(cudaMalloc(&h->d_taps, sizeof(float) * T * C));
+    FX_TRY(cudaMalloc(&h->d_twiddle, sizeof(float2) * C));
+    FX_TRY(cudaMalloc(&h->d_centres, sizeof(double) * SB));
+    FX_TRY(cudaMalloc(&h->d_phase, sizeof(float2) * SB * N * C));
+    FX_TRY(cudaMalloc(&h->d_status, sizeof(int) * 4));
+    FX_TRY(cudaMalloc(&h->d_xf32_tiles, sizeof(int2) * ntiles));
+    FX_TRY(cudaMemcpy(h->d_taps, p.h_taps, sizeof(float) * T * C, cudaMemcpyHostToDevice));
+    FX_TRY(cudaMemcpy(h->d_twiddle, tw.data(), sizeof(float2) * C, cudaMemcpyHostToDevice));
+    FX_TRY(cudaMemcpy(h->d_centres, p.h_subband_centre_hz, sizeof(double) * SB,
+                      cudaMemcpyHostToDevice));
+    FX_TRY(cudaMemcpy(h->d_xf32_tiles, tiles.data(), sizeof(int2) * ntiles, cudaMemcpyHostToDevice));
+    FX_TRY(cudaMemset(h->d_status, 0, sizeof(int) * 4));
+#undef FX_TRY
+    *out = h;
+    g_err[0] = 0;
+    return FX_OK;
+}
+
+extern "C" void fx_destroy(fx_handle *h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    cudaFree(h->d_taps);
+    cudaFree(h->d_twiddle);
+    cudaFree(h->d_centres);
+    cudaFree(h->d_phase);
+    cudaFree(h->d_status);
+    cudaFree(h->d_xf32_tiles);
+    delete h;
+}
+
+extern "C" fx_status fx_query_sizes(const fx_handle *h, fx_sizes *o)
+{
+    if (!h || !o) return fail(FX_ERR_INVALID, "fx_query_sizes: NULL argument");
+    const fx_params &p = h->p;
+    const size_t SB = p.n_subbands, N = p.n_stations, C = p.n_channels, S = p.n_spectra;
+    const size_t L = (S + p.n_taps - 1) * C;
+    const size_t bpc = p.format == FX_CI16 ? 4 : 2;
+    o->raw_bytes = SB * N * L * 2 * bpc;
+    o->chan_bytes = SB * N * 2 * S * C * sizeof(float2);
+    switch (p.precision) {
+    case FX_F32: o->corr_bytes = SB * C * S * N * 2 * sizeof(float2); o->corr_planes = 0; break;
+    case FX_F16:
+    case FX_BF16: o->corr_bytes = SB * C * 2 * (size_t)h->I_pad * h->S_pad * 2; o->corr_planes = 2; break;
+    default: o->corr_bytes = SB * C * 4 * (size_t)h->I_pad * h->S_pad * 2; o->corr_planes = 4; break;
+    }
+    o->vis_bytes = SB * C * (size_t)h->B * 4 * sizeof(float2);
+    o->n_inputs = h->I;
+    o->n_inputs_pad = h->I_pad;
+    o->n_spectra_pad = h->S_pad;
+    o->n_baselines = h->B;
+    return FX_OK;
+}
+
+static fx_status check_handle(const fx_handle *h, const char *who)
+{
+    if (!h) return fail(FX_ERR_INVALID, "%s: handle is NULL", who);
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != h->device)
+        return fail(FX_ERR_INVALID, "%s: current device %d is not the handle's device %d", who, dev,
+                    h->device);
+    return FX_OK;
+}
+
+static fx_status after_launch(cudaError_t e, const char *who)
+{
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return FX_OK;
+}
+
+extern "C" fx_status fx_channelize(fx_handle *h, const void *d_raw, float *d_chan, fx_stream stream)
+{
+    fx_status st = check_handle(h, "fx_channelize");
+    if (st) return st;
+    if (!d_raw || !d_chan) return fail(FX_ERR_INVALID, "fx_channelize: NULL buffer");
+    if (((uintptr_t)d_raw & 15) || ((uintptr_t)d_chan & 15))
+        return fail(FX_ERR_INVALID, "fx_channelize: buffers must be 16-byte aligned");
+    return after_launch(fxi::launch_ppf(*h, d_raw, reinterpret_cast<float2 *>(d_chan),
+                                        (cudaStream_t)stream),
+                        "fx_channelize");
+}
+
+extern "C" fx_status fx_correct(fx_handle *h, const float *d_chan, const double *d_delay_begin,
+                                const double *d_delay_end, const float *d_bandpass,
+                                const float *d_gains, void *d_corr, fx_stream stream)
+{
+    fx_status st = check_handle(h, "fx_correct");
+    if (st) return st;
+    if (!d_chan || !d_corr || !d_delay_begin || !d_delay_end)
+        return fail(FX_ERR_INVALID, "fx_correct: NULL buffer");
+    if (((uintptr_t)d_chan & 15) || ((uintptr_t)d_corr & 15) || ((uintptr_t)d_gains & 7) ||
+        ((uintptr_t)d_bandpass & 3) || ((uintptr_t)d_delay_begin & 7) || ((uintptr_t)d_delay_end & 7))
+        return fail(FX_ERR_INVALID, "fx_correct: misaligned buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = fxi::launch_phase_table(*h, d_delay_begin, d_delay_end, s);
+    if (e == cudaSuccess)
+        e = fxi::launch_correct(*h, reinterpret_cast<const float2 *>(d_chan), d_bandpass,
+                                reinterpret_cast<const float2 *>(d_gains), d_corr, s);
+    return after_launch(e, "fx_correct");
+}
+
+extern "C" fx_status fx_correlate(fx_handle *h, const void *d_corr, float *d_vis, fx_stream stream)
+{
+    fx_status st = check_handle(h, "fx_correlate");
+    if (st) return st;
+    if (!d_corr || !d_vis) return fail(FX_ERR_INVALID, "fx_correlate: NULL buffer");
+    if (((uintptr_t)d_corr & 127) || ((uintptr_t)d_vis & 15))
+        return fail(FX_ERR_INVALID, "fx_correlate: corr must be 128-byte and vis 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    float2 *vis = reinterpret_cast<float2 *>(d_vis);
+    cudaError_t e;
+    if (h->p.precision == FX_F32)
+        e = fxi::launch_xcorr_f32(*h, reinterpret_cast<const float2 *>(d_corr), vis, s);
+    else
+        e = fxi::launch_xcorr_tc(*h, d_corr, vis, s);
+    return after_launch(e, "fx_correlate");
+}

@@ -1,0 +1,48 @@
+// internal.h -- declarations shared by the library's translation units.
+// Not part of the public ABI (include/fx.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/fx.h"
+
+namespace fxi {
+
+constexpr int kPols = 2;
+
+// Handle state. Device pointers are owned by the handle.
+struct Handle {
+    fx_params p;                 // copy; host pointers inside are cleared
+    int I, I_pad, S_pad, B;
+    float operand_scale;
+    int device;
+    // device buffers
+    float *d_taps = nullptr;           // [T*C]
+    float2 *d_twiddle = nullptr;       // [C]  exp(-2 pi i m / C), from host FP64
+    double *d_centres = nullptr;       // [SB]
+    float2 *d_phase = nullptr;         // [SB][N][C] (phi0 mod 2pi, per-spectrum step)
+    int *d_status = nullptr;           // device-side error word
+    int2 *d_xf32_tiles = nullptr;      // tile list of the FP32 correlator
+    int xf32_ntiles = 0;
+};
+
+// ppf.cu
+cudaError_t launch_ppf(const Handle &h, const void *raw, float2 *chan, cudaStream_t st);
+bool ppf_supported(int C, int T);
+
+// correct.cu
+cudaError_t launch_phase_table(const Handle &h, const double *tau_b, const double *tau_e,
+                               cudaStream_t st);
+cudaError_t launch_correct(const Handle &h, const float2 *chan, const float *bandpass,
+                           const float2 *gains, void *corr, cudaStream_t st);
+
+// xcorr_f32.cu
+int xf32_build_tiles(int N, int2 *host_tiles /* may be null: count only */);
+cudaError_t launch_xcorr_f32(const Handle &h, const float2 *corr, float2 *vis, cudaStream_t st);
+
+// xcorr_tc.cu
+cudaError_t launch_xcorr_tc(const Handle &h, const void *corr, float2 *vis, cudaStream_t st);
+
+}  // namespace fxi

@@ -1,0 +1,249 @@
+// ppf.cu -- polyphase filter bank: int16/int8 -> FP32 conversion, T-tap FIR
+// per channel and C-point FFT, per (subband, station, polarisation).
+//
+// Paper: Sec. "Signal processing with GPU kernels" (FIR and FFT kernels
+// channelise each subband, FIR history is carried across blocks) and
+// Sec. "Processing steps" (fixed-point input converted to floating point).
+// The paper's FFT was a cuFFT call; here the FFT is fused behind the FIR.
+//
+// Work decomposition (one CTA = NPC stations x 2 pols x all C channels x a run
+// of spectra):
+//   * Raw samples stream through shared memory 16 time rows (one row = C
+//     samples) at a time with cp.async, double buffered.
+//   * FIR: thread (station, channel c, pol p) keeps the last T samples of its
+//     channel in registers as a circular buffer and its T taps in registers;
+//     each new row costs one 4-byte (int16) or 2-byte (int8) shared load and
+//     2T FMAs. Rounds are 16 spectra long, a multiple of T, so the circular
+//     indices are compile-time constants.
+//   * FFT: C = R*R. Pass 1: R threads per transform, each an R-point FFT over
+//     stride-R samples in registers, times the inter-pass twiddle (host-FP64
+//     table); pass 2: R threads per transform, R-point FFTs along the other
+//     index. Shared memory holds the 16-spectrum batch between passes.
+//   * Output channel k = (m + C/2) mod C (ascending sky frequency).
+#include "internal.h"
+#include "fft_reg.cuh"
+
+namespace fxi {
+namespace {
+
+constexpr int kRound = 16;  // spectra per round; a multiple of every supported T
+
+template <int C>
+struct PpfCfg {
+    static constexpr int R = (C == 16) ? 4 : (C == 64) ? 8 : 16;  // C = R * R
+    static constexpr int NPC = (C * kPols >= 256) ? 1 : 256 / (C * kPols);  // stations per CTA
+    static constexpr int NT = NPC * C * kPols;                    // threads per CTA
+    static constexpr int PAD = (R == 4) ? 4 : 8;                  // float2 pad per smem row
+    static constexpr int ROW = C + PAD;
+    static constexpr int NTR = NPC * kPols * kRound;              // transforms per round
+    static constexpr int FFT_ITERS = NTR * R / NT;
+    static_assert(R * R == C, "C must be a square of R");
+    static_assert(NTR * R % NT == 0, "FFT tasks must tile the CTA");
+};
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, int src_bytes)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ float2 to_f2(short2 v) { return make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ float2 to_f2(char2 v) { return make_float2((float)v.x, (float)v.y); }
+
+template <int C, typename TIn>
+constexpr size_t ppf_smem_bytes()
+{
+    using Cfg = PpfCfg<C>;
+    return (size_t)C * sizeof(float2) + 2ull * kRound * Cfg::NPC * C * kPols * sizeof(TIn) +
+           (size_t)Cfg::NTR * Cfg::ROW * sizeof(float2);
+}
+
+template <int C, int T, typename TIn>
+__global__ void __launch_bounds__(PpfCfg<C>::NT)
+ppf_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *__restrict__ taps,
+           const float2 *__restrict__ twiddle, int N, int S, int rounds_per_cta)
+{
+    using Cfg = PpfCfg<C>;
+    constexpr int R = Cfg::R, NPC = Cfg::NPC, NT = Cfg::NT, ROW = Cfg::ROW;
+    constexpr int ROW_BYTES = C * kPols * (int)sizeof(TIn);     // one time row of one station
+    constexpr int BUF_BYTES = kRound * NPC * ROW_BYTES;
+    static_assert(ROW_BYTES % 16 == 0, "rows must be whole 16-byte chunks");
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2 *tw = reinterpret_cast<float2 *>(smem);
+    unsigned char *inbuf = smem + C * sizeof(float2);
+    float2 *u = reinterpret_cast<float2 *>(inbuf + 2 * BUF_BYTES);
+
+    const int tid = threadIdx.x;
+    const int sb = blockIdx.z;
+    const int n0 = blockIdx.y * NPC;
+    const int s0 = blockIdx.x * rounds_per_cta * kRound;
+    const int rows_total = S + T - 1;
+    const long long L = (long long)rows_total * C;
+    const int nrounds = min(rounds_per_cta, (S - s0 + kRound - 1) / kRound);
+
+    // stage rows [r0, r0 + nrows) of the CTA's stations into buffer `buf`
+    auto stage = [&](int buf, int r0, int nrows) {
+        const int chunks = nrows * ROW_BYTES / 16;
+        for (int q = tid; q < NPC * chunks; q += NT) {
+            const int st = q / chunks, ch = q - st * chunks;
+            const int n = n0 + st;
+            const int row_in = (ch * 16) / ROW_BYTES;
+            const int byte_in_row = (ch * 16) - row_in * ROW_BYTES;
+            unsigned char *dst = inbuf + buf * BUF_BYTES + (row_in * NPC + st) * ROW_BYTES + byte_in_row;
+            const bool ok = (n < N) && (r0 + row_in < rows_total);
+            const unsigned char *src = reinterpret_cast<const unsigned char *>(raw);
+            if (ok) src += ((((long long)sb * N + n) * L + (long long)r0 * C) * kPols) * sizeof(TIn) + ch * 16;
+            cp_async16(dst, src, ok ? 16 : 0);
+        }
+    };
+
+    // FIR role of this thread
+    const int p = tid % kPols;
+    const int c = (tid / kPols) % C;
+    const int nl = tid / (kPols * C);
+
+    for (int i = tid; i < C; i += NT) tw[i] = twiddle[i];
+    float h[T];
+#pragma unroll
+    for (int k = 0; k < T; ++k) h[k] = taps[k * C + c];
+
+    // warm-up rows (FIR history) into buffer 1, first round into buffer 0
+    stage(1, s0, T - 1);
+    cp_async_commit();
+    stage(0, s0 + T - 1, kRound);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+
+    float2 win[T];
+    const TIn *in1 = reinterpret_cast<const TIn *>(inbuf + BUF_BYTES);
+#pragma unroll
+    for (int k = 0; k < T - 1; ++k) win[k] = to_f2(in1[k * NT + tid]);
+    win[T - 1] = make_float2(0.f, 0.f);
+    __syncthreads();
+    if (nrounds > 1) stage(1, s0 + T - 1 + kRound, kRound);
+    cp_async_commit();
+
+    for (int b = 0; b < nrounds; ++b) {
+        cp_async_wait<1>();
+        __syncthreads();
+        // ---- FIR over 16 new rows ----
+        const TIn *in = reinterpret_cast<const TIn *>(inbuf + (b & 1) * BUF_BYTES);
+#pragma unroll
+        for (int j = 0; j < kRound; ++j) {
+            win[(T - 1 + j) % T] = to_f2(in[j * NT + tid]);
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < T; ++k) {
+                const float2 x = win[(j + k) % T];
+                acc.x = fmaf(h[k], x.x, acc.x);
+                acc.y = fmaf(h[k], x.y, acc.y);
+            }
+            u[((nl * kPols + p) * kRound + j) * ROW + c] = acc;
+        }
+        __syncthreads();
+        if (b + 2 < nrounds) stage(b & 1, s0 + T - 1 + (b + 2) * kRound, kRound);
+        cp_async_commit();
+
+        // ---- FFT pass 1: R-point FFTs over n1 (stride R), times W_C^(n2 k1) ----
+#pragma unroll
+        for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
+            const int task = it * NT + tid;
+            const int tr = task / R, n2 = task % R;
+            float2 *row = u + tr * ROW;
+            float2 v[R];
+#pragma unroll
+            for (int n1 = 0; n1 < R; ++n1) v[n1] = row[R * n1 + n2];
+            fft_reg<R>(v);
+#pragma unroll
+            for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], tw[n2 * k1]);
+#pragma unroll
+            for (int k1 = 0; k1 < R; ++k1) row[R * k1 + n2] = v[k1];
+        }
+        __syncthreads();
+        // ---- FFT pass 2: R-point FFTs over n2, X[k1 + R k2] ----
+#pragma unroll
+        for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
+            const int task = it * NT + tid;
+            const int tr = task / R, k1 = task % R;
+            const float2 *row = u + tr * ROW;
+            float2 v[R];
+#pragma unroll
+            for (int n2 = 0; n2 < R; ++n2) v[n2] = row[R * k1 + n2];
+            fft_reg<R>(v);
+            const int j = tr % kRound;
+            const int pp = (tr / kRound) % kPols;
+            const int n = n0 + tr / (kRound * kPols);
+            const int s = s0 + b * kRound + j;
+            if (s < S && n < N) {
+                float2 *out = chan + ((((long long)blockIdx.z * N + n) * kPols + pp) * S + s) * C;
+#pragma unroll
+                for (int k2 = 0; k2 < R; ++k2) out[k1 + R * ((k2 + R / 2) % R)] = v[k2];
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
+template <int C, int T, typename TIn>
+cudaError_t launch_t(const Handle &h, const void *raw, float2 *chan, cudaStream_t st)
+{
+    using Cfg = PpfCfg<C>;
+    const int N = h.p.n_stations, S = h.p.n_spectra, SB = h.p.n_subbands;
+    const int rounds_total = (S + kRound - 1) / kRound;
+    const int sgroups = (N + Cfg::NPC - 1) / Cfg::NPC;
+    int rpc = 8;
+    while (rpc > 1 && (long long)((rounds_total + rpc - 1) / rpc) * sgroups * SB < 152LL * 4) rpc /= 2;
+    dim3 grid((rounds_total + rpc - 1) / rpc, sgroups, SB);
+    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+    constexpr size_t smem = ppf_smem_bytes<C, TIn>();
+    auto kern = ppf_kernel<C, T, TIn>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, Cfg::NT, smem, st>>>(reinterpret_cast<const TIn *>(raw), chan, h.d_taps, h.d_twiddle,
+                                      N, S, rpc);
+    return cudaGetLastError();
+}
+
+template <int C, typename TIn>
+cudaError_t launch_taps(const Handle &h, const void *raw, float2 *chan, cudaStream_t st)
+{
+    switch (h.p.n_taps) {
+    case 4: return launch_t<C, 4, TIn>(h, raw, chan, st);
+    case 8: return launch_t<C, 8, TIn>(h, raw, chan, st);
+    case 16: return launch_t<C, 16, TIn>(h, raw, chan, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename TIn>
+cudaError_t launch_fmt(const Handle &h, const void *raw, float2 *chan, cudaStream_t st)
+{
+    switch (h.p.n_channels) {
+    case 16: return launch_taps<16, TIn>(h, raw, chan, st);
+    case 64: return launch_taps<64, TIn>(h, raw, chan, st);
+    case 256: return launch_taps<256, TIn>(h, raw, chan, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+bool ppf_supported(int C, int T)
+{
+    return (C == 16 || C == 64 || C == 256) && (T == 4 || T == 8 || T == 16);
+}
+
+cudaError_t launch_ppf(const Handle &h, const void *raw, float2 *chan, cudaStream_t st)
+{
+    if (h.p.format == FX_CI16) return launch_fmt<short2>(h, raw, chan, st);
+    return launch_fmt<char2>(h, raw, chan, st);
+}
+
+}  // namespace fxi

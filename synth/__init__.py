@@ -154,6 +154,11 @@ def random_gains(rng: np.random.Generator, n_stations: int, n_pols: int = 2,
     return np.stack([amp * np.cos(ph), amp * np.sin(ph)], axis=-1)
 
 
+def noise(seed: int, shape, sigma: float = 1.0) -> np.ndarray:
+    """Plain seeded Gaussian noise of any shape (float64)."""
+    return np.random.Generator(np.random.PCG64(seed)).standard_normal(shape) * sigma
+
+
 def channelised_noise(seed: int, n_subbands: int, n_stations: int, n_pols: int,
                       n_channels: int, n_spectra: int, sigma: float = 1.0) -> np.ndarray:
     """Already-channelised complex samples [SB][N][P][S][C][2] float64 (the
