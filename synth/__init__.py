@@ -179,35 +179,39 @@ def make_raw_torch(seed: int, fmt: int, n_subbands: int, n_stations: int, n_chan
                    tones: list | None = None, centre_hz: float = 150e6, device="cuda",
                    out=None):
     """Returns a torch int16/int8 tensor [SB][N][L][P][2] on `device`, made one
-    subband at a time so the float scratch stays small."""
+    subband at a time so the float scratch stays small. Same signal model as
+    make_block (noise + channel-centred tones with per-station delays)."""
     import torch
-    C, T, S = n_channels, n_taps, n_spectra
+    C, T, S, N, P = n_channels, n_taps, n_spectra, n_stations, n_pols
     L = (S + T - 1) * C
     dt = torch.int16 if fmt == CI16 else torch.int8
     lim = FORMAT_MAX[fmt]
     if out is None:
-        out = torch.empty((n_subbands, n_stations, L, n_pols, 2), dtype=dt, device=device)
+        out = torch.empty((n_subbands, N, L, P, 2), dtype=dt, device=device)
     g = torch.Generator(device=device)
     centres = subband_centres(n_subbands, centre_hz)
-    tone_cache = []
+    t = torch.arange(L, device=device, dtype=torch.int64)
+    pol_ph = torch.tensor([p * math.pi / 3 for p in range(P)], device=device, dtype=torch.float64)
+    pol_amp = torch.tensor([1.0 - 0.25 * p for p in range(P)], device=device, dtype=torch.float64)
+    prepared = []
     for tone in tones or []:
         m = tone.channel - C // 2
-        t = torch.arange(L, device=device, dtype=torch.int64)
-        bb = 2 * math.pi * ((m * t) % C).to(torch.float64) / C
-        tone_cache.append((tone, m, bb))
+        bb = (2 * math.pi * ((m * t) % C).to(torch.float64) / C)                 # [L]
+        amp = torch.full((N,), float(tone.amp), dtype=torch.float64, device=device)
+        if tone.ripple is not None:
+            amp = amp * torch.as_tensor(np.asarray(tone.ripple)[:, tone.channel], device=device)
+        delays = torch.as_tensor(np.asarray(tone.delays, np.float64), device=device)
+        prepared.append((m, bb, amp, delays))
     for sb in range(n_subbands):
         g.manual_seed(seed * 1000003 + sb)
-        z = torch.randn((n_stations, L, n_pols, 2), generator=g, device=device,
-                        dtype=torch.float32) * sigma
-        for tone, m, bb in tone_cache:
+        z = torch.randn((N, L, P, 2), generator=g, device=device, dtype=torch.float32) * sigma
+        for m, bb, amp, delays in prepared:
             f_sky = centres[sb] + m * SAMPLE_RATE_HZ / C
-            for n in range(n_stations):
-                a = tone.amp * (1.0 if tone.ripple is None else float(tone.ripple[n, tone.channel]))
-                ph0 = -2 * math.pi * f_sky * float(tone.delays[n])
-                for p in range(n_pols):
-                    ph = bb + (ph0 + p * math.pi / 3)
-                    amp = a * (1.0 - 0.25 * p)
-                    z[n, :, p, 0] += (amp * torch.cos(ph)).to(torch.float32)
-                    z[n, :, p, 1] += (amp * torch.sin(ph)).to(torch.float32)
+            ph0 = -2 * math.pi * f_sky * delays                                    # [N]
+            ph = (bb[None, :, None] + ph0[:, None, None] + pol_ph[None, None, :])  # [N][L][P]
+            a = (amp[:, None, None] * pol_amp[None, None, :])
+            z[..., 0] += (a * torch.cos(ph)).to(torch.float32)
+            z[..., 1] += (a * torch.sin(ph)).to(torch.float32)
+            del ph
         out[sb] = torch.clamp(torch.round(z), -lim, lim).to(dt)
     return out
