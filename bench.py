@@ -210,7 +210,7 @@ def workload_inputs(w, device):
 # reference arm / cpu baseline: the FP64 oracle on a bounded sample
 # ---------------------------------------------------------------------------
 
-def oracle_sample(w, budget_s=20.0, max_subbands=4):
+def oracle_sample(w, budget_s=30.0, max_subbands=32):
     """Time the oracle on whole subbands of the workload (subbands are
     independent, so the per-subband time scales linearly to SB)."""
     import numpy as np

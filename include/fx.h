@@ -83,8 +83,14 @@ typedef struct {
                                     k*C + c; copied at fx_create */
     float operand_scale;         /* power of two multiplied into FP16/BF16
                                     operands and divided out of vis; 0 means 1 */
-    unsigned flags;              /* reserved, must be 0 */
+    unsigned flags;              /* 0, or FX_FLAG_TEST_NO_LOADS */
 } fx_params;
+
+/* Failure-detection test hook: the tensor-core X-stage issues no operand
+ * loads, so its consumer waits run out after about a millisecond; the call
+ * itself succeeds and fx_poll_status() then reports FX_ERR_TIMEOUT. The GPU
+ * context stays usable. Never set in production. */
+#define FX_FLAG_TEST_NO_LOADS 0x80000000u
 
 typedef struct fx_handle fx_handle;
 
@@ -147,6 +153,15 @@ fx_status fx_correct(fx_handle *h, const float *d_chan, const double *d_delay_be
  * operands run on the CUDA cores; FP16/BF16/split operands on the tcgen05
  * tensor cores with FP32 accumulation (split: hi*hi' + hi*lo' + lo*hi'). */
 fx_status fx_correlate(fx_handle *h, const void *d_corr, float *d_vis, fx_stream stream);
+
+/* Synchronises the device, then reports asynchronous failures of earlier
+ * calls: FX_ERR_CUDA for a CUDA error, FX_ERR_TIMEOUT if a bounded device-side
+ * wait of the tensor-core X-stage gave up (each wait has a budget of about two
+ * seconds; the kernel then drains its in-flight copies, frees its tensor
+ * memory and exits, and that call's visibilities are incomplete). *code (may
+ * be NULL) receives the role that gave up: 1 loader, 2 MMA issuer, 3 epilogue.
+ * The status word is cleared by the call. Not capturable in a CUDA graph. */
+fx_status fx_poll_status(fx_handle *h, int *code);
 
 #ifdef __cplusplus
 }

@@ -52,7 +52,9 @@ SIGNATURES = {
     "fx_channelize": (I, [P, P, P, P]),
     "fx_correct": (I, [P, P, P, P, P, P, P, P]),
     "fx_correlate": (I, [P, P, P, P]),
+    "fx_poll_status": (I, [P, ctypes.POINTER(ctypes.c_int)]),
 }
+FX_FLAG_TEST_NO_LOADS = 0x80000000
 
 _lib = None
 

@@ -65,7 +65,7 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
     if (!(p.sample_rate_hz > 0)) return fail(FX_ERR_INVALID, "sample_rate_hz must be > 0");
     if (!p.h_subband_centre_hz) return fail(FX_ERR_INVALID, "h_subband_centre_hz is NULL");
     if (!p.h_taps) return fail(FX_ERR_INVALID, "h_taps is NULL");
-    if (p.flags != 0) return fail(FX_ERR_INVALID, "flags must be 0");
+    if ((p.flags & ~FX_FLAG_TEST_NO_LOADS) != 0) return fail(FX_ERR_INVALID, "unknown flags 0x%x", p.flags);
     float scale = p.operand_scale == 0.f ? 1.f : p.operand_scale;
     if (!is_pow2(scale)) return fail(FX_ERR_INVALID, "operand_scale must be a power of two");
     if (p.precision == FX_F32 && scale != 1.f)
@@ -87,6 +87,11 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
     h->B = p.n_stations * (p.n_stations + 1) / 2;
     h->operand_scale = scale;
     cudaGetDevice(&h->device);
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (h->num_sms <= 0) h->num_sms = 152;
+    h->tc_test_no_tma = (p.flags & FX_FLAG_TEST_NO_LOADS) ? 1 : 0;
+    // ~2 s at 2 GHz; ~1 ms for the failure-detection test hook
+    h->tc_timeout_cycles = h->tc_test_no_tma ? 2000000LL : 4000000000LL;
 
     const int C = p.n_channels, T = p.n_taps, N = p.n_stations;
     std::vector<float2> tw(C);
@@ -213,6 +218,24 @@ extern "C" fx_status fx_correct(fx_handle *h, const float *d_chan, const double 
     return after_launch(e, "fx_correct");
 }
 
+extern "C" fx_status fx_poll_status(fx_handle *h, int *code)
+{
+    fx_status st = check_handle(h, "fx_poll_status");
+    if (st) return st;
+    if (code) *code = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "fx_poll_status: asynchronous error");
+    int w[2] = {0, 0};
+    e = cudaMemcpy(w, h->d_status, sizeof(w), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "fx_poll_status");
+    if (w[0] != 0) {
+        cudaMemset(h->d_status, 0, sizeof(int) * 4);
+        if (code) *code = w[0];
+        return fail(FX_ERR_TIMEOUT, "device-side wait gave up (role %d, CTA %d)", w[0], w[1]);
+    }
+    return FX_OK;
+}
+
 extern "C" fx_status fx_correlate(fx_handle *h, const void *d_corr, float *d_vis, fx_stream stream)
 {
     fx_status st = check_handle(h, "fx_correlate");
@@ -223,9 +246,15 @@ extern "C" fx_status fx_correlate(fx_handle *h, const void *d_corr, float *d_vis
     cudaStream_t s = (cudaStream_t)stream;
     float2 *vis = reinterpret_cast<float2 *>(d_vis);
     cudaError_t e;
-    if (h->p.precision == FX_F32)
+    if (h->p.precision == FX_F32) {
         e = fxi::launch_xcorr_f32(*h, reinterpret_cast<const float2 *>(d_corr), vis, s);
-    else
+    } else {
+        int rl, stg;
+        unsigned sb;
+        if (!fxi::xtc_plan(*h, &rl, &stg, &sb))
+            return fail(FX_ERR_UNSUPPORTED,
+                        "fx_correlate: tensor-core X-stage needs <= 128 stations (<= 100 for split FP16)");
         e = fxi::launch_xcorr_tc(*h, d_corr, vis, s);
+    }
     return after_launch(e, "fx_correlate");
 }

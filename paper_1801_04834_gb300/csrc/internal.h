@@ -26,6 +26,9 @@ struct Handle {
     int *d_status = nullptr;           // device-side error word
     int2 *d_xf32_tiles = nullptr;      // tile list of the FP32 correlator
     int xf32_ntiles = 0;
+    int num_sms = 0;
+    long long tc_timeout_cycles = 0;   // budget of every bounded device-side wait
+    int tc_test_no_tma = 0;            // failure-detection test hook (FX_FLAG_TEST_NO_LOADS)
 };
 
 // ppf.cu
@@ -43,6 +46,7 @@ int xf32_build_tiles(int N, int2 *host_tiles /* may be null: count only */);
 cudaError_t launch_xcorr_f32(const Handle &h, const float2 *corr, float2 *vis, cudaStream_t st);
 
 // xcorr_tc.cu
+bool xtc_plan(const Handle &h, int *rload, int *stages, unsigned *stage_bytes);
 cudaError_t launch_xcorr_tc(const Handle &h, const void *corr, float2 *vis, cudaStream_t st);
 
 }  // namespace fxi
