@@ -83,6 +83,22 @@ def fp32_alu_peak_tflops(mhz=SM_MAX_MHZ):
     return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu record, or None when the
+    kernel's source changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        if sha != rec["sha256"] or rec["workload"] != workload:
+            return None
+        return float(rec["bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -333,14 +349,16 @@ def run_fx(args, w):
         x_ach = xflops / (ms_x * 1e-3) / 1e12
         roof = {"kernel": "xcorr_f32_kernel", "bound": "alu", "achieved": x_ach,
                 "peak": fp32_alu_peak_tflops(), "unit": "TFLOP/s",
-                "frac": x_ach / fp32_alu_peak_tflops(), "traffic": None,
+                "frac": x_ach / fp32_alu_peak_tflops(),
+                "traffic": recorded_traffic("xcorr_f32_kernel", args.workload),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "algorithmic": f"{xflops:.4e} useful flop per launch (8 per complex MAC)"}
     else:
         x_bytes = sz.corr_bytes + sz.vis_bytes
         x_ach = x_bytes / (ms_x * 1e-3) / 1e9
         roof = {"kernel": "xcorr_tc_kernel", "bound": "hbm", "achieved": x_ach, "peak": hbm,
-                "unit": "GB/s", "frac": x_ach / hbm, "traffic": None,
+                "unit": "GB/s", "frac": x_ach / hbm,
+                "traffic": recorded_traffic("xcorr_tc_kernel", args.workload),
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
                 "algorithmic": f"{x_bytes:.4e} B per launch (operands + visibilities)"}
     f_bytes = sz.raw_bytes + sz.chan_bytes
