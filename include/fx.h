@@ -163,6 +163,39 @@ fx_status fx_correlate(fx_handle *h, const void *d_corr, float *d_vis, fx_stream
  * The status word is cleared by the call. Not capturable in a CUDA graph. */
 fx_status fx_poll_status(fx_handle *h, int *code);
 
+/* The same correction as fx_correct with FP32 output, for callers that must
+ * not allocate device memory: no handle (fx_create allocates) and no
+ * cudaMalloc, cudaFree or allocating library call anywhere on this path. This
+ * serves code that owns a fixed device-memory budget handed out at start-up,
+ * hosts that forbid their plugins to touch the CUDA allocator, and real-time
+ * threads that cannot risk the device-wide synchronisation an allocation may
+ * cause. The paper has no counterpart; it is a packaging variant of the
+ * delay/bandpass step.
+ *
+ * The per-call FP64 phase table lives in a fixed device array built into the
+ * library, FX_NOALLOC_MAX_PHASES entries (8 MiB, held by every GPU that loads
+ * the library until the process exits); a request with
+ * n_subbands * n_stations * n_channels above that limit is rejected with
+ * FX_ERR_INVALID before anything is launched. The first call on each device
+ * looks up that array's device address (with that device current) and caches
+ * it, so make the first call on a device before any stream capture. Every call
+ * reuses the same array and overwrites all of the entries it reads, so no
+ * state carries over between calls; calls whose work overlaps on the GPU
+ * (different streams, or different host threads without ordering) race on
+ * the array and must be serialised by the caller.
+ *
+ * Arguments as for fx_correct with an FX_F32 handle: d_subband_centre_hz [SB]
+ * double (device), d_delay_begin/d_delay_end [N] double seconds (device),
+ * d_bandpass [N][C] float or NULL, d_gains [N][P] complex float or NULL,
+ * d_chan the chan layout, d_corr the FP32 corr layout [SB][C][S][I]. Pols = 2,
+ * channels in {16, 64, 256}. */
+#define FX_NOALLOC_MAX_PHASES (1u << 20)
+fx_status fx_correct_f32_noalloc(int n_stations, int n_subbands, int n_channels, int n_spectra,
+                                 double sample_rate_hz, const double *d_subband_centre_hz,
+                                 const double *d_delay_begin, const double *d_delay_end,
+                                 const float *d_bandpass, const float *d_gains, const float *d_chan,
+                                 float *d_corr, fx_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -53,7 +53,9 @@ SIGNATURES = {
     "fx_correct": (I, [P, P, P, P, P, P, P, P]),
     "fx_correlate": (I, [P, P, P, P]),
     "fx_poll_status": (I, [P, ctypes.POINTER(ctypes.c_int)]),
+    "fx_correct_f32_noalloc": (I, [I, I, I, I, D, P, P, P, P, P, P, P, P]),
 }
+FX_NOALLOC_MAX_PHASES = 1 << 20
 FX_FLAG_TEST_NO_LOADS = 0x80000000
 
 _lib = None

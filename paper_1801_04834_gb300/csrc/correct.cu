@@ -20,6 +20,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace fxi {
@@ -170,6 +172,12 @@ correct_planar_kernel(const float2 *__restrict__ chan, const float2 *__restrict_
     }
 }
 
+// Scratch of the no-allocation correction entry point (fx_correct_f32_noalloc):
+// the phase table lives in this fixed-size device array instead of memory
+// allocated by fx_create. Every GPU that loads the library holds these 8 MiB
+// until the process exits.
+static __device__ __align__(256) float2 g_noalloc_phase[FX_NOALLOC_MAX_PHASES];
+
 }  // namespace
 
 cudaError_t launch_phase_table(const Handle &h, const double *tau_b, const double *tau_e,
@@ -183,6 +191,49 @@ cudaError_t launch_phase_table(const Handle &h, const double *tau_b, const doubl
                                                              h.p.n_subbands, h.p.n_stations,
                                                              h.p.n_channels, h.p.n_spectra,
                                                              h.p.sample_rate_hz);
+    return cudaGetLastError();
+}
+
+// Device address of g_noalloc_phase on the current device. In host code the
+// array's name is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress once per device (the first call on that device does
+// it) and cached.
+static cudaError_t noalloc_phase_ptr(float2 **out)
+{
+    static std::mutex mu;
+    static float2 *ptrs[kMaxDevices] = {};
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptrs[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_phase);
+        if (e != cudaSuccess) return e;
+        ptrs[dev] = static_cast<float2 *>(p);
+    }
+    *out = ptrs[dev];
+    return cudaSuccess;
+}
+
+cudaError_t launch_correct_f32_noalloc(int N, int SB, int C, int S, double fs, const double *centres,
+                                       const double *tau_b, const double *tau_e, const float *bandpass,
+                                       const float2 *gains, const float2 *chan, float2 *corr, cudaStream_t st)
+{
+    float2 *table = nullptr;
+    cudaError_t e = noalloc_phase_ptr(&table);
+    if (e != cudaSuccess) return e;
+    const long long n = (long long)SB * N * C;
+    phase_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(centres, tau_b, tau_e, table, SB, N, C, S,
+                                                                    fs);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(float2) * kCB * (2 * N + 1);
+    e = cudaFuncSetAttribute(correct_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(S, (C + kCB - 1) / kCB, SB);
+    correct_f32_kernel<<<grid, kNT, smem, st>>>(chan, table, bandpass, gains, corr, N, C, S);
     return cudaGetLastError();
 }
 

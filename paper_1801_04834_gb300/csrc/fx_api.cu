@@ -258,3 +258,39 @@ extern "C" fx_status fx_correlate(fx_handle *h, const void *d_corr, float *d_vis
     }
     return after_launch(e, "fx_correlate");
 }
+
+// Handle-free correction for callers that cannot allocate device memory; the
+// phase table lives in a fixed device array in correct.cu (see fx.h).
+extern "C" fx_status fx_correct_f32_noalloc(int n_stations, int n_subbands, int n_channels, int n_spectra,
+                                            double sample_rate_hz, const double *d_subband_centre_hz,
+                                            const double *d_delay_begin, const double *d_delay_end,
+                                            const float *d_bandpass, const float *d_gains, const float *d_chan,
+                                            float *d_corr, fx_stream stream)
+{
+    const char *who = "fx_correct_f32_noalloc";
+    if (n_stations < 1 || n_subbands < 1 || n_spectra < 1)
+        return fail(FX_ERR_INVALID, "%s: sizes must be >= 1", who);
+    if (n_channels != 16 && n_channels != 64 && n_channels != 256)
+        return fail(FX_ERR_UNSUPPORTED, "%s: channels must be 16, 64 or 256 (got %d)", who, n_channels);
+    if (!(sample_rate_hz > 0)) return fail(FX_ERR_INVALID, "%s: sample_rate_hz must be > 0", who);
+    const long long entries = (long long)n_subbands * n_stations * n_channels;
+    if (entries > (long long)FX_NOALLOC_MAX_PHASES)
+        return fail(FX_ERR_INVALID,
+                    "%s: subbands x stations x channels = %lld exceeds the built-in phase table of %u entries",
+                    who, entries, FX_NOALLOC_MAX_PHASES);
+    if (n_subbands > 65535 || n_spectra > (1 << 24) || n_stations > 4096)
+        return fail(FX_ERR_INVALID, "%s: sizes out of range", who);
+    if ((size_t)sizeof(float2) * 32 * (2 * n_stations + 1) > 227 * 1024)
+        return fail(FX_ERR_UNSUPPORTED, "%s: too many stations", who);
+    if (!d_subband_centre_hz || !d_delay_begin || !d_delay_end || !d_chan || !d_corr)
+        return fail(FX_ERR_INVALID, "%s: NULL buffer", who);
+    if (((uintptr_t)d_chan & 15) || ((uintptr_t)d_corr & 15) || ((uintptr_t)d_gains & 7) ||
+        ((uintptr_t)d_bandpass & 3) || ((uintptr_t)d_delay_begin & 7) || ((uintptr_t)d_delay_end & 7) ||
+        ((uintptr_t)d_subband_centre_hz & 7))
+        return fail(FX_ERR_INVALID, "%s: misaligned buffer", who);
+    cudaError_t e = fxi::launch_correct_f32_noalloc(
+        n_stations, n_subbands, n_channels, n_spectra, sample_rate_hz, d_subband_centre_hz, d_delay_begin,
+        d_delay_end, d_bandpass, reinterpret_cast<const float2 *>(d_gains), reinterpret_cast<const float2 *>(d_chan),
+        reinterpret_cast<float2 *>(d_corr), (cudaStream_t)stream);
+    return after_launch(e, who);
+}

@@ -40,6 +40,10 @@ cudaError_t launch_phase_table(const Handle &h, const double *tau_b, const doubl
                                cudaStream_t st);
 cudaError_t launch_correct(const Handle &h, const float2 *chan, const float *bandpass,
                            const float2 *gains, void *corr, cudaStream_t st);
+constexpr int kMaxDevices = 64;
+cudaError_t launch_correct_f32_noalloc(int N, int SB, int C, int S, double fs, const double *centres,
+                                       const double *tau_b, const double *tau_e, const float *bandpass,
+                                       const float2 *gains, const float2 *chan, float2 *corr, cudaStream_t st);
 
 // xcorr_f32.cu
 int xf32_build_tiles(int N, int2 *host_tiles /* may be null: count only */);
