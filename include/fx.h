@@ -154,6 +154,28 @@ fx_status fx_correct(fx_handle *h, const float *d_chan, const double *d_delay_be
  * tensor cores with FP32 accumulation (split: hi*hi' + hi*lo' + lo*hi'). */
 fx_status fx_correlate(fx_handle *h, const void *d_corr, float *d_vis, fx_stream stream);
 
+/* ---- differentiation form ------------------------------------------------
+ * With the delay held constant over the block (tau_begin = tau_end = tau) the
+ * corrected sample is Y_a = c_a X_a, c_a(k) = g_a exp(2 pi i f_k tau_n(a))
+ * (Sec. "Signal processing with GPU kernels": delay compensation is a
+ * per-channel phase rotation), so V_ab = c_a conj(c_b) R_ab, where R ("raw
+ * visibilities") is what fx_correct with NULL gains and zero delays followed
+ * by fx_correlate produces (bandpass included). Both calls below read R in
+ * the vis layout; d_gains is [N][P] complex float (NULL = ones), d_delays is
+ * [N] double seconds. They need a handle with n_stations <= 512. */
+
+/* Forward from raw visibilities: d_vis = c_a conj(c_b) R for every entry. */
+fx_status fx_apply_gains(fx_handle *h, const float *d_raw_vis, const float *d_gains,
+                         const double *d_delays, float *d_vis, fx_stream stream);
+
+/* Adjoint of correct + correlate: given d_grad_vis = (dL/dRe V, dL/dIm V) per
+ * entry (vis layout) of a real loss L, writes d_grad_gains [N][P] complex
+ * float = (dL/dRe g, dL/dIm g) and d_grad_delays [N] double = dL/dtau. Either
+ * output may be NULL. Deterministic (fixed-order reductions, FP64 sums). */
+fx_status fx_correct_correlate_backward(fx_handle *h, const float *d_raw_vis, const float *d_gains,
+                                        const double *d_delays, const float *d_grad_vis,
+                                        float *d_grad_gains, double *d_grad_delays, fx_stream stream);
+
 /* Synchronises the device, then reports asynchronous failures of earlier
  * calls: FX_ERR_CUDA for a CUDA error, FX_ERR_TIMEOUT if a bounded device-side
  * wait of the tensor-core X-stage gave up (each wait has a budget of about two

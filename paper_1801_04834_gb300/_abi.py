@@ -53,6 +53,8 @@ SIGNATURES = {
     "fx_correct": (I, [P, P, P, P, P, P, P, P]),
     "fx_correlate": (I, [P, P, P, P]),
     "fx_poll_status": (I, [P, ctypes.POINTER(ctypes.c_int)]),
+    "fx_apply_gains": (I, [P, P, P, P, P, P]),
+    "fx_correct_correlate_backward": (I, [P, P, P, P, P, P, P, P]),
     "fx_correct_f32_noalloc": (I, [I, I, I, I, D, P, P, P, P, P, P, P, P]),
 }
 FX_NOALLOC_MAX_PHASES = 1 << 20

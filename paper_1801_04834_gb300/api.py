@@ -131,6 +131,41 @@ class Correlator:
                                     _stream_ptr(stream)), "fx_correlate")
         return out
 
+    # -- differentiation form -------------------------------------------------
+    def raw_vis(self, chan, bandpass=None, stream=None):
+        """R: correlation of the bandpass-corrected data with unit gains and zero
+        delays (fx_correct + fx_correlate); input of fx_apply_gains and of the
+        adjoint."""
+        zero = torch.zeros(self.N, dtype=torch.float64, device=self.device)
+        return self.correlate(self.correct(chan, zero, zero, bandpass=bandpass, stream=stream), stream=stream)
+
+    def apply_gains(self, raw_vis, gains, delays, out=None, stream=None):
+        if out is None:
+            out = torch.empty(self.vis_shape(), dtype=torch.float32, device=self.device)
+        vb = self.sizes.vis_bytes
+        check(self.lib.fx_apply_gains(self.handle, self._dev(raw_vis, "raw_vis", torch.float32, vb),
+                                      self._opt(gains, "gains", torch.float32, 16 * self.N),
+                                      self._dev(delays, "delays", torch.float64, 8 * self.N),
+                                      self._dev(out, "vis", torch.float32, vb), _stream_ptr(stream)),
+              "fx_apply_gains")
+        return out
+
+    def backward(self, raw_vis, gains, delays, grad_vis, stream=None):
+        """(dL/d gains [N][2][2] float32, dL/d delays [N] float64) from
+        grad_vis = (dL/dRe V, dL/dIm V) in the vis layout."""
+        gg = torch.empty((self.N, 2, 2), dtype=torch.float32, device=self.device)
+        gt = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        vb = self.sizes.vis_bytes
+        check(self.lib.fx_correct_correlate_backward(
+            self.handle, self._dev(raw_vis, "raw_vis", torch.float32, vb),
+            self._opt(gains, "gains", torch.float32, 16 * self.N),
+            self._dev(delays, "delays", torch.float64, 8 * self.N),
+            self._dev(grad_vis, "grad_vis", torch.float32, vb),
+            self._dev(gg, "grad_gains", torch.float32, 16 * self.N),
+            self._dev(gt, "grad_delays", torch.float64, 8 * self.N), _stream_ptr(stream)),
+            "fx_correct_correlate_backward")
+        return gg, gt
+
     def close(self):
         if getattr(self, "handle", None):
             self.lib.fx_destroy(self.handle)

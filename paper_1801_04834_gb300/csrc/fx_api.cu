@@ -121,6 +121,7 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
     FX_TRY(cudaMalloc(&h->d_phase, sizeof(float2) * SB * N * C));
     FX_TRY(cudaMalloc(&h->d_status, sizeof(int) * 4));
     FX_TRY(cudaMalloc(&h->d_xf32_tiles, sizeof(int2) * ntiles));
+    FX_TRY(cudaMalloc(&h->d_adj_partial, sizeof(double) * 3 * (size_t)fxi::adjoint_blocks(*h) * h->I));
     FX_TRY(cudaMemcpy(h->d_taps, p.h_taps, sizeof(float) * T * C, cudaMemcpyHostToDevice));
     FX_TRY(cudaMemcpy(h->d_twiddle, tw.data(), sizeof(float2) * C, cudaMemcpyHostToDevice));
     FX_TRY(cudaMemcpy(h->d_centres, p.h_subband_centre_hz, sizeof(double) * SB,
@@ -143,6 +144,7 @@ extern "C" void fx_destroy(fx_handle *h)
     cudaFree(h->d_phase);
     cudaFree(h->d_status);
     cudaFree(h->d_xf32_tiles);
+    cudaFree(h->d_adj_partial);
     delete h;
 }
 
@@ -257,6 +259,40 @@ extern "C" fx_status fx_correlate(fx_handle *h, const void *d_corr, float *d_vis
         e = fxi::launch_xcorr_tc(*h, d_corr, vis, s);
     }
     return after_launch(e, "fx_correlate");
+}
+
+extern "C" fx_status fx_apply_gains(fx_handle *h, const float *d_raw_vis, const float *d_gains,
+                                    const double *d_delays, float *d_vis, fx_stream stream)
+{
+    fx_status st = check_handle(h, "fx_apply_gains");
+    if (st) return st;
+    if (!d_raw_vis || !d_delays || !d_vis) return fail(FX_ERR_INVALID, "fx_apply_gains: NULL buffer");
+    if (((uintptr_t)d_raw_vis & 7) || ((uintptr_t)d_vis & 7) || ((uintptr_t)d_gains & 7) || ((uintptr_t)d_delays & 7))
+        return fail(FX_ERR_INVALID, "fx_apply_gains: misaligned buffer");
+    return after_launch(fxi::launch_apply_gains(*h, reinterpret_cast<const float2 *>(d_raw_vis),
+                                                reinterpret_cast<const float2 *>(d_gains), d_delays,
+                                                reinterpret_cast<float2 *>(d_vis), (cudaStream_t)stream),
+                        "fx_apply_gains");
+}
+
+extern "C" fx_status fx_correct_correlate_backward(fx_handle *h, const float *d_raw_vis, const float *d_gains,
+                                                   const double *d_delays, const float *d_grad_vis,
+                                                   float *d_grad_gains, double *d_grad_delays, fx_stream stream)
+{
+    const char *who = "fx_correct_correlate_backward";
+    fx_status st = check_handle(h, who);
+    if (st) return st;
+    if (!d_raw_vis || !d_delays || !d_grad_vis) return fail(FX_ERR_INVALID, "%s: NULL buffer", who);
+    if (h->I > 1024) return fail(FX_ERR_UNSUPPORTED, "%s: at most 512 stations", who);
+    if (((uintptr_t)d_raw_vis & 7) || ((uintptr_t)d_grad_vis & 7) || ((uintptr_t)d_gains & 7) ||
+        ((uintptr_t)d_delays & 7) || ((uintptr_t)d_grad_gains & 7) || ((uintptr_t)d_grad_delays & 7))
+        return fail(FX_ERR_INVALID, "%s: misaligned buffer", who);
+    return after_launch(fxi::launch_adjoint(*h, reinterpret_cast<const float2 *>(d_raw_vis),
+                                            reinterpret_cast<const float2 *>(d_grad_vis),
+                                            reinterpret_cast<const float2 *>(d_gains), d_delays,
+                                            reinterpret_cast<float2 *>(d_grad_gains), d_grad_delays,
+                                            (cudaStream_t)stream),
+                        who);
 }
 
 // Handle-free correction for callers that cannot allocate device memory; the

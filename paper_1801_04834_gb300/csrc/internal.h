@@ -26,6 +26,7 @@ struct Handle {
     int *d_status = nullptr;           // device-side error word
     int2 *d_xf32_tiles = nullptr;      // tile list of the FP32 correlator
     int xf32_ntiles = 0;
+    double *d_adj_partial = nullptr;   // [adjoint CTAs][I][3] per-CTA gradient sums
     int num_sms = 0;
     long long tc_timeout_cycles = 0;   // budget of every bounded device-side wait
     int tc_test_no_tma = 0;            // failure-detection test hook (FX_FLAG_TEST_NO_LOADS)
@@ -48,6 +49,13 @@ cudaError_t launch_correct_f32_noalloc(int N, int SB, int C, int S, double fs, c
 // xcorr_f32.cu
 int xf32_build_tiles(int N, int2 *host_tiles /* may be null: count only */);
 cudaError_t launch_xcorr_f32(const Handle &h, const float2 *corr, float2 *vis, cudaStream_t st);
+
+// adjoint.cu
+int adjoint_blocks(const Handle &h);
+cudaError_t launch_apply_gains(const Handle &h, const float2 *R, const float2 *gains, const double *tau,
+                               float2 *V, cudaStream_t st);
+cudaError_t launch_adjoint(const Handle &h, const float2 *R, const float2 *G, const float2 *gains,
+                           const double *tau, float2 *grad_gains, double *grad_tau, cudaStream_t st);
 
 // xcorr_tc.cu
 bool xtc_plan(const Handle &h, int *rload, int *stages, unsigned *stage_bytes);
