@@ -176,6 +176,55 @@ fx_status fx_correct_correlate_backward(fx_handle *h, const float *d_raw_vis, co
                                         const double *d_delays, const float *d_grad_vis,
                                         float *d_grad_gains, double *d_grad_delays, fx_stream stream);
 
+/* ---- batching form ----------------------------------------------------------
+ * Many uneven correlation jobs (each its own station count, subbands,
+ * channels and spectra) in one persistent tensor-core launch. The paper maps
+ * subbands statically to GPUs and compiles kernels per observation
+ * (Sec. "Workload distribution"); here one launch walks a cost-sorted list of
+ * (job, channel, tile) items so small and large jobs share the GPU, and the
+ * tile plan (tile width, pipeline depth, item order) comes from an autotuner
+ * that times the candidates on the batch itself. */
+typedef struct {
+    int n_stations;              /* N of this job (P = 2) */
+    int n_subbands;              /* SB */
+    int n_channels;              /* C (any, the X-stage does not care) */
+    int n_spectra;               /* S */
+    const void *d_corr;          /* planar corr layout of this job in the batch's
+                                    precision: [SB][C][planes][I_pad][S_pad],
+                                    I_pad = 2N rounded up to 16, S_pad = S rounded
+                                    up to 64, 128-byte aligned, padding zero */
+    float *d_vis;                /* vis layout [SB][C][N(N+1)/2][4] complex float */
+} fx_job;
+
+typedef struct fx_batch fx_batch;
+
+/* Builds a plan for 1..64 jobs: tensor maps over each job's operands, the
+ * device list of work items, a status word. precision is FX_F16, FX_BF16 or
+ * FX_F16_SPLIT; operand_scale as in fx_params (0 = 1). Uses a tile plan tuned
+ * earlier for the same job shapes in this process, else a default.
+ * Allocates device memory (the item list); synchronises. */
+fx_status fx_batch_create(const fx_job *jobs, int n_jobs, int precision, float operand_scale,
+                          fx_batch **out);
+
+/* Times each candidate tile plan (wide tiles / 128- / 64-column tiles,
+ * longest-first / job-major order) with `reps` launches on `stream`, keeps the
+ * fastest and remembers it for this set of job shapes. Writes every job's
+ * visibilities while doing so. Synchronises; not capturable. */
+fx_status fx_batch_autotune(fx_batch *b, int reps, fx_stream stream);
+
+/* One persistent launch correlating every job of the plan; no host work
+ * besides the launch, so it can be captured in a CUDA graph. */
+fx_status fx_correlate_batched(fx_batch *b, fx_stream stream);
+
+/* The plan in use, as text (tile mode, column tile, stages, accumulator
+ * buffers, item order, item count). */
+const char *fx_batch_describe(const fx_batch *b);
+
+/* As fx_poll_status, for a batch plan's launches. */
+fx_status fx_batch_poll_status(fx_batch *b, int *code);
+
+void fx_batch_destroy(fx_batch *b);
+
 /* Synchronises the device, then reports asynchronous failures of earlier
  * calls: FX_ERR_CUDA for a CUDA error, FX_ERR_TIMEOUT if a bounded device-side
  * wait of the tensor-core X-stage gave up (each wait has a budget of about two

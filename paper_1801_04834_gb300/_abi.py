@@ -54,6 +54,12 @@ SIGNATURES = {
     "fx_correlate": (I, [P, P, P, P]),
     "fx_poll_status": (I, [P, ctypes.POINTER(ctypes.c_int)]),
     "fx_apply_gains": (I, [P, P, P, P, P, P]),
+    "fx_batch_create": (I, [P, I, I, ctypes.c_float, ctypes.POINTER(P)]),
+    "fx_batch_autotune": (I, [P, I, P]),
+    "fx_correlate_batched": (I, [P, P]),
+    "fx_batch_describe": (ctypes.c_char_p, [P]),
+    "fx_batch_poll_status": (I, [P, ctypes.POINTER(ctypes.c_int)]),
+    "fx_batch_destroy": (None, [P]),
     "fx_correct_correlate_backward": (I, [P, P, P, P, P, P, P, P]),
     "fx_correct_f32_noalloc": (I, [I, I, I, I, D, P, P, P, P, P, P, P, P]),
 }
@@ -88,3 +94,9 @@ def last_error() -> str:
 def check(status: int, where: str):
     if status != FX_OK:
         raise FxError(status, where, last_error())
+
+
+class fx_job(ctypes.Structure):
+    _fields_ = [("n_stations", ctypes.c_int), ("n_subbands", ctypes.c_int),
+                ("n_channels", ctypes.c_int), ("n_spectra", ctypes.c_int),
+                ("d_corr", ctypes.c_void_p), ("d_vis", ctypes.c_void_p)]

@@ -295,6 +295,83 @@ extern "C" fx_status fx_correct_correlate_backward(fx_handle *h, const float *d_
                         who);
 }
 
+extern "C" fx_status fx_batch_create(const fx_job *jobs, int n_jobs, int precision, float operand_scale,
+                                     fx_batch **out)
+{
+    const char *who = "fx_batch_create";
+    if (!out) return fail(FX_ERR_INVALID, "%s: out is NULL", who);
+    *out = nullptr;
+    if (!jobs || n_jobs < 1 || n_jobs > 64) return fail(FX_ERR_INVALID, "%s: need 1..64 jobs", who);
+    if (precision != FX_F16 && precision != FX_BF16 && precision != FX_F16_SPLIT)
+        return fail(FX_ERR_INVALID, "%s: precision must be FX_F16, FX_BF16 or FX_F16_SPLIT", who);
+    const float scale = operand_scale == 0.f ? 1.f : operand_scale;
+    if (!is_pow2(scale)) return fail(FX_ERR_INVALID, "%s: operand_scale must be a power of two", who);
+    for (int j = 0; j < n_jobs; ++j) {
+        const fx_job &J = jobs[j];
+        if (J.n_stations < 1 || J.n_stations > 4096 || J.n_subbands < 1 || J.n_channels < 1 || J.n_spectra < 1 ||
+            J.n_spectra > (1 << 24))
+            return fail(FX_ERR_INVALID, "%s: job %d has bad sizes", who, j);
+        if (!J.d_corr || !J.d_vis) return fail(FX_ERR_INVALID, "%s: job %d has a NULL buffer", who, j);
+        if (((uintptr_t)J.d_corr & 127) || ((uintptr_t)J.d_vis & 15))
+            return fail(FX_ERR_INVALID, "%s: job %d: corr must be 128-byte, vis 16-byte aligned", who, j);
+    }
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const char *why = "";
+    cudaError_t e = fxi_batch_create(jobs, n_jobs, precision, scale, sms, out, &why);
+    if (e == cudaErrorMemoryAllocation) return fail(FX_ERR_NOMEM, "%s: %s", who, why);
+    if (e == cudaErrorNotSupported) return fail(FX_ERR_UNSUPPORTED, "%s: %s", who, why);
+    if (e != cudaSuccess) return fail(FX_ERR_INVALID, "%s: %s (%s)", who, why, cudaGetErrorString(e));
+    return FX_OK;
+}
+
+static fx_status check_batch(const fx_batch *b, const char *who)
+{
+    if (!b) return fail(FX_ERR_INVALID, "%s: batch is NULL", who);
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != fxi_batch_device(b)) return fail(FX_ERR_INVALID, "%s: wrong current device", who);
+    return FX_OK;
+}
+
+extern "C" fx_status fx_batch_autotune(fx_batch *b, int reps, fx_stream stream)
+{
+    fx_status st = check_batch(b, "fx_batch_autotune");
+    if (st) return st;
+    if (reps < 1) reps = 1;
+    return after_launch(fxi_batch_autotune(b, reps, (cudaStream_t)stream), "fx_batch_autotune");
+}
+
+extern "C" fx_status fx_correlate_batched(fx_batch *b, fx_stream stream)
+{
+    fx_status st = check_batch(b, "fx_correlate_batched");
+    if (st) return st;
+    return after_launch(fxi_batch_launch(b, (cudaStream_t)stream), "fx_correlate_batched");
+}
+
+extern "C" const char *fx_batch_describe(const fx_batch *b) { return b ? fxi_batch_describe(b) : ""; }
+
+extern "C" fx_status fx_batch_poll_status(fx_batch *b, int *code)
+{
+    fx_status st = check_batch(b, "fx_batch_poll_status");
+    if (st) return st;
+    if (code) *code = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "fx_batch_poll_status: asynchronous error");
+    int w[2] = {0, 0};
+    e = cudaMemcpy(w, fxi_batch_status(b), sizeof(w), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "fx_batch_poll_status");
+    if (w[0] != 0) {
+        cudaMemset(fxi_batch_status(b), 0, sizeof(int) * 4);
+        if (code) *code = w[0];
+        return fail(FX_ERR_TIMEOUT, "device-side wait gave up (role %d, CTA %d)", w[0], w[1]);
+    }
+    return FX_OK;
+}
+
+extern "C" void fx_batch_destroy(fx_batch *b) { fxi_batch_destroy(b); }
+
 // Handle-free correction for callers that cannot allocate device memory; the
 // phase table lives in a fixed device array in correct.cu (see fx.h).
 extern "C" fx_status fx_correct_f32_noalloc(int n_stations, int n_subbands, int n_channels, int n_spectra,

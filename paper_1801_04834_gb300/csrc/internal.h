@@ -62,3 +62,13 @@ bool xtc_plan(const Handle &h, int *rload, int *stages, unsigned *stage_bytes);
 cudaError_t launch_xcorr_tc(const Handle &h, const void *corr, float2 *vis, cudaStream_t st);
 
 }  // namespace fxi
+
+// batched tensor-core X-stage (xcorr_tc.cu)
+cudaError_t fxi_batch_create(const fx_job *jobs, int n_jobs, int precision, float scale, int num_sms,
+                             fx_batch **out, const char **why);
+cudaError_t fxi_batch_launch(fx_batch *b, cudaStream_t st);
+cudaError_t fxi_batch_autotune(fx_batch *b, int reps, cudaStream_t st);
+void fxi_batch_destroy(fx_batch *b);
+const char *fxi_batch_describe(const fx_batch *b);
+int *fxi_batch_status(fx_batch *b);
+int fxi_batch_device(const fx_batch *b);
