@@ -306,19 +306,19 @@ def run_fx(args, w):
     vis = torch.empty(c.vis_shape(), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    # one step = fx_channelize_correct (phase table + fused F-stage/correction)
+    # + fx_correlate: 3 kernel launches
     def step(ev=None):
         if ev: ev[0].record(stream)
-        c.channelize(raw, chan)
+        c.channelize_correct(raw, delays, delays, bandpass=bandpass, out=corr)
         if ev: ev[1].record(stream)
-        c.correct(chan, delays, delays, bandpass=bandpass, out=corr)
-        if ev: ev[2].record(stream)
         c.correlate(corr, vis)
-        if ev: ev[3].record(stream)
+        if ev: ev[2].record(stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     vis_ids = os.environ.get("CUDA_VISIBLE_DEVICES")
     sampler = ClockSampler(vis_ids.split(",")[local] if vis_ids else str(local))
     sampler.start()
@@ -334,9 +334,26 @@ def run_fx(args, w):
     barrier(ws)
     clocks = sampler.stop()
     total_ms = start.elapsed_time(stop)
-    ms_f = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
-    ms_c = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
-    ms_x = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+    ms_fc = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    ms_x = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+
+    # the same step through the three separate calls (paper's kernel split)
+    def step3(ev):
+        ev[0].record(stream)
+        c.channelize(raw, chan)
+        ev[1].record(stream)
+        c.correct(chan, delays, delays, bandpass=bandpass, out=corr)
+        ev[2].record(stream)
+        c.correlate(corr, vis)
+        ev[3].record(stream)
+
+    ev3 = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps + 1)]
+    for e in ev3:
+        step3(e)
+    torch.cuda.synchronize()
+    ms_f = statistics.mean(e[0].elapsed_time(e[1]) for e in ev3[1:])
+    ms_c = statistics.mean(e[1].elapsed_time(e[2]) for e in ev3[1:])
+    ms_3 = statistics.mean(e[0].elapsed_time(e[3]) for e in ev3[1:])
     max_ms = max_over_ranks(total_ms, ws, dev)
     ms_step = max_ms / args.steps
     value = aggregate_value(sky_seconds(w) * args.steps, ws, max_ms / 1e3)
@@ -363,12 +380,17 @@ def run_fx(args, w):
                 "algorithmic": f"{x_bytes:.4e} B per launch (operands + visibilities)"}
     f_bytes = sz.raw_bytes + sz.chan_bytes
     c_bytes = sz.chan_bytes + sz.corr_bytes
+    fc_bytes = sz.raw_bytes + sz.corr_bytes
     kernels = {
-        "channelize_ms": ms_f, "channelize_GBps": f_bytes / (ms_f * 1e-3) / 1e9,
-        "channelize_hbm_frac": f_bytes / (ms_f * 1e-3) / 1e9 / hbm,
-        "correct_ms": ms_c, "correct_GBps": c_bytes / (ms_c * 1e-3) / 1e9,
-        "correct_hbm_frac": c_bytes / (ms_c * 1e-3) / 1e9 / hbm,
+        "channelize_correct_ms": ms_fc, "channelize_correct_GBps": fc_bytes / (ms_fc * 1e-3) / 1e9,
+        "channelize_correct_hbm_frac": fc_bytes / (ms_fc * 1e-3) / 1e9 / hbm,
         "correlate_ms": ms_x, "correlate_useful_TFLOPs": xflops / (ms_x * 1e-3) / 1e12,
+        "three_call_path": {
+            "step_ms": ms_3, "rtf": sky_seconds(w) / (ms_3 * 1e-3),
+            "channelize_ms": ms_f, "channelize_GBps": f_bytes / (ms_f * 1e-3) / 1e9,
+            "channelize_hbm_frac": f_bytes / (ms_f * 1e-3) / 1e9 / hbm,
+            "correct_ms": ms_c, "correct_GBps": c_bytes / (ms_c * 1e-3) / 1e9,
+            "correct_hbm_frac": c_bytes / (ms_c * 1e-3) / 1e9 / hbm},
     }
 
     # ---- end to end: pinned host raw in, visibilities out, copies timed ----
@@ -433,6 +455,20 @@ def run_fx(args, w):
             except Exception as ex:  # report, do not hide
                 variants[name] = {"error": str(ex)[:200]}
 
+    del raw, chan
+    extras = {}
+    if not args.no_extras:
+        torch.cuda.empty_cache()
+        try:
+            extras["batching"] = measure_batching(args, dev)
+        except Exception as ex:
+            extras["batching"] = {"error": str(ex)[:300]}
+        torch.cuda.empty_cache()
+        try:
+            extras["differentiation"] = measure_adjoint(args, dev)
+        except Exception as ex:
+            extras["differentiation"] = {"error": str(ex)[:300]}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(w)
@@ -453,9 +489,10 @@ def run_fx(args, w):
         "samples_per_s": samples(w) * ws / (ms_step * 1e-3),
         "x_stage_useful_TFLOPs": xflops / (ms_x * 1e-3) / 1e12,
         "variants": variants,
+        **extras,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }
     if rank == 0:
@@ -465,6 +502,134 @@ def run_fx(args, w):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def _time(fn, reps, stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def measure_batching(args, dev):
+    """Batching workload: 48 uneven correlation jobs (stations U{24..96},
+    channels {16, 64, 256}, spectra U{256..3072}, int16 noise + one point
+    source, FP16 operands). One autotuned persistent launch, replayed from a
+    CUDA graph, against 48 fx_correlate launches (one per job)."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import paper_1801_04834_gb300 as fxg
+    import synth
+    from paper_1801_04834_gb300 import _abi
+    lib = _abi.load()
+    rng = np.random.default_rng(synth.BASE_SEED + 3)
+    n_jobs = 48
+    Ns, Cs, Ss = rng.integers(24, 97, n_jobs), rng.choice([16, 64, 256], n_jobs), rng.integers(256, 3073, n_jobs)
+    jobs, flops, op_bytes, vis_bytes = [], 0.0, 0, 0
+    for k in range(n_jobs):
+        N, C, S = int(Ns[k]), int(Cs[k]), int(Ss[k])
+        jr = np.random.default_rng(synth.BASE_SEED + 3000 + k)
+        tau = jr.uniform(-5e-6, 5e-6, N)
+        tone = synth.Tone(amp=50.0, channel=int(jr.integers(1, C)), delays=tau)
+        c = fxg.Correlator(N, 1, C, S, taps=synth.kaiser_sinc_taps(16, C),
+                           centres=synth.subband_centres(1, 120e6 + 0.2e6 * k), precision=1)
+        raw = synth.make_raw_torch(synth.BASE_SEED + 3000 + k, 0, 1, N, C, S, tones=[tone],
+                                   centre_hz=120e6 + 0.2e6 * k, device=dev)
+        d = torch.as_tensor(tau, device=dev)
+        corr = c.correct(c.channelize(raw), d, d)
+        del raw
+        jobs.append(dict(c=c, corr=corr, vis1=torch.empty(c.vis_shape(), dtype=torch.float32, device=dev),
+                         visb=torch.empty(c.vis_shape(), dtype=torch.float32, device=dev), N=N, C=C, S=S))
+        flops += 8.0 * (N * (N + 1) // 2) * 4 * C * S
+        op_bytes += c.sizes.corr_bytes
+        vis_bytes += c.sizes.vis_bytes
+    stream = torch.cuda.current_stream()
+
+    def singles():
+        for j in jobs:
+            j["c"].correlate(j["corr"], j["vis1"])
+
+    singles()
+    single_ms = _time(singles, args.steps, stream)
+    arr = (_abi.fx_job * n_jobs)()
+    for k, j in enumerate(jobs):
+        arr[k].n_stations, arr[k].n_subbands, arr[k].n_channels, arr[k].n_spectra = j["N"], 1, j["C"], j["S"]
+        arr[k].d_corr, arr[k].d_vis = j["corr"].data_ptr(), j["visb"].data_ptr()
+    b = ctypes.c_void_p()
+    _abi.check(lib.fx_batch_create(arr, n_jobs, 1, 0.0, ctypes.byref(b)), "fx_batch_create")
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    default_plan = lib.fx_batch_describe(b).decode()
+    default_ms = _time(lambda: lib.fx_correlate_batched(b, sp), args.steps, stream)
+    _abi.check(lib.fx_batch_autotune(b, 3, sp), "fx_batch_autotune")
+    plan = lib.fx_batch_describe(b).decode()
+    gs = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=gs):
+        _abi.check(lib.fx_correlate_batched(b, ctypes.c_void_p(gs.cuda_stream)), "capture")
+    g.replay()
+    torch.cuda.synchronize()
+    graph_ms = _time(g.replay, args.steps, stream)
+    diff = max(float((j["visb"] - j["vis1"]).abs().max() / j["vis1"].abs().max()) for j in jobs)
+    lib.fx_batch_destroy(b)
+    peaks, _ = measured_peaks()
+    by = op_bytes + vis_bytes
+    return {"jobs": n_jobs, "single_launches_ms": single_ms, "batched_default_ms": default_ms,
+            "batched_graph_ms": graph_ms, "speedup_vs_single_launches": single_ms / graph_ms,
+            "useful_TFLOPs": flops / (graph_ms * 1e-3) / 1e12,
+            "hbm_GBps": by / (graph_ms * 1e-3) / 1e9, "hbm_frac": by / (graph_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+            "default_plan": default_plan, "autotuned_plan": plan,
+            "max_rel_diff_vs_single": diff, "operand_GB": op_bytes / 1e9}
+
+
+def measure_adjoint(args, dev):
+    """Differentiation workload: 76 stations x 2 pols, 32 subbands, 64
+    channels, 768 spectra, channelised FP32 (0.96 GB), gains |g| 0.8..1.2,
+    delays +-50 ns. Forward (hot path with gains), raw visibilities
+    (recomputed from the channelised block), adjoint, forward from R."""
+    import numpy as np
+    import torch
+
+    import paper_1801_04834_gb300 as fxg
+    import synth
+    N, SB, C, S = 76, 32, 64, 768
+    rng = np.random.default_rng(synth.BASE_SEED + 4)
+    c = fxg.Correlator(N, SB, C, S, taps=synth.kaiser_sinc_taps(16, C), centres=synth.subband_centres(SB))
+    chan = torch.empty(c.chan_shape(), dtype=torch.float32, device=dev)
+    chan.normal_(generator=torch.Generator(device=dev).manual_seed(synth.BASE_SEED + 4))
+    g = torch.as_tensor(synth.random_gains(rng, N), dtype=torch.float32, device=dev)
+    t = torch.as_tensor(rng.uniform(-50e-9, 50e-9, N), device=dev)
+    corr = torch.empty(c.corr_shape(), dtype=torch.float32, device=dev)
+    vis = torch.empty(c.vis_shape(), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def fwd():
+        c.correct(chan, t, t, gains=g, out=corr)
+        c.correlate(corr, vis)
+
+    fwd()
+    fwd_ms = _time(fwd, args.steps, stream)
+    R = c.raw_vis(chan)
+    raw_ms = _time(lambda: c.raw_vis(chan), args.steps, stream)
+    G = torch.randn_like(vis)
+    c.backward(R, g, t, G)
+    bwd_ms = _time(lambda: c.backward(R, g, t, G), args.steps, stream)
+    app_ms = _time(lambda: c.apply_gains(R, g, t, out=vis), args.steps, stream)
+    peaks, _ = measured_peaks()
+    vb = c.sizes.vis_bytes
+    c.close()
+    return {"workload": "76 stations x 2 pols, 32 subbands, 64 channels, 768 spectra, FP32",
+            "forward_ms": fwd_ms, "raw_vis_recompute_ms": raw_ms, "backward_ms": bwd_ms,
+            "apply_gains_ms": app_ms,
+            "backward_hbm_frac": 2 * vb / (bwd_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+            "train_step_ms_recompute": raw_ms + bwd_ms + fwd_ms}
 
 
 def main(argv=None):
@@ -477,6 +642,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batching and differentiation measurements")
     args = ap.parse_args(argv)
     w = WORKLOADS[args.workload]
     if args.impl == "reference":

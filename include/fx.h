@@ -146,6 +146,17 @@ fx_status fx_correct(fx_handle *h, const float *d_chan, const double *d_delay_be
                      const double *d_delay_end, const float *d_bandpass,
                      const float *d_gains, void *d_corr, fx_stream stream);
 
+/* fx_channelize followed by fx_correct in one pass, without the channelised
+ * intermediate: the same arithmetic per sample (FIR, FFT, then bandpass x gain
+ * x exp(i phi) with the FP64-formed phase) and the same corr output as the
+ * two calls, for the handle's precision. The per-sample sin/cos is evaluated
+ * with a fast intrinsic after an FP32 reduction to [-pi, pi] (absolute error
+ * ~4e-7), so results agree with the two-call path to FP32 rounding, not bit
+ * for bit. Arguments as for fx_channelize (d_raw) and fx_correct (the rest). */
+fx_status fx_channelize_correct(fx_handle *h, const void *d_raw, const double *d_delay_begin,
+                                const double *d_delay_end, const float *d_bandpass,
+                                const float *d_gains, void *d_corr, fx_stream stream);
+
 /* X-stage correlation (Sec. "Signal processing with GPU kernels": the last
  * kernel correlates all pairs of antenna fields and integrates ~1 s):
  *   vis[sb][k][b(i,j)][2p+q] = sum_{s<S} Y[i,p] conj(Y[j,q])  for i <= j.

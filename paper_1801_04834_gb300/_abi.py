@@ -52,6 +52,7 @@ SIGNATURES = {
     "fx_channelize": (I, [P, P, P, P]),
     "fx_correct": (I, [P, P, P, P, P, P, P, P]),
     "fx_correlate": (I, [P, P, P, P]),
+    "fx_channelize_correct": (I, [P, P, P, P, P, P, P, P]),
     "fx_poll_status": (I, [P, ctypes.POINTER(ctypes.c_int)]),
     "fx_apply_gains": (I, [P, P, P, P, P, P]),
     "fx_batch_create": (I, [P, I, I, ctypes.c_float, ctypes.POINTER(P)]),

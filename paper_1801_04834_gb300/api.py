@@ -122,6 +122,23 @@ class Correlator:
             _stream_ptr(stream)), "fx_correct")
         return out
 
+    def channelize_correct(self, raw, delay_begin, delay_end, bandpass=None, gains=None, out=None,
+                           stream=None):
+        """fx_channelize + fx_correct in one pass (no channelised intermediate)."""
+        rdt = torch.int16 if self.fmt == FX_CI16 else torch.int8
+        if out is None:
+            out = torch.empty(self.corr_shape(), dtype=self.corr_dtype(), device=self.device)
+        N, C = self.N, self.C
+        check(self.lib.fx_channelize_correct(
+            self.handle, self._dev(raw, "raw", rdt, self.sizes.raw_bytes),
+            self._dev(delay_begin, "delay_begin", torch.float64, 8 * N),
+            self._dev(delay_end, "delay_end", torch.float64, 8 * N),
+            self._opt(bandpass, "bandpass", torch.float32, 4 * N * C),
+            self._opt(gains, "gains", torch.float32, 16 * N),
+            self._dev(out, "corr", self.corr_dtype(), self.sizes.corr_bytes),
+            _stream_ptr(stream)), "fx_channelize_correct")
+        return out
+
     def correlate(self, corr, out=None, stream=None):
         if out is None:
             out = torch.empty(self.vis_shape(), dtype=torch.float32, device=self.device)

@@ -1,0 +1,379 @@
+// channelize_correct.cu -- the F-stage and the delay/bandpass correction in one
+// pass: raw int16/int8 samples in, corrected operands in the X-stage layout
+// out, with no channelised intermediate in HBM.
+//
+// Paper, Sec. "Signal processing with GPU kernels": FIR and FFT channelise
+// each subband, then fine delay compensation and bandpass correction end the
+// per-station processing and transpose on write-back so the correlator reads
+// all stations of a channel together. The paper runs these as separate
+// kernels through device memory; fusing them removes the write and re-read of
+// the channelised block (8 + 8 bytes per complex sample).
+//
+// The FIR and FFT are those of ppf.cu (register sliding-window FIR, two-pass
+// in-register FFT). After FFT pass 2 each output X(n, p, s, k) is multiplied
+// by bandpass(n, k) * gain(n, p) * exp(i phi), phi = phi0(n, k) + s * step(n, k)
+// (phi0 reduced mod 2 pi and step formed in FP64 by the phase-table kernel,
+// as in fx_correct). Per 16-spectrum round the CTA tabulates exp(i phi) for
+// its (station, channel, spectrum) triples once (both pols share them): phi
+// is reduced to [-pi, pi] in FP32 with a two-constant Cody-Waite split of
+// 2 pi and passed to __sincosf, whose absolute error on that interval is
+// about 4e-7.
+//
+// The corrected round is turned in shared memory (reusing the FFT buffer) and
+// written as
+//   FP32   [SB][C][S][I]: per (channel, spectrum) a run of 2*NPC inputs;
+//          the grid walks station groups fastest so neighbouring CTAs fill
+//          the same lines while they are in L2;
+//   planar [SB][C][planes][I_pad][S_pad]: per (channel, plane, input) a run of
+//          16 spectra (32 bytes), FP16/BF16 (x operand_scale) or hi/lo FP16.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "fft_reg.cuh"
+#include "internal.h"
+#include "ppf_common.cuh"
+
+namespace fxi {
+namespace {
+
+using namespace ppf;
+
+// OUT: 1 FP32 interleaved, 2 FP16 planar, 3 BF16 planar, 4 split FP16 planar
+template <int C, typename TIn>
+constexpr size_t fused_smem_bytes()
+{
+    using Cfg = PpfCfg<C>;
+    return ppf_smem_bytes<C, TIn>() + (size_t)kRound * Cfg::NPC * C * sizeof(float2)   // phasors
+           + (size_t)Cfg::NPC * kPols * C * sizeof(float2);                              // bandpass x gain
+}
+
+__device__ __forceinline__ unsigned short to_bits(float x, int out)
+{
+    if (out == 3) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    return __half_as_ushort(__float2half_rn(x));
+}
+
+template <int C, int T, typename TIn, int OUT>
+__global__ void __launch_bounds__(PpfCfg<C>::NT, PpfCfg<C>::NT >= 512 ? 1 : 2)
+ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const float *__restrict__ taps,
+                   const float2 *__restrict__ twiddle, const float2 *__restrict__ phase,
+                   const float *__restrict__ bandpass, const float2 *__restrict__ gains, int N, int S, int I_pad,
+                   int S_pad, float scale, int rounds_per_cta)
+{
+    using Cfg = PpfCfg<C>;
+    constexpr int R = Cfg::R, NPC = Cfg::NPC, NT = Cfg::NT, ROW = Cfg::ROW;
+    constexpr int ROW_BYTES = C * kPols * (int)sizeof(TIn);
+    constexpr int BUF_BYTES = kRound * NPC * ROW_BYTES;
+    constexpr int IC = NPC * kPols;                 // inputs of this CTA
+    static_assert(ROW_BYTES % 16 == 0, "rows must be whole 16-byte chunks");
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2 *tw = reinterpret_cast<float2 *>(smem);
+    unsigned char *inbuf = smem + C * sizeof(float2);
+    float2 *u = reinterpret_cast<float2 *>(inbuf + 2 * BUF_BYTES);
+    float2 *ph = u + Cfg::NTR * ROW;                // [kRound][NPC][C]
+    float2 *bg = ph + kRound * NPC * C;             // [NPC][P][C]
+
+    const int tid = threadIdx.x;
+    const int sb = blockIdx.z;
+    const int n0 = blockIdx.x * NPC;                // station groups fastest
+    const int s0 = blockIdx.y * rounds_per_cta * kRound;
+    const int rows_total = S + T - 1;
+    const long long L = (long long)rows_total * C;
+    const int nrounds = min(rounds_per_cta, (S - s0 + kRound - 1) / kRound);
+    const int I = N * kPols;
+
+    auto stage = [&](int buf, int r0, int nrows) {
+        const int chunks = nrows * ROW_BYTES / 16;
+        for (int q = tid; q < NPC * chunks; q += NT) {
+            const int st = q / chunks, ch = q - st * chunks;
+            const int n = n0 + st;
+            const int row_in = (ch * 16) / ROW_BYTES;
+            const int byte_in_row = (ch * 16) - row_in * ROW_BYTES;
+            unsigned char *dst = inbuf + buf * BUF_BYTES + (row_in * NPC + st) * ROW_BYTES + byte_in_row;
+            const bool ok = (n < N) && (r0 + row_in < rows_total);
+            const unsigned char *src = reinterpret_cast<const unsigned char *>(raw);
+            if (ok) src += ((((long long)sb * N + n) * L + (long long)r0 * C) * kPols) * sizeof(TIn) + ch * 16;
+            cp_async16(dst, src, ok ? 16 : 0);
+        }
+    };
+
+    const int p = tid % kPols;
+    const int c = (tid / kPols) % C;
+    const int nl = tid / (kPols * C);
+
+    for (int i = tid; i < C; i += NT) tw[i] = twiddle[i];
+    for (int i = tid; i < NPC * kPols * C; i += NT) {
+        const int k = i % C, pp = (i / C) % kPols, st = i / (kPols * C);
+        const int n = min(n0 + st, N - 1);
+        const float b = bandpass ? bandpass[(long long)n * C + k] : 1.f;
+        const float2 g = gains ? gains[n * kPols + pp] : make_float2(1.f, 0.f);
+        bg[i] = make_float2(b * g.x * scale, b * g.y * scale);
+    }
+    // phasor ownership: (station, channel) = tid mod NPC*C, spectra j = j0, j0+2, ...
+    constexpr int OWN = NPC * C;                    // = NT / 2
+    const int own_nc = tid % OWN, own_j0 = tid / OWN;
+    const int own_n = min(n0 + own_nc / C, N - 1), own_k = own_nc % C;
+    const float2 pst = phase[((long long)sb * N + own_n) * C + own_k];   // (phi0, step)
+
+    float h[T];
+#pragma unroll
+    for (int k = 0; k < T; ++k) h[k] = taps[k * C + c];
+
+    stage(1, s0, T - 1);
+    cp_async_commit();
+    stage(0, s0 + T - 1, kRound);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+
+    float2 win[T];
+    const TIn *in1 = reinterpret_cast<const TIn *>(inbuf + BUF_BYTES);
+#pragma unroll
+    for (int k = 0; k < T - 1; ++k) win[k] = to_f2(in1[k * NT + tid]);
+    win[T - 1] = make_float2(0.f, 0.f);
+    __syncthreads();
+    if (nrounds > 1) stage(1, s0 + T - 1 + kRound, kRound);
+    cp_async_commit();
+
+    for (int b = 0; b < nrounds; ++b) {
+        const int sr = s0 + b * kRound;             // first spectrum of this round
+        cp_async_wait<1>();
+        __syncthreads();
+        // ---- FIR over 16 new rows ----
+        const TIn *in = reinterpret_cast<const TIn *>(inbuf + (b & 1) * BUF_BYTES);
+#pragma unroll
+        for (int j = 0; j < kRound; ++j) {
+            win[(T - 1 + j) % T] = to_f2(in[j * NT + tid]);
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < T; ++k) {
+                const float2 x = win[(j + k) % T];
+                acc.x = fmaf(h[k], x.x, acc.x);
+                acc.y = fmaf(h[k], x.y, acc.y);
+            }
+            u[((nl * kPols + p) * kRound + j) * ROW + c] = acc;
+        }
+        // ---- phasors exp(i phi) of this round ----
+#pragma unroll
+        for (int q = 0; q < kRound / 2; ++q) {
+            const int j = own_j0 + 2 * q;
+            const float phi = fmaf((float)(sr + j), pst.y, pst.x);
+            const float kq = rintf(phi * 0.15915494309189535f);           // phi / (2 pi)
+            float r = fmaf(-kq, 6.28125f, phi);                           // 2 pi = 6.28125 + 1.9353...e-3
+            r = fmaf(-kq, 1.9353071795864769e-3f, r);
+            float sn, cs;
+            __sincosf(r, &sn, &cs);
+            ph[j * OWN + own_nc] = make_float2(cs, sn);
+        }
+        __syncthreads();
+        if (b + 2 < nrounds) stage(b & 1, s0 + T - 1 + (b + 2) * kRound, kRound);
+        cp_async_commit();
+
+        // ---- FFT pass 1 ----
+#pragma unroll
+        for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
+            const int task = it * NT + tid;
+            const int tr = task / R, n2 = task % R;
+            float2 *row = u + tr * ROW;
+            float2 v[R];
+#pragma unroll
+            for (int n1 = 0; n1 < R; ++n1) v[n1] = row[R * n1 + n2];
+            fft_reg<R>(v);
+#pragma unroll
+            for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], tw[n2 * k1]);
+#pragma unroll
+            for (int k1 = 0; k1 < R; ++k1) row[R * k1 + n2] = v[k1];
+        }
+        __syncthreads();
+        // ---- FFT pass 2 + correction, results held in registers ----
+        float2 y[Cfg::FFT_ITERS][R];
+#pragma unroll
+        for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
+            const int task = it * NT + tid;
+            const int tr = task / R, k1 = task % R;
+            const float2 *row = u + tr * ROW;
+#pragma unroll
+            for (int n2 = 0; n2 < R; ++n2) y[it][n2] = row[R * k1 + n2];
+            fft_reg<R>(y[it]);
+            const int j = tr % kRound;
+            const int pp = (tr / kRound) % kPols;
+            const int tnl = tr / (kRound * kPols);
+#pragma unroll
+            for (int k2 = 0; k2 < R; ++k2) {
+                const int kout = k1 + R * ((k2 + R / 2) % R);
+                const float2 w = cmul(bg[(tnl * kPols + pp) * C + kout], ph[j * OWN + tnl * C + kout]);
+                y[it][k2] = cmul(y[it][k2], w);
+            }
+        }
+        __syncthreads();                             // every read of u is done
+        // ---- stage the corrected round in u, in the output's order ----
+#pragma unroll
+        for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
+            const int task = it * NT + tid;
+            const int tr = task / R, k1 = task % R;
+            const int j = tr % kRound;
+            const int il = (tr / kRound) % kPols + kPols * (tr / (kRound * kPols));
+#pragma unroll
+            for (int k2 = 0; k2 < R; ++k2) {
+                const int kout = k1 + R * ((k2 + R / 2) % R);
+                if constexpr (OUT == 1)
+                    u[(kout * kRound + j) * IC + il] = y[it][k2];     // [C][16][IC]
+                else
+                    u[(kout * IC + il) * kRound + j] = y[it][k2];     // [C][IC][16]
+            }
+        }
+        __syncthreads();
+        // ---- write out ----
+        if constexpr (OUT == 1) {
+            float2 *out = reinterpret_cast<float2 *>(corr);
+            // float4 = two consecutive inputs of one (channel, spectrum)
+            for (int e = tid; e < C * kRound * (IC / 2); e += NT) {
+                const int ip = e % (IC / 2);
+                const int j = (e / (IC / 2)) % kRound;
+                const int kout = e / ((IC / 2) * kRound);
+                const int s = sr + j;
+                const int i = 2 * n0 + 2 * ip;        // = input index of pol 0 of station n0 + ip
+                if (s < S && i < I) {
+                    const float2 a0 = u[(kout * kRound + j) * IC + 2 * ip];
+                    const float2 a1 = u[(kout * kRound + j) * IC + 2 * ip + 1];
+                    *reinterpret_cast<float4 *>(out + (((long long)sb * C + kout) * S + s) * I + i) =
+                        make_float4(a0.x, a0.y, a1.x, a1.y);
+                }
+            }
+        } else {
+            constexpr int planes = (OUT == 4) ? 4 : 2;
+            unsigned short *out = reinterpret_cast<unsigned short *>(corr);
+            const long long pstride = (long long)I_pad * S_pad;
+            for (int e = tid; e < C * IC; e += NT) {
+                const int il = e % IC, kout = e / IC;
+                const int i = 2 * n0 + il;
+                if (i >= I) continue;
+                const float2 *src = u + (kout * IC + il) * kRound;
+                unsigned short re[kRound], im[kRound], rl[kRound], iml[kRound];
+#pragma unroll
+                for (int j = 0; j < kRound; ++j) {
+                    const float2 v = (sr + j < S) ? src[j] : make_float2(0.f, 0.f);
+                    re[j] = to_bits(v.x, OUT);
+                    im[j] = to_bits(v.y, OUT);
+                    if constexpr (OUT == 4) {
+                        rl[j] = __half_as_ushort(__float2half_rn(v.x - __half2float(__ushort_as_half(re[j]))));
+                        iml[j] = __half_as_ushort(__float2half_rn(v.y - __half2float(__ushort_as_half(im[j]))));
+                    }
+                }
+                const long long base = (((long long)sb * C + kout) * planes) * pstride + (long long)i * S_pad + sr;
+                auto put = [&](long long off, const unsigned short (&v)[kRound]) {
+                    uint4 w0, w1;
+                    w0.x = v[0] | ((unsigned)v[1] << 16);
+                    w0.y = v[2] | ((unsigned)v[3] << 16);
+                    w0.z = v[4] | ((unsigned)v[5] << 16);
+                    w0.w = v[6] | ((unsigned)v[7] << 16);
+                    w1.x = v[8] | ((unsigned)v[9] << 16);
+                    w1.y = v[10] | ((unsigned)v[11] << 16);
+                    w1.z = v[12] | ((unsigned)v[13] << 16);
+                    w1.w = v[14] | ((unsigned)v[15] << 16);
+                    uint4 *d = reinterpret_cast<uint4 *>(out + off);
+                    d[0] = w0;
+                    d[1] = w1;
+                };
+                put(base, re);
+                put(base + pstride, im);
+                if constexpr (OUT == 4) {
+                    put(base + 2 * pstride, rl);
+                    put(base + 3 * pstride, iml);
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
+// Zero the padding of the planar layout that the fused kernel does not cover:
+// inputs [I, I_pad) and spectra [ceil16(S), S_pad) of every (subband, channel, plane).
+__global__ void planar_pad_kernel(unsigned short *__restrict__ corr, long long n_rows, int I, int I_pad, int S16,
+                                  int S_pad)
+{
+    const long long row = blockIdx.x;               // (sb, c, plane, i) flattened
+    if (row >= n_rows) return;
+    const int i = (int)(row % I_pad);
+    unsigned short *r = corr + row * S_pad;
+    const int from = (i >= I) ? 0 : S16;
+    for (int s = from + threadIdx.x; s < S_pad; s += blockDim.x) r[s] = 0;
+}
+
+template <int C, int T, typename TIn, int OUT>
+cudaError_t launch_t(const Handle &h, const void *raw, void *corr, const float *bandpass, const float2 *gains,
+                     cudaStream_t st)
+{
+    using Cfg = PpfCfg<C>;
+    const int N = h.p.n_stations, S = h.p.n_spectra, SB = h.p.n_subbands;
+    const int rounds_total = (S + kRound - 1) / kRound;
+    const int sgroups = (N + Cfg::NPC - 1) / Cfg::NPC;
+    int rpc = 8;
+    while (rpc > 1 && (long long)((rounds_total + rpc - 1) / rpc) * sgroups * SB < 152LL * 4) rpc /= 2;
+    dim3 grid(sgroups, (rounds_total + rpc - 1) / rpc, SB);
+    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+    constexpr size_t smem = fused_smem_bytes<C, TIn>();
+    auto kern = ppf_correct_kernel<C, T, TIn, OUT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const float scale = (OUT == 1) ? 1.f : h.operand_scale;
+    kern<<<grid, Cfg::NT, smem, st>>>(reinterpret_cast<const TIn *>(raw), corr, h.d_taps, h.d_twiddle, h.d_phase,
+                                      bandpass, gains, N, S, h.I_pad, h.S_pad, scale, rpc);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || OUT == 1) return e;
+    const int S16 = rounds_total * kRound;
+    if (h.I_pad > h.I || h.S_pad > S16) {
+        const long long rows = (long long)SB * C * (OUT == 4 ? 4 : 2) * h.I_pad;
+        if (rows > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+        planar_pad_kernel<<<(unsigned)rows, 64, 0, st>>>(reinterpret_cast<unsigned short *>(corr), rows, h.I, h.I_pad,
+                                                          S16, h.S_pad);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+template <int C, int T, typename TIn>
+cudaError_t launch_out(const Handle &h, const void *raw, void *corr, const float *bp, const float2 *g, cudaStream_t st)
+{
+    switch (h.p.precision) {
+    case FX_F32: return launch_t<C, T, TIn, 1>(h, raw, corr, bp, g, st);
+    case FX_F16: return launch_t<C, T, TIn, 2>(h, raw, corr, bp, g, st);
+    case FX_BF16: return launch_t<C, T, TIn, 3>(h, raw, corr, bp, g, st);
+    default: return launch_t<C, T, TIn, 4>(h, raw, corr, bp, g, st);
+    }
+}
+
+template <int C, typename TIn>
+cudaError_t launch_taps(const Handle &h, const void *raw, void *corr, const float *bp, const float2 *g,
+                        cudaStream_t st)
+{
+    switch (h.p.n_taps) {
+    case 4: return launch_out<C, 4, TIn>(h, raw, corr, bp, g, st);
+    case 8: return launch_out<C, 8, TIn>(h, raw, corr, bp, g, st);
+    case 16: return launch_out<C, 16, TIn>(h, raw, corr, bp, g, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename TIn>
+cudaError_t launch_fmt(const Handle &h, const void *raw, void *corr, const float *bp, const float2 *g, cudaStream_t st)
+{
+    switch (h.p.n_channels) {
+    case 16: return launch_taps<16, TIn>(h, raw, corr, bp, g, st);
+    case 64: return launch_taps<64, TIn>(h, raw, corr, bp, g, st);
+    case 256: return launch_taps<256, TIn>(h, raw, corr, bp, g, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_channelize_correct(const Handle &h, const void *raw, const float *bandpass, const float2 *gains,
+                                      void *corr, cudaStream_t st)
+{
+    if (h.p.format == FX_CI16) return launch_fmt<short2>(h, raw, corr, bandpass, gains, st);
+    return launch_fmt<char2>(h, raw, corr, bandpass, gains, st);
+}
+
+}  // namespace fxi

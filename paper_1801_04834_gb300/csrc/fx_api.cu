@@ -220,6 +220,24 @@ extern "C" fx_status fx_correct(fx_handle *h, const float *d_chan, const double 
     return after_launch(e, "fx_correct");
 }
 
+extern "C" fx_status fx_channelize_correct(fx_handle *h, const void *d_raw, const double *d_delay_begin,
+                                           const double *d_delay_end, const float *d_bandpass,
+                                           const float *d_gains, void *d_corr, fx_stream stream)
+{
+    const char *who = "fx_channelize_correct";
+    fx_status st = check_handle(h, who);
+    if (st) return st;
+    if (!d_raw || !d_corr || !d_delay_begin || !d_delay_end) return fail(FX_ERR_INVALID, "%s: NULL buffer", who);
+    if (((uintptr_t)d_raw & 15) || ((uintptr_t)d_corr & 15) || ((uintptr_t)d_gains & 7) ||
+        ((uintptr_t)d_bandpass & 3) || ((uintptr_t)d_delay_begin & 7) || ((uintptr_t)d_delay_end & 7))
+        return fail(FX_ERR_INVALID, "%s: misaligned buffer", who);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = fxi::launch_phase_table(*h, d_delay_begin, d_delay_end, s);
+    if (e == cudaSuccess)
+        e = fxi::launch_channelize_correct(*h, d_raw, d_bandpass, reinterpret_cast<const float2 *>(d_gains), d_corr, s);
+    return after_launch(e, who);
+}
+
 extern "C" fx_status fx_poll_status(fx_handle *h, int *code)
 {
     fx_status st = check_handle(h, "fx_poll_status");

@@ -36,6 +36,10 @@ struct Handle {
 cudaError_t launch_ppf(const Handle &h, const void *raw, float2 *chan, cudaStream_t st);
 bool ppf_supported(int C, int T);
 
+// channelize_correct.cu
+cudaError_t launch_channelize_correct(const Handle &h, const void *raw, const float *bandpass, const float2 *gains,
+                                      void *corr, cudaStream_t st);
+
 // correct.cu
 cudaError_t launch_phase_table(const Handle &h, const double *tau_b, const double *tau_e,
                                cudaStream_t st);

@@ -22,46 +22,12 @@
 //   * Output channel k = (m + C/2) mod C (ascending sky frequency).
 #include "internal.h"
 #include "fft_reg.cuh"
+#include "ppf_common.cuh"
 
 namespace fxi {
 namespace {
 
-constexpr int kRound = 16;  // spectra per round; a multiple of every supported T
-
-template <int C>
-struct PpfCfg {
-    static constexpr int R = (C == 16) ? 4 : (C == 64) ? 8 : 16;  // C = R * R
-    static constexpr int NPC = (C * kPols >= 256) ? 1 : 256 / (C * kPols);  // stations per CTA
-    static constexpr int NT = NPC * C * kPols;                    // threads per CTA
-    static constexpr int PAD = (R == 4) ? 4 : 8;                  // float2 pad per smem row
-    static constexpr int ROW = C + PAD;
-    static constexpr int NTR = NPC * kPols * kRound;              // transforms per round
-    static constexpr int FFT_ITERS = NTR * R / NT;
-    static_assert(R * R == C, "C must be a square of R");
-    static_assert(NTR * R % NT == 0, "FFT tasks must tile the CTA");
-};
-
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, int src_bytes)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc),
-                 "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-__device__ __forceinline__ float2 to_f2(short2 v) { return make_float2((float)v.x, (float)v.y); }
-__device__ __forceinline__ float2 to_f2(char2 v) { return make_float2((float)v.x, (float)v.y); }
-
-template <int C, typename TIn>
-constexpr size_t ppf_smem_bytes()
-{
-    using Cfg = PpfCfg<C>;
-    return (size_t)C * sizeof(float2) + 2ull * kRound * Cfg::NPC * C * kPols * sizeof(TIn) +
-           (size_t)Cfg::NTR * Cfg::ROW * sizeof(float2);
-}
+using namespace ppf;
 
 template <int C, int T, typename TIn>
 __global__ void __launch_bounds__(PpfCfg<C>::NT)

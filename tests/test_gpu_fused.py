@@ -1,0 +1,80 @@
+"""fx_channelize_correct (F-stage + correction in one pass) against the
+two-call path (fx_channelize, fx_correct) and against the FP64 oracle.
+
+The fused kernel evaluates the per-sample phasor with a fast sin/cos after an
+FP32 reduction (absolute error ~4e-7), so FP32 outputs agree with the
+two-call path to ~1e-6 normwise (bound 2e-6); FP16/BF16 outputs may differ by
+one unit in the last place where that difference crosses a rounding
+boundary. End to end against the oracle the stated bounds apply.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from test_gpu_parity import make_corr, per_subband_rel, tone_block
+
+pytestmark = pytest.mark.gpu
+FS = synth.SAMPLE_RATE_HZ
+
+
+def d(a, dt=torch.float32):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
+
+
+CASES = [  # (fmt, SB, N, C, T, S)
+    (synth.CI16, 2, 3, 64, 16, 37),
+    (synth.CI16, 1, 9, 16, 16, 40),
+    (synth.CI8, 2, 2, 256, 16, 19),
+    (synth.CI16, 1, 5, 16, 4, 33),
+    (synth.CI8, 1, 64, 64, 8, 130),
+    (synth.CI16, 1, 1, 64, 16, 1),
+]
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
+@pytest.mark.parametrize("fmt,SB,N,C,T,S", CASES)
+def test_fused_matches_two_calls(precision, fmt, SB, N, C, T, S):
+    blk, tau, rip = tone_block(300 + S + N, fmt, SB, N, C, S, T=T, ripple=True,
+                               sigma=20.0 if fmt == synth.CI8 else 100.0)
+    rng = np.random.default_rng(4)
+    te = tau + rng.uniform(-2e-8, 2e-8, N)
+    g = synth.random_gains(rng, N)
+    c = make_corr(blk, precision=precision, operand_scale=0.5 if precision else 0.0)
+    raw = torch.from_numpy(blk.raw).cuda()
+    tb_d, te_d, bp_d, g_d = d(tau, torch.float64), d(te, torch.float64), d(1.0 / rip), d(g)
+    two = c.correct(c.channelize(raw), tb_d, te_d, bandpass=bp_d, gains=g_d)
+    out = torch.full_like(two, float("nan")) if precision == 0 else torch.full_like(two, 7.0)
+    fused = c.channelize_correct(raw, tb_d, te_d, bandpass=bp_d, gains=g_d, out=out)
+    torch.cuda.synchronize()
+    a, b = fused.double(), two.double()
+    if precision == 3:   # compare the represented value hi + lo
+        a, b = a[:, :, 0:2] + a[:, :, 2:4], b[:, :, 0:2] + b[:, :, 2:4]
+    rel = (torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item()
+    if precision in (0, 3):
+        assert rel < 2e-6, rel
+        if precision == 3 and (c.I_pad > c.I or c.S_pad > S):
+            assert torch.all(fused[:, :, :, c.I:, :] == 0) and torch.all(fused[:, :, :, :, S:] == 0)
+    else:
+        # ulp flips only: the difference is at most one unit of the operand type per element
+        ulp = {1: 2.0 ** -10, 2: 2.0 ** -7}[precision]
+        assert torch.all((a - b).abs() <= ulp * b.abs() + 2.0 ** -24), rel
+        assert rel < {1: 1e-4, 2: 1e-3}[precision], rel
+        if c.I_pad > c.I or c.S_pad > S:
+            assert torch.all(fused[:, :, :, c.I:, :] == 0) and torch.all(fused[:, :, :, :, S:] == 0)
+
+
+@pytest.mark.parametrize("precision,bound", [(0, 1e-5), (1, 5e-3), (3, 1e-4)])
+def test_fused_end_to_end_vs_oracle(precision, bound):
+    """8 stations x 2 pols, 1 subband, 64 channels, 768 spectra (the tiny
+    workload) and a ragged 5-station int8 case, through the fused path."""
+    for (fmt, SB, N, C, S) in [(synth.CI16, 1, 8, 64, 768), (synth.CI8, 2, 5, 256, 33)]:
+        blk, tau, _ = tone_block(synth.BASE_SEED + N, fmt, SB, N, C, S,
+                                 sigma=20.0 if fmt == synth.CI8 else 100.0)
+        ref = oracle.fx(blk.fmt, blk.raw, 16, C, S, blk.taps, FS, blk.centres, tau, tau)
+        c = make_corr(blk, precision=precision)
+        t = d(tau, torch.float64)
+        vis = c.correlate(c.channelize_correct(torch.from_numpy(blk.raw).cuda(), t, t))
+        e = per_subband_rel(vis.cpu().numpy().astype(np.float64), ref)
+        assert np.all(e < bound), (precision, N, e)
