@@ -14,9 +14,16 @@
 // 4 inputs) x 4 stations (columns, 8 inputs) = 32 complex accumulators, i.e.
 // 128 FFMAs per time sample against 6 shared-memory vector loads. Tiles
 // (row pair r, column quad q) are kept only where some pair i <= j exists
-// (2r <= 4q+3), which gives N(N+1)/2 useful pairs out of ~N(N+2)/2 computed.
-// A CTA holds the tile set of `cpb` channels; time is streamed through shared
-// memory in chunks of KC samples with double-buffered cp.async.
+// (2r <= 4q+3): 272 tiles for 64 stations, 4.6% more MACs than the triangle.
+//
+// Threads are numbered over the flattened (channel, tile) index, up to 512 per
+// CTA (16 warps, 4 per scheduler), so a CTA covers the tiles of one to a few
+// channels whatever the station count; it streams the time samples of every
+// channel it touches through shared memory in chunks of KC samples with
+// double-buffered cp.async. Within a time row the 16-byte station entries are
+// stored as [even stations][odd stations], so the two row loads of
+// consecutive row-pair tiles fall on consecutive 16-byte words (no bank
+// conflicts); column loads are mostly broadcasts.
 #include <algorithm>
 
 #include "internal.h"
@@ -24,8 +31,8 @@
 namespace fxi {
 namespace {
 
-constexpr int kKC = 32;          // time samples per shared-memory chunk
-constexpr int kMaxThreads = 544;   // 2 channels x 272 tiles at N = 64; 120 registers
+constexpr int kMaxThreads = 512;   // 16 warps
+constexpr size_t kSmemBudget = 200 * 1024;
 
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, int src_bytes)
 {
@@ -38,41 +45,49 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// One CTA: channels [chb*cpb, +cpb) of the flattened (subband, channel) index
-// and part `part` of the tile list (parts > 1 only when one channel's tiles
-// exceed a CTA, then cpb = 1); thread t works on tile part*tpp + t % tpp of
-// channel t / tpp.
+// Thread g = blockIdx.x * blockDim.x + threadIdx.x works on tile g % ntiles of
+// channel g / ntiles; the CTA stages the rows of channels [ch_first, ch_first + max_ch).
+// kKC time samples per shared-memory chunk (32, or less for very many stations).
+template <int kKC>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
-                 const int2 *__restrict__ tiles, int ntiles, int tpp, int parts, int N, int S,
-                 int IP, int cpb, long long total_ch)
+                 const int2 *__restrict__ tiles, int ntiles, int N, int S, int IP, int max_ch,
+                 long long total_ch)
 {
-    extern __shared__ float4 sm[];   // [2][cpb][KC][IP/2] float4
+    extern __shared__ float4 sm[];   // [2][max_ch][KC][IP/2] float4
     const int I = 2 * N;
-    const int row4 = IP / 2;                       // float4 per time row
-    const int stage_f4 = cpb * kKC * row4;
+    const int row4 = IP / 2;                       // float4 (= station entries) per time row
+    const int half = IP / 4;                       // offset of the odd-station half
+    const int stage_f4 = max_ch * kKC * row4;
     const int tid = threadIdx.x;
-    const int part = blockIdx.x % parts;
-    const long long ch0 = (long long)(blockIdx.x / parts) * cpb;
+    const long long g0 = (long long)blockIdx.x * blockDim.x;
+    const long long ch_first = g0 / ntiles;
+    const long long ch_last = (g0 + blockDim.x - 1) / ntiles + 1;
+    const long long ch_end = ch_last < total_ch ? ch_last : total_ch;
+    const int nch = (int)(ch_end - ch_first);
     const int nthr = blockDim.x;
 
     auto load_chunk = [&](int stage, int s0) {
         float4 *dst0 = sm + stage * stage_f4;
-        for (int v = tid; v < stage_f4; v += nthr) {
-            const int x = v % row4;
+        const int per_ch = kKC * row4;
+        for (int v = tid; v < nch * per_ch; v += nthr) {
+            const int x = v % row4;                // station entry in global order
             const int s = (v / row4) % kKC;
-            const int cl = v / (row4 * kKC);
-            const long long gch = ch0 + cl;
-            const bool ok = (2 * x < I) && (s0 + s < S) && (gch < total_ch);
+            const int cl = v / per_ch;
+            const long long gch = ch_first + cl;
+            const bool ok = (2 * x < I) && (s0 + s < S);
             const float2 *src = corr;
             if (ok) src = corr + (gch * S + s0 + s) * (long long)I + 2 * x;
-            cp_async16(dst0 + v, src, ok ? 16 : 0);
+            const int xs = (x & 1) * half + (x >> 1);   // [even stations][odd stations]
+            cp_async16(dst0 + (cl * kKC + s) * row4 + xs, src, ok ? 16 : 0);
         }
     };
 
-    const int cl = tid / tpp;
-    const int tl = part * tpp + (tid - cl * tpp);
-    const bool active = cl < cpb && (ch0 + cl) < total_ch && tl < ntiles;
+    const long long g = g0 + tid;
+    const long long gch = g / ntiles;
+    const int tl = (int)(g - gch * ntiles);
+    const int cl = (int)(gch - ch_first);
+    const bool active = gch < total_ch;
     int2 rq = make_int2(0, 0);
     if (active) rq = tiles[tl];
     const int r = rq.x, q = rq.y;
@@ -96,9 +111,11 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
 #pragma unroll 2
             for (int s = 0; s < kKC; ++s) {
                 const float4 *rowp = base + s * row4;
-                const float4 x0 = rowp[2 * r], x1 = rowp[2 * r + 1];
-                const float4 y0 = rowp[4 * q], y1 = rowp[4 * q + 1], y2 = rowp[4 * q + 2],
-                             y3 = rowp[4 * q + 3];
+                // row stations 2r (even half) and 2r+1 (odd half)
+                const float4 x0 = rowp[r], x1 = rowp[half + r];
+                // column stations 4q, 4q+1, 4q+2, 4q+3
+                const float4 y0 = rowp[2 * q], y1 = rowp[half + 2 * q], y2 = rowp[2 * q + 1],
+                             y3 = rowp[half + 2 * q + 1];
                 const float xr[4] = {x0.x, x0.z, x1.x, x1.z};
                 const float xi[4] = {x0.y, x0.w, x1.y, x1.w};
                 const float yr[8] = {y0.x, y0.z, y1.x, y1.z, y2.x, y2.z, y3.x, y3.z};
@@ -118,7 +135,6 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
         __syncthreads();
     }
     if (!active) return;
-    const long long gch = ch0 + cl;
     const long long B = (long long)N * (N + 1) / 2;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -152,29 +168,50 @@ int xf32_build_tiles(int N, int2 *out)
     return n;
 }
 
+// CTA size (largest of 512, 384, 256, 128, 96, 64, 32 threads) whose touched
+// channels fit in shared memory, shrunk while the grid would not fill the GPU.
+bool xf32_geometry(int N, long long total_ch, int ntiles, int kc, int *threads, int *max_ch)
+{
+    const int IP = 8 * ((N + 3) / 4);
+    const size_t row_bytes = (size_t)kc * IP * sizeof(float2);
+    static const int cand[] = {512, 384, 256, 128, 96, 64, 32};
+    int t = 0, mc = 0, k = 0;
+    for (; k < 7; ++k) {
+        mc = (cand[k] + ntiles - 1) / ntiles + 1;
+        if (2 * mc * row_bytes <= kSmemBudget) {
+            t = cand[k];
+            break;
+        }
+    }
+    if (!t) return false;
+    while (k + 1 < 7 && (total_ch * ntiles + t - 1) / t < 2 * 152) {
+        ++k;
+        t = cand[k];
+        mc = (t + ntiles - 1) / ntiles + 1;
+    }
+    *threads = t;
+    *max_ch = mc;
+    return true;
+}
+
 cudaError_t launch_xcorr_f32(const Handle &h, const float2 *corr, float2 *vis, cudaStream_t st)
 {
     const int N = h.p.n_stations, S = h.p.n_spectra;
     const int IP = 8 * ((N + 3) / 4);
     const int nt = h.xf32_ntiles;
-    const int parts = (nt + kMaxThreads - 1) / kMaxThreads;
-    const int tpp = (nt + parts - 1) / parts;          // tiles per CTA part
     const long long total = (long long)h.p.n_subbands * h.p.n_channels;
-    const size_t per_ch = 2ull * kKC * IP * sizeof(float2);
-    if (per_ch > 200 * 1024) return cudaErrorNotSupported;   // > ~400 stations
-    int cpb = parts > 1 ? 1 : std::max(1, kMaxThreads / nt);
-    cpb = (int)std::min<long long>(cpb, std::max<size_t>(1, (200 * 1024) / per_ch));
-    // keep at least ~2 waves of CTAs on 152 SMs
-    while (cpb > 1 && (total + cpb - 1) / cpb < 2 * 152) --cpb;
-    const int threads = (cpb * tpp + 31) / 32 * 32;
-    const size_t smem = per_ch * cpb;
-    cudaError_t e = cudaFuncSetAttribute(xcorr_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    const long long blocks = (total + cpb - 1) / cpb * parts;
+    int threads = 0, max_ch = 0, kc = 32;
+    for (; kc >= 4; kc /= 2)
+        if (xf32_geometry(N, total, nt, kc, &threads, &max_ch)) break;
+    if (kc < 4) return cudaErrorNotSupported;   // > ~800 stations
+    const size_t smem = 2ull * max_ch * kc * IP * sizeof(float2);
+    const long long blocks = (total * nt + threads - 1) / threads;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    xcorr_f32_kernel<<<(unsigned)blocks, threads, smem, st>>>(corr, vis, h.d_xf32_tiles, nt, tpp, parts,
-                                                              N, S, IP, cpb, total);
+    auto kern = kc == 32 ? xcorr_f32_kernel<32> : kc == 16 ? xcorr_f32_kernel<16> : kc == 8 ? xcorr_f32_kernel<8>
+                                                                                            : xcorr_f32_kernel<4>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)blocks, threads, smem, st>>>(corr, vis, h.d_xf32_tiles, nt, N, S, IP, max_ch, total);
     return cudaGetLastError();
 }
 

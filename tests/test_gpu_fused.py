@@ -57,9 +57,11 @@ def test_fused_matches_two_calls(precision, fmt, SB, N, C, T, S):
         if precision == 3 and (c.I_pad > c.I or c.S_pad > S):
             assert torch.all(fused[:, :, :, c.I:, :] == 0) and torch.all(fused[:, :, :, :, S:] == 0)
     else:
-        # ulp flips only: the difference is at most one unit of the operand type per element
+        # at most one unit of the operand type per element, plus the FP32-level
+        # absolute difference (~1e-7 of the block's largest value) that shows on
+        # elements near cancellation
         ulp = {1: 2.0 ** -10, 2: 2.0 ** -7}[precision]
-        assert torch.all((a - b).abs() <= ulp * b.abs() + 2.0 ** -24), rel
+        assert torch.all((a - b).abs() <= ulp * b.abs() + 1e-6 * b.abs().max()), rel
         assert rel < {1: 1e-4, 2: 1e-3}[precision], rel
         if c.I_pad > c.I or c.S_pad > S:
             assert torch.all(fused[:, :, :, c.I:, :] == 0) and torch.all(fused[:, :, :, :, S:] == 0)

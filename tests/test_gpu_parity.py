@@ -102,7 +102,8 @@ def test_correct_f32_parity(N, C, S, ramp):
 
 
 @pytest.mark.parametrize("N,C,S,SB", [(8, 64, 100, 2), (64, 4 * 4, 33, 1), (1, 16, 20, 3),
-                                      (13, 16, 65, 1), (76, 16, 40, 1), (96, 16, 17, 1)])
+                                      (13, 16, 65, 1), (76, 16, 40, 1), (96, 16, 17, 1),
+                                      (150, 16, 45, 1), (64, 64, 70, 3)])
 def test_correlate_f32_parity(N, C, S, SB):
     if C not in (16, 64, 256):
         pytest.skip("channel count not built")
