@@ -84,6 +84,9 @@ typedef struct {
     float operand_scale;         /* power of two multiplied into FP16/BF16
                                     operands and divided out of vis; 0 means 1 */
     unsigned flags;              /* 0, or FX_FLAG_TEST_NO_LOADS */
+    int host_chunk_subbands;     /* > 0: allocate the double-buffered workspaces of
+                                    fx_process_host for chunks of this many
+                                    subbands; 0: no host pipeline */
 } fx_params;
 
 /* Failure-detection test hook: the tensor-core X-stage issues no operand
@@ -164,6 +167,25 @@ fx_status fx_channelize_correct(fx_handle *h, const void *d_raw, const double *d
  * operands run on the CUDA cores; FP16/BF16/split operands on the tcgen05
  * tensor cores with FP32 accumulation (split: hi*hi' + hi*lo' + lo*hi'). */
 fx_status fx_correlate(fx_handle *h, const void *d_corr, float *d_vis, fx_stream stream);
+
+/* End to end from host memory: raw samples in, visibilities out, for all
+ * subbands of the handle. The subbands are processed in chunks of
+ * host_chunk_subbands (set at fx_create) on three library streams so that the
+ * host-to-device copy of chunk k+1 and the device-to-host copy of chunk k-1
+ * overlap the fused channelise/correct and the X-stage of chunk k (double
+ * buffered device workspaces). The paper's input and output stages run in
+ * parallel with GPU processing in the same way (Sec. "Workload distribution":
+ * task parallelism of input, GPU control and output). h_raw: raw layout,
+ * h_vis: vis layout, h_delay_begin/h_delay_end: [N] double, h_bandpass: [N][C]
+ * or NULL, h_gains: [N][P] complex or NULL, all host memory; h_raw and h_vis
+ * should be page-locked (cudaHostAlloc / cudaHostRegister) for the copies to
+ * overlap. Asynchronous: `stream` waits for the whole pipeline, so
+ * synchronising `stream` makes h_vis valid; the host inputs must stay
+ * unchanged until then. Uses its own streams, so it is not capturable.
+ * FX_ERR_INVALID if the handle was created with host_chunk_subbands = 0. */
+fx_status fx_process_host(fx_handle *h, const void *h_raw, const double *h_delay_begin,
+                          const double *h_delay_end, const float *h_bandpass, const float *h_gains,
+                          float *h_vis, fx_stream stream);
 
 /* ---- differentiation form ------------------------------------------------
  * With the delay held constant over the block (tau_begin = tau_end = tau) the

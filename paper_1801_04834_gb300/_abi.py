@@ -31,7 +31,8 @@ class fx_params(ctypes.Structure):
                 ("sample_rate_hz", ctypes.c_double),
                 ("h_subband_centre_hz", ctypes.POINTER(ctypes.c_double)),
                 ("h_taps", ctypes.POINTER(ctypes.c_float)),
-                ("operand_scale", ctypes.c_float), ("flags", ctypes.c_uint)]
+                ("operand_scale", ctypes.c_float), ("flags", ctypes.c_uint),
+                ("host_chunk_subbands", ctypes.c_int)]
 
 
 class fx_sizes(ctypes.Structure):
@@ -53,6 +54,7 @@ SIGNATURES = {
     "fx_correct": (I, [P, P, P, P, P, P, P, P]),
     "fx_correlate": (I, [P, P, P, P]),
     "fx_channelize_correct": (I, [P, P, P, P, P, P, P, P]),
+    "fx_process_host": (I, [P, P, P, P, P, P, P, P]),
     "fx_poll_status": (I, [P, ctypes.POINTER(ctypes.c_int)]),
     "fx_apply_gains": (I, [P, P, P, P, P, P]),
     "fx_batch_create": (I, [P, I, I, ctypes.c_float, ctypes.POINTER(P)]),

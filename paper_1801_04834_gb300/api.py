@@ -30,7 +30,8 @@ class Correlator:
 
     def __init__(self, n_stations: int, n_subbands: int, n_channels: int, n_spectra: int,
                  taps, centres, n_taps: int = 16, fmt: int = FX_CI16, precision: int = FX_F32,
-                 sample_rate_hz: float = SAMPLE_RATE_HZ, operand_scale: float = 0.0, device=None):
+                 sample_rate_hz: float = SAMPLE_RATE_HZ, operand_scale: float = 0.0, device=None,
+                 host_chunk_subbands: int = 0):
         self.lib = _abi.load()
         if device is not None:
             torch.cuda.set_device(device)
@@ -53,6 +54,7 @@ class Correlator:
         p.h_taps = taps.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         p.operand_scale = operand_scale
         p.flags = 0
+        p.host_chunk_subbands = host_chunk_subbands
         h = ctypes.c_void_p()
         check(self.lib.fx_create(ctypes.byref(p), ctypes.byref(h)), "fx_create")
         self.handle = h
@@ -94,6 +96,37 @@ class Correlator:
         if t.numel() * t.element_size() != nbytes:
             raise ValueError(f"{name} has {t.numel() * t.element_size()} bytes, expected {nbytes}")
         return ctypes.c_void_p(t.data_ptr())
+
+    def _host(self, t, name, dtype, nbytes, optional=False):
+        if t is None and optional:
+            return None
+        if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+            raise TypeError(f"{name} must be a CPU torch tensor")
+        if t.dtype != dtype or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+        if t.numel() * t.element_size() != nbytes:
+            raise ValueError(f"{name} has {t.numel() * t.element_size()} bytes, expected {nbytes}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def process_host(self, raw, delay_begin, delay_end, bandpass=None, gains=None, out=None, stream=None):
+        """fx_process_host: host raw block in, host visibilities out (page-locked
+        CPU tensors for overlap), pipelined over subband chunks. Returns `out`
+        after synchronising `stream`."""
+        rdt = torch.int16 if self.fmt == FX_CI16 else torch.int8
+        if out is None:
+            out = torch.empty(self.vis_shape(), dtype=torch.float32, pin_memory=True)
+        N, C = self.N, self.C
+        s = torch.cuda.current_stream() if stream is None else stream
+        check(self.lib.fx_process_host(
+            self.handle, self._host(raw, "raw", rdt, self.sizes.raw_bytes),
+            self._host(delay_begin, "delay_begin", torch.float64, 8 * N),
+            self._host(delay_end, "delay_end", torch.float64, 8 * N),
+            self._host(bandpass, "bandpass", torch.float32, 4 * N * C, optional=True),
+            self._host(gains, "gains", torch.float32, 16 * N, optional=True),
+            self._host(out, "vis", torch.float32, self.sizes.vis_bytes), ctypes.c_void_p(s.cuda_stream)),
+            "fx_process_host")
+        s.synchronize()
+        return out
 
     def _opt(self, t, name, dtype, nbytes):
         return None if t is None else self._dev(t, name, dtype, nbytes)

@@ -66,6 +66,7 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
     if (!p.h_subband_centre_hz) return fail(FX_ERR_INVALID, "h_subband_centre_hz is NULL");
     if (!p.h_taps) return fail(FX_ERR_INVALID, "h_taps is NULL");
     if ((p.flags & ~FX_FLAG_TEST_NO_LOADS) != 0) return fail(FX_ERR_INVALID, "unknown flags 0x%x", p.flags);
+    if (p.host_chunk_subbands < 0) return fail(FX_ERR_INVALID, "host_chunk_subbands must be >= 0");
     float scale = p.operand_scale == 0.f ? 1.f : p.operand_scale;
     if (!is_pow2(scale)) return fail(FX_ERR_INVALID, "operand_scale must be a power of two");
     if (p.precision == FX_F32 && scale != 1.f)
@@ -128,6 +129,7 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
                       cudaMemcpyHostToDevice));
     FX_TRY(cudaMemcpy(h->d_xf32_tiles, tiles.data(), sizeof(int2) * ntiles, cudaMemcpyHostToDevice));
     FX_TRY(cudaMemset(h->d_status, 0, sizeof(int) * 4));
+    if (p.host_chunk_subbands > 0) FX_TRY(fxi::pipe_create(*h, p.host_chunk_subbands));
 #undef FX_TRY
     *out = h;
     g_err[0] = 0;
@@ -145,6 +147,7 @@ extern "C" void fx_destroy(fx_handle *h)
     cudaFree(h->d_status);
     cudaFree(h->d_xf32_tiles);
     cudaFree(h->d_adj_partial);
+    fxi::pipe_destroy(*h);
     delete h;
 }
 
@@ -236,6 +239,25 @@ extern "C" fx_status fx_channelize_correct(fx_handle *h, const void *d_raw, cons
     if (e == cudaSuccess)
         e = fxi::launch_channelize_correct(*h, d_raw, d_bandpass, reinterpret_cast<const float2 *>(d_gains), d_corr, s);
     return after_launch(e, who);
+}
+
+extern "C" fx_status fx_process_host(fx_handle *h, const void *h_raw, const double *h_delay_begin,
+                                     const double *h_delay_end, const float *h_bandpass, const float *h_gains,
+                                     float *h_vis, fx_stream stream)
+{
+    const char *who = "fx_process_host";
+    fx_status st = check_handle(h, who);
+    if (st) return st;
+    if (!h->pipe) return fail(FX_ERR_INVALID, "%s: handle was created with host_chunk_subbands = 0", who);
+    if (!h_raw || !h_vis || !h_delay_begin || !h_delay_end) return fail(FX_ERR_INVALID, "%s: NULL buffer", who);
+    if (h->p.precision != FX_F32) {
+        int rl, stg;
+        unsigned sb;
+        if (!fxi::xtc_plan(*h, &rl, &stg, &sb)) return fail(FX_ERR_UNSUPPORTED, "%s: no tensor-core plan", who);
+    }
+    return after_launch(fxi::pipe_run(*h, h_raw, h_delay_begin, h_delay_end, h_bandpass, h_gains, h_vis,
+                                      (cudaStream_t)stream),
+                        who);
 }
 
 extern "C" fx_status fx_poll_status(fx_handle *h, int *code)

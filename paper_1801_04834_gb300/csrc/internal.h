@@ -27,6 +27,8 @@ struct Handle {
     int2 *d_xf32_tiles = nullptr;      // tile list of the FP32 correlator
     int xf32_ntiles = 0;
     double *d_adj_partial = nullptr;   // [adjoint CTAs][I][3] per-CTA gradient sums
+    // host pipeline (fx_process_host), when host_chunk_subbands > 0
+    struct HostPipe *pipe = nullptr;
     int num_sms = 0;
     long long tc_timeout_cycles = 0;   // budget of every bounded device-side wait
     int tc_test_no_tma = 0;            // failure-detection test hook (FX_FLAG_TEST_NO_LOADS)
@@ -53,6 +55,12 @@ cudaError_t launch_correct_f32_noalloc(int N, int SB, int C, int S, double fs, c
 // xcorr_f32.cu
 int xf32_build_tiles(int N, int2 *host_tiles /* may be null: count only */);
 cudaError_t launch_xcorr_f32(const Handle &h, const float2 *corr, float2 *vis, cudaStream_t st);
+
+// host_pipeline.cu
+cudaError_t pipe_create(Handle &h, int chunk);
+void pipe_destroy(Handle &h);
+cudaError_t pipe_run(Handle &h, const void *h_raw, const double *h_tb, const double *h_te, const float *h_bp,
+                     const float *h_gains, float *h_vis, cudaStream_t st);
 
 // adjoint.cu
 int adjoint_blocks(const Handle &h);
