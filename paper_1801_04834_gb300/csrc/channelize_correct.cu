@@ -43,7 +43,7 @@ template <int C, typename TIn>
 constexpr size_t fused_smem_bytes()
 {
     using Cfg = PpfCfg<C>;
-    return ppf_smem_bytes<C, TIn>() + (size_t)kRound * Cfg::NPC * C * sizeof(float2)   // phasors
+    return ppf_smem_bytes<C, TIn>() + (size_t)kRound * (Cfg::NPC * C + 8) * sizeof(float2)   // phasors
            + (size_t)Cfg::NPC * kPols * C * sizeof(float2);                              // bandpass x gain
 }
 
@@ -65,6 +65,9 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
     constexpr int ROW_BYTES = C * kPols * (int)sizeof(TIn);
     constexpr int BUF_BYTES = kRound * NPC * ROW_BYTES;
     constexpr int IC = NPC * kPols;                 // inputs of this CTA
+    constexpr int SROW = kRound * IC + 2;           // staging row per channel (16-byte pad)
+    constexpr int PHROW = NPC * C + 8;              // phasor row per spectrum (padded)
+    static_assert(C * SROW <= Cfg::NTR * ROW, "staging fits in the FFT buffer");
     static_assert(ROW_BYTES % 16 == 0, "rows must be whole 16-byte chunks");
 
     extern __shared__ __align__(16) unsigned char smem[];
@@ -72,7 +75,7 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
     unsigned char *inbuf = smem + C * sizeof(float2);
     float2 *u = reinterpret_cast<float2 *>(inbuf + 2 * BUF_BYTES);
     float2 *ph = u + Cfg::NTR * ROW;                // [kRound][NPC][C]
-    float2 *bg = ph + kRound * NPC * C;             // [NPC][P][C]
+    float2 *bg = ph + kRound * PHROW;               // [NPC][P][C]
 
     const int tid = threadIdx.x;
     const int sb = blockIdx.z;
@@ -164,37 +167,42 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
             r = fmaf(-kq, 1.9353071795864769e-3f, r);
             float sn, cs;
             __sincosf(r, &sn, &cs);
-            ph[j * OWN + own_nc] = make_float2(cs, sn);
+            ph[j * PHROW + own_nc] = make_float2(cs, sn);
         }
         __syncthreads();
         if (b + 2 < nrounds) stage(b & 1, s0 + T - 1 + (b + 2) * kRound, kRound);
         cp_async_commit();
 
-        // ---- FFT pass 1 ----
+        // ---- FFT pass 1 (all inputs read before the transposed writes) ----
+        float2 y[Cfg::FFT_ITERS][R];
+#pragma unroll
+        for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
+            const int task = it * NT + tid;
+            const float2 *row = u + (task / R) * ROW;
+#pragma unroll
+            for (int n1 = 0; n1 < R; ++n1) y[it][n1] = row[R * n1 + task % R];
+        }
+        __syncthreads();
 #pragma unroll
         for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
             const int task = it * NT + tid;
             const int tr = task / R, n2 = task % R;
             float2 *row = u + tr * ROW;
-            float2 v[R];
+            fft_reg<R>(y[it]);
 #pragma unroll
-            for (int n1 = 0; n1 < R; ++n1) v[n1] = row[R * n1 + n2];
-            fft_reg<R>(v);
+            for (int k1 = 1; k1 < R; ++k1) y[it][k1] = cmul(y[it][k1], tw[n2 * k1]);
 #pragma unroll
-            for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], tw[n2 * k1]);
-#pragma unroll
-            for (int k1 = 0; k1 < R; ++k1) row[R * k1 + n2] = v[k1];
+            for (int k1 = 0; k1 < R; ++k1) row[(R + 1) * k1 + n2] = y[it][k1];
         }
         __syncthreads();
         // ---- FFT pass 2 + correction, results held in registers ----
-        float2 y[Cfg::FFT_ITERS][R];
 #pragma unroll
         for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
             const int task = it * NT + tid;
             const int tr = task / R, k1 = task % R;
             const float2 *row = u + tr * ROW;
 #pragma unroll
-            for (int n2 = 0; n2 < R; ++n2) y[it][n2] = row[R * k1 + n2];
+            for (int n2 = 0; n2 < R; ++n2) y[it][n2] = row[(R + 1) * k1 + n2];
             fft_reg<R>(y[it]);
             const int j = tr % kRound;
             const int pp = (tr / kRound) % kPols;
@@ -202,12 +210,12 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
 #pragma unroll
             for (int k2 = 0; k2 < R; ++k2) {
                 const int kout = k1 + R * ((k2 + R / 2) % R);
-                const float2 w = cmul(bg[(tnl * kPols + pp) * C + kout], ph[j * OWN + tnl * C + kout]);
+                const float2 w = cmul(bg[(tnl * kPols + pp) * C + kout], ph[j * PHROW + tnl * C + kout]);
                 y[it][k2] = cmul(y[it][k2], w);
             }
         }
         __syncthreads();                             // every read of u is done
-        // ---- stage the corrected round in u, in the output's order ----
+        // ---- stage the corrected round in u, in the output's order (padded rows) ----
 #pragma unroll
         for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
             const int task = it * NT + tid;
@@ -218,9 +226,9 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
             for (int k2 = 0; k2 < R; ++k2) {
                 const int kout = k1 + R * ((k2 + R / 2) % R);
                 if constexpr (OUT == 1)
-                    u[(kout * kRound + j) * IC + il] = y[it][k2];     // [C][16][IC]
+                    u[kout * SROW + j * IC + il] = y[it][k2];        // [C][16][IC] + pad
                 else
-                    u[(kout * IC + il) * kRound + j] = y[it][k2];     // [C][IC][16]
+                    u[kout * SROW + il * kRound + j] = y[it][k2];    // [C][IC][16] + pad
             }
         }
         __syncthreads();
@@ -235,8 +243,8 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
                 const int s = sr + j;
                 const int i = 2 * n0 + 2 * ip;        // = input index of pol 0 of station n0 + ip
                 if (s < S && i < I) {
-                    const float2 a0 = u[(kout * kRound + j) * IC + 2 * ip];
-                    const float2 a1 = u[(kout * kRound + j) * IC + 2 * ip + 1];
+                    const float4 a = *reinterpret_cast<const float4 *>(u + kout * SROW + j * IC + 2 * ip);
+                    const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
                     *reinterpret_cast<float4 *>(out + (((long long)sb * C + kout) * S + s) * I + i) =
                         make_float4(a0.x, a0.y, a1.x, a1.y);
                 }
@@ -249,7 +257,7 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
                 const int il = e % IC, kout = e / IC;
                 const int i = 2 * n0 + il;
                 if (i >= I) continue;
-                const float2 *src = u + (kout * IC + il) * kRound;
+                const float2 *src = u + kout * SROW + il * kRound;
                 unsigned short re[kRound], im[kRound], rl[kRound], iml[kRound];
 #pragma unroll
                 for (int j = 0; j < kRound; ++j) {

@@ -118,19 +118,27 @@ ppf_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *
         cp_async_commit();
 
         // ---- FFT pass 1: R-point FFTs over n1 (stride R), times W_C^(n2 k1) ----
+        // inputs of every task are read before any output is written, because
+        // the outputs go to other positions (row k1 of length R + 1)
+        float2 v1[Cfg::FFT_ITERS][R];
+#pragma unroll
+        for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
+            const int task = it * NT + tid;
+            const float2 *row = u + (task / R) * ROW;
+#pragma unroll
+            for (int n1 = 0; n1 < R; ++n1) v1[it][n1] = row[R * n1 + task % R];
+        }
+        __syncthreads();
 #pragma unroll
         for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
             const int task = it * NT + tid;
             const int tr = task / R, n2 = task % R;
             float2 *row = u + tr * ROW;
-            float2 v[R];
+            fft_reg<R>(v1[it]);
 #pragma unroll
-            for (int n1 = 0; n1 < R; ++n1) v[n1] = row[R * n1 + n2];
-            fft_reg<R>(v);
+            for (int k1 = 1; k1 < R; ++k1) v1[it][k1] = cmul(v1[it][k1], tw[n2 * k1]);
 #pragma unroll
-            for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], tw[n2 * k1]);
-#pragma unroll
-            for (int k1 = 0; k1 < R; ++k1) row[R * k1 + n2] = v[k1];
+            for (int k1 = 0; k1 < R; ++k1) row[(R + 1) * k1 + n2] = v1[it][k1];
         }
         __syncthreads();
         // ---- FFT pass 2: R-point FFTs over n2, X[k1 + R k2] ----
@@ -141,7 +149,7 @@ ppf_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *
             const float2 *row = u + tr * ROW;
             float2 v[R];
 #pragma unroll
-            for (int n2 = 0; n2 < R; ++n2) v[n2] = row[R * k1 + n2];
+            for (int n2 = 0; n2 < R; ++n2) v[n2] = row[(R + 1) * k1 + n2];
             fft_reg<R>(v);
             const int j = tr % kRound;
             const int pp = (tr / kRound) % kPols;

@@ -17,8 +17,9 @@ struct PpfCfg {
     static constexpr int R = (C == 16) ? 4 : (C == 64) ? 8 : 16;  // C = R * R
     static constexpr int NPC = (C * kPols >= 256) ? 1 : 256 / (C * kPols);  // stations per CTA
     static constexpr int NT = NPC * C * kPols;                    // threads per CTA
-    static constexpr int PAD = (R == 4) ? 4 : 8;                  // float2 pad per smem row
-    static constexpr int ROW = C + PAD;
+    // smem row of one transform: C + R float2, which holds the pass-1 output
+    // as R rows of R + 1 (the odd row length keeps pass-2 reads conflict free)
+    static constexpr int ROW = R * (R + 1);
     static constexpr int NTR = NPC * kPols * kRound;              // transforms per round
     static constexpr int FFT_ITERS = NTR * R / NT;
     static_assert(R * R == C, "C must be a square of R");

@@ -67,19 +67,28 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
     const int nch = (int)(ch_end - ch_first);
     const int nthr = blockDim.x;
 
+    // element v = (cl * KC + s) * row4 + x; the thread's first (x, cl*KC + s) is
+    // found once and advanced by nthr with a carry (no division per element)
+    const int x_first = tid % row4, r_first = tid / row4;
+    const int dx = nthr % row4, dr = nthr / row4;
     auto load_chunk = [&](int stage, int s0) {
         float4 *dst0 = sm + stage * stage_f4;
-        const int per_ch = kKC * row4;
-        for (int v = tid; v < nch * per_ch; v += nthr) {
-            const int x = v % row4;                // station entry in global order
-            const int s = (v / row4) % kKC;
-            const int cl = v / per_ch;
+        const int total = nch * kKC * row4;
+        int x = x_first, rr = r_first;
+        for (int v = tid; v < total; v += nthr) {
+            const int s = rr % kKC, cl = rr / kKC;      // kKC is a power of two
             const long long gch = ch_first + cl;
             const bool ok = (2 * x < I) && (s0 + s < S);
             const float2 *src = corr;
             if (ok) src = corr + (gch * S + s0 + s) * (long long)I + 2 * x;
             const int xs = (x & 1) * half + (x >> 1);   // [even stations][odd stations]
-            cp_async16(dst0 + (cl * kKC + s) * row4 + xs, src, ok ? 16 : 0);
+            cp_async16(dst0 + rr * row4 + xs, src, ok ? 16 : 0);
+            x += dx;
+            rr += dr;
+            if (x >= row4) {
+                x -= row4;
+                ++rr;
+            }
         }
     };
 
