@@ -53,6 +53,9 @@ WORKLOADS = {
     "lofar16_fp32_small": dict(N=64, SB=8, C=64, S=3072, T=16, fmt=0, precision=0, sigma=100.0,
                                ntones=3, ripple=True, seed_index=1,
                                desc="LOFAR 16-bit FP32 path on 8 subbands (profiling size, ~4 GB)"),
+    "lofar8_fp16_small": dict(N=64, SB=16, C=256, S=768, T=16, fmt=1, precision=1, sigma=20.0,
+                              ntones=1, ripple=False, seed_index=2,
+                              desc="LOFAR 8-bit FP16 X-stage on 16 subbands (profiling size, ~2.5 GB)"),
     "tiny_fp32": dict(N=8, SB=1, C=64, S=768, T=16, fmt=0, precision=0, sigma=100.0,
                       ntones=1, ripple=False, seed_index=0,
                       desc="8 stations x 2 pols, 1 subband, 64 channels, 768 spectra"),

@@ -119,9 +119,10 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
     const int own_n = min(n0 + own_nc / C, N - 1), own_k = own_nc % C;
     const float2 pst = phase[((long long)sb * N + own_n) * C + own_k];   // (phi0, step)
 
-    float h[T];
+    // taps duplicated into (h, h) pairs: one packed FMA filters re and im
+    float2 h[T];
 #pragma unroll
-    for (int k = 0; k < T; ++k) h[k] = taps[k * C + c];
+    for (int k = 0; k < T; ++k) h[k] = make_float2(taps[k * C + c], taps[k * C + c]);
 
     stage(1, s0, T - 1);
     cp_async_commit();
@@ -151,9 +152,7 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < T; ++k) {
-                const float2 x = win[(j + k) % T];
-                acc.x = fmaf(h[k], x.x, acc.x);
-                acc.y = fmaf(h[k], x.y, acc.y);
+                acc = __ffma2_rn(h[k], win[(j + k) % T], acc);
             }
             u[((nl * kPols + p) * kRound + j) * ROW + c] = acc;
         }

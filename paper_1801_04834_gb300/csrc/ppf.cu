@@ -75,9 +75,10 @@ ppf_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *
     const int nl = tid / (kPols * C);
 
     for (int i = tid; i < C; i += NT) tw[i] = twiddle[i];
-    float h[T];
+    // taps duplicated into (h, h) pairs: one packed FMA filters re and im
+    float2 h[T];
 #pragma unroll
-    for (int k = 0; k < T; ++k) h[k] = taps[k * C + c];
+    for (int k = 0; k < T; ++k) h[k] = make_float2(taps[k * C + c], taps[k * C + c]);
 
     // warm-up rows (FIR history) into buffer 1, first round into buffer 0
     stage(1, s0, T - 1);
@@ -107,9 +108,7 @@ ppf_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < T; ++k) {
-                const float2 x = win[(j + k) % T];
-                acc.x = fmaf(h[k], x.x, acc.x);
-                acc.y = fmaf(h[k], x.y, acc.y);
+                acc = __ffma2_rn(h[k], win[(j + k) % T], acc);
             }
             u[((nl * kPols + p) * kRound + j) * ROW + c] = acc;
         }
