@@ -26,7 +26,7 @@
  *
  * Layouts (row-major; N stations, P = 2 polarisations, I = N*P inputs with
  * input index i = n*P + p, SB subbands, C channels, T taps, S spectra):
- *   raw   [SB][N][L][P]      complex int16 or int8, L = (S + T - 1) * C samples
+ *   raw   [SB][N][L][P]      complex int16, int8 or int4, L = (S + T - 1) * C samples
  *   chan  [SB][N][P][S][C]   complex float
  *   corr  FX_F32:            [SB][C][S][I] complex float
  *         FX_F16, FX_BF16:   [SB][C][2][I_pad][S_pad] half / bfloat16,
@@ -62,7 +62,10 @@ typedef enum {
     FX_ERR_UNSUPPORTED = -5  /* valid request this build does not implement */
 } fx_status;
 
-typedef enum { FX_CI16 = 0, FX_CI8 = 1 } fx_format;
+/* Complex sample formats of the station data. FX_CI4 (the 4-bit mode): one
+ * byte per complex sample, real part in the high nibble and imaginary part
+ * in the low nibble, each two's complement in [-8, 7]. */
+typedef enum { FX_CI16 = 0, FX_CI8 = 1, FX_CI4 = 2 } fx_format;
 
 /* Arithmetic type of the corrected samples and of the X-stage operands. The
  * FIR and FFT always run in FP32; the X-stage always accumulates in FP32. */

@@ -30,7 +30,9 @@
  *            XX, XY, YX, YY (index 2p + q), V = sum_s Y_ip conj(Y_jq)
  *
  * Layouts (row-major, complex = two doubles re, im unless stated):
- *   raw   [SB][N][L][P] complex int16 or int8, L = (S + T - 1) * C
+ *   raw   [SB][N][L][P] complex int16, int8 or int4, L = (S + T - 1) * C;
+ *         int4: one byte per complex sample, real part in the high nibble,
+ *         imaginary part in the low nibble, each two's complement in [-8, 7]
  *   chan  [SB][N][P][S][C]      corr [SB][C][S][N][P]      vis [SB][C][B][4]
  */
 #include <math.h>
@@ -43,13 +45,18 @@
 
 #define FXO_CI16 0
 #define FXO_CI8 1
+#define FXO_CI4 2
 
 static const double TWO_PI = 6.283185307179586476925286766559;
 
 static double raw_component(const void *raw, int fmt, size_t idx)
 {
     if (fmt == FXO_CI16) return (double)((const int16_t *)raw)[idx];
-    return (double)((const int8_t *)raw)[idx];
+    if (fmt == FXO_CI8) return (double)((const int8_t *)raw)[idx];
+    /* int4: component idx of the complex sample in byte idx / 2 */
+    const unsigned byte = ((const uint8_t *)raw)[idx / 2];
+    const unsigned nib = (idx % 2 == 0) ? (byte >> 4) : (byte & 15u);
+    return (nib >= 8) ? (double)nib - 16.0 : (double)nib;
 }
 
 /* Polyphase filter bank (Sec. "Hardware requirements and design priorities";
@@ -59,7 +66,7 @@ static double raw_component(const void *raw, int fmt, size_t idx)
 int fxo_channelize(int fmt, const void *raw, int SB, int N, int P, int C, int T, int S,
                    const double *taps, double *chan)
 {
-    if (fmt != FXO_CI16 && fmt != FXO_CI8) return -1;
+    if (fmt != FXO_CI16 && fmt != FXO_CI8 && fmt != FXO_CI4) return -1;
     const size_t L = (size_t)(S + T - 1) * C;
     /* exact twiddle table: angle depends only on (c*m mod C) */
     double *wre = malloc(sizeof(double) * C), *wim = malloc(sizeof(double) * C);

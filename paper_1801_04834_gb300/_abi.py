@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfx_gb300.so")
 
 FX_OK, FX_ERR_INVALID, FX_ERR_CUDA, FX_ERR_NOMEM, FX_ERR_TIMEOUT, FX_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
-FX_CI16, FX_CI8 = 0, 1
+FX_CI16, FX_CI8, FX_CI4 = 0, 1, 2
 FX_F32, FX_F16, FX_BF16, FX_F16_SPLIT = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "FX_OK", -1: "FX_ERR_INVALID", -2: "FX_ERR_CUDA", -3: "FX_ERR_NOMEM",

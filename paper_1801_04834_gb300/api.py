@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import FX_CI8, FX_CI16, FX_F16, FX_F16_SPLIT, FX_F32, check
+from ._abi import FX_CI4, FX_CI8, FX_CI16, FX_F16, FX_F16_SPLIT, FX_F32, check
 
 SAMPLE_RATE_HZ = 195312.5
 
@@ -66,7 +66,11 @@ class Correlator:
 
     # -- shapes -----------------------------------------------------------
     def raw_shape(self):
-        return (self.SB, self.N, (self.S + self.T - 1) * self.C, 2, 2)
+        # int16/int8: trailing (re, im); int4: one packed byte per complex sample
+        return (self.SB, self.N, (self.S + self.T - 1) * self.C, 2, 1 if self.fmt == FX_CI4 else 2)
+
+    def raw_dtype(self):
+        return {FX_CI16: torch.int16, FX_CI8: torch.int8, FX_CI4: torch.uint8}[self.fmt]
 
     def chan_shape(self):
         return (self.SB, self.N, 2, self.S, self.C, 2)
@@ -112,7 +116,7 @@ class Correlator:
         """fx_process_host: host raw block in, host visibilities out (page-locked
         CPU tensors for overlap), pipelined over subband chunks. Returns `out`
         after synchronising `stream`."""
-        rdt = torch.int16 if self.fmt == FX_CI16 else torch.int8
+        rdt = self.raw_dtype()
         if out is None:
             out = torch.empty(self.vis_shape(), dtype=torch.float32, pin_memory=True)
         N, C = self.N, self.C
@@ -133,7 +137,7 @@ class Correlator:
 
     # -- entry points -----------------------------------------------------
     def channelize(self, raw: torch.Tensor, out: torch.Tensor | None = None, stream=None):
-        rdt = torch.int16 if self.fmt == FX_CI16 else torch.int8
+        rdt = self.raw_dtype()
         if out is None:
             out = torch.empty(self.chan_shape(), dtype=torch.float32, device=self.device)
         check(self.lib.fx_channelize(self.handle, self._dev(raw, "raw", rdt, self.sizes.raw_bytes),
@@ -158,7 +162,7 @@ class Correlator:
     def channelize_correct(self, raw, delay_begin, delay_end, bandpass=None, gains=None, out=None,
                            stream=None):
         """fx_channelize + fx_correct in one pass (no channelised intermediate)."""
-        rdt = torch.int16 if self.fmt == FX_CI16 else torch.int8
+        rdt = self.raw_dtype()
         if out is None:
             out = torch.empty(self.corr_shape(), dtype=self.corr_dtype(), device=self.device)
         N, C = self.N, self.C

@@ -65,7 +65,9 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
     constexpr int ROW_BYTES = C * kPols * (int)sizeof(TIn);
     constexpr int BUF_BYTES = kRound * NPC * ROW_BYTES;
     constexpr int IC = NPC * kPols;                 // inputs of this CTA
-    constexpr int SROW = kRound * IC + 2;           // staging row per channel (16-byte pad)
+    // staging: FP32 out [C][16][IC] with a 16-byte pad per channel; planar out
+    // [C][IC][17] (odd rows, so the read-out of 16 spectra per input is conflict free)
+    constexpr int SROW = (OUT == 1) ? kRound * IC + 2 : IC * (kRound + 1);
     constexpr int PHROW = NPC * C + 8;              // phasor row per spectrum (padded)
     static_assert(C * SROW <= Cfg::NTR * ROW, "staging fits in the FFT buffer");
     static_assert(ROW_BYTES % 16 == 0, "rows must be whole 16-byte chunks");
@@ -227,7 +229,7 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
                 if constexpr (OUT == 1)
                     u[kout * SROW + j * IC + il] = y[it][k2];        // [C][16][IC] + pad
                 else
-                    u[kout * SROW + il * kRound + j] = y[it][k2];    // [C][IC][16] + pad
+                    u[kout * SROW + il * (kRound + 1) + j] = y[it][k2];   // [C][IC][17]
             }
         }
         __syncthreads();
@@ -256,7 +258,7 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
                 const int il = e % IC, kout = e / IC;
                 const int i = 2 * n0 + il;
                 if (i >= I) continue;
-                const float2 *src = u + kout * SROW + il * kRound;
+                const float2 *src = u + kout * SROW + il * (kRound + 1);
                 unsigned short re[kRound], im[kRound], rl[kRound], iml[kRound];
 #pragma unroll
                 for (int j = 0; j < kRound; ++j) {
@@ -380,7 +382,8 @@ cudaError_t launch_channelize_correct(const Handle &h, const void *raw, const fl
                                       void *corr, cudaStream_t st)
 {
     if (h.p.format == FX_CI16) return launch_fmt<short2>(h, raw, corr, bandpass, gains, st);
-    return launch_fmt<char2>(h, raw, corr, bandpass, gains, st);
+    if (h.p.format == FX_CI8) return launch_fmt<char2>(h, raw, corr, bandpass, gains, st);
+    return launch_fmt<ppf::ci4_t>(h, raw, corr, bandpass, gains, st);
 }
 
 }  // namespace fxi

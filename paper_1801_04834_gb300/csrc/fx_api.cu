@@ -59,7 +59,8 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
     if (!fxi::ppf_supported(p.n_channels, p.n_taps))
         return fail(FX_ERR_UNSUPPORTED, "channels %d / taps %d not built (C in {16,64,256}, T in {4,8,16})",
                     p.n_channels, p.n_taps);
-    if (p.format != FX_CI16 && p.format != FX_CI8) return fail(FX_ERR_INVALID, "bad format %d", p.format);
+    if (p.format != FX_CI16 && p.format != FX_CI8 && p.format != FX_CI4)
+        return fail(FX_ERR_INVALID, "bad format %d", p.format);
     if (p.precision < FX_F32 || p.precision > FX_F16_SPLIT)
         return fail(FX_ERR_INVALID, "bad precision %d", p.precision);
     if (!(p.sample_rate_hz > 0)) return fail(FX_ERR_INVALID, "sample_rate_hz must be > 0");
@@ -157,7 +158,7 @@ extern "C" fx_status fx_query_sizes(const fx_handle *h, fx_sizes *o)
     const fx_params &p = h->p;
     const size_t SB = p.n_subbands, N = p.n_stations, C = p.n_channels, S = p.n_spectra;
     const size_t L = (S + p.n_taps - 1) * C;
-    const size_t bpc = p.format == FX_CI16 ? 4 : 2;
+    const size_t bpc = p.format == FX_CI16 ? 4 : p.format == FX_CI8 ? 2 : 1;   // bytes per complex sample
     o->raw_bytes = SB * N * L * 2 * bpc;
     o->chan_bytes = SB * N * 2 * S * C * sizeof(float2);
     switch (p.precision) {

@@ -75,7 +75,7 @@ cudaError_t pipe_create(Handle &h, int chunk)
     const int SB = h.p.n_subbands, N = h.p.n_stations, C = h.p.n_channels;
     P->chunk = chunk < SB ? chunk : SB;
     const size_t L = (size_t)(h.p.n_spectra + h.p.n_taps - 1) * C;
-    P->raw_sb = (size_t)N * L * 2 * (h.p.format == FX_CI16 ? 4 : 2);
+    P->raw_sb = (size_t)N * L * 2 * (h.p.format == FX_CI16 ? 4 : h.p.format == FX_CI8 ? 2 : 1);
     P->corr_sb = corr_bytes_per_subband(h);
     P->vis_sb = (size_t)C * h.B * 4 * sizeof(float2);
     cudaError_t e = cudaSuccess;

@@ -216,7 +216,8 @@ bool ppf_supported(int C, int T)
 cudaError_t launch_ppf(const Handle &h, const void *raw, float2 *chan, cudaStream_t st)
 {
     if (h.p.format == FX_CI16) return launch_fmt<short2>(h, raw, chan, st);
-    return launch_fmt<char2>(h, raw, chan, st);
+    if (h.p.format == FX_CI8) return launch_fmt<char2>(h, raw, chan, st);
+    return launch_fmt<ci4_t>(h, raw, chan, st);
 }
 
 }  // namespace fxi

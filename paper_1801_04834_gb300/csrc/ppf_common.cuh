@@ -38,6 +38,16 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 __device__ __forceinline__ float2 to_f2(short2 v) { return make_float2((float)v.x, (float)v.y); }
 __device__ __forceinline__ float2 to_f2(char2 v) { return make_float2((float)v.x, (float)v.y); }
+// 4-bit complex sample: real part in the high nibble, imaginary part in the low
+// nibble, two's complement (sign-extended by arithmetic shifts of a signed byte)
+struct ci4_t {
+    unsigned char v;
+};
+__device__ __forceinline__ float2 to_f2(ci4_t s)
+{
+    const int b = (int)(signed char)s.v;
+    return make_float2((float)(b >> 4), (float)((int)(signed char)(s.v << 4) >> 4));
+}
 
 // twiddles + double-buffered raw rows + one round of FFT rows
 template <int C, typename TIn>

@@ -30,9 +30,18 @@ import numpy as np
 SAMPLE_RATE_HZ = 195312.5          # one LOFAR subband, complex sampled
 BASE_SEED = 180104834              # seeds are BASE_SEED + workload index
 
-CI16, CI8 = 0, 1                   # sample formats (match include/fx.h)
-FORMAT_MAX = {CI16: 32767, CI8: 127}
-FORMAT_DTYPE = {CI16: np.int16, CI8: np.int8}
+CI16, CI8, CI4 = 0, 1, 2           # sample formats (match include/fx.h)
+FORMAT_MAX = {CI16: 32767, CI8: 127, CI4: 7}
+FORMAT_DTYPE = {CI16: np.int16, CI8: np.int8, CI4: np.uint8}
+FORMAT_LAST = {CI16: 2, CI8: 2, CI4: 1}   # trailing axis: (re, im), or one packed byte
+
+
+def pack_ci4(re: np.ndarray, im: np.ndarray) -> np.ndarray:
+    """Complex 4-bit samples, one byte each: real part in the high nibble,
+    imaginary part in the low nibble, two's complement."""
+    r = np.asarray(re).astype(np.int64) & 15
+    i = np.asarray(im).astype(np.int64) & 15
+    return ((r << 4) | i).astype(np.uint8)
 
 
 def kaiser_sinc_taps(n_taps: int, n_channels: int, beta: float = 9.0) -> np.ndarray:
@@ -117,10 +126,13 @@ def tone_samples(tone: Tone, n_channels: int, f_sub: float, n_stations: int,
 
 
 def quantise(z: np.ndarray, fmt: int) -> np.ndarray:
-    """Round half to even and clip to the format's range; returns [..., 2]."""
+    """Round half to even and clip to the format's range; returns [..., 2]
+    (int16/int8) or [..., 1] packed bytes (int4)."""
     lim = FORMAT_MAX[fmt]
     re = np.clip(np.rint(z.real), -lim, lim)
     im = np.clip(np.rint(z.imag), -lim, lim)
+    if fmt == CI4:
+        return pack_ci4(re, im)[..., None]
     return np.stack([re, im], axis=-1).astype(FORMAT_DTYPE[fmt])
 
 
@@ -134,7 +146,7 @@ def make_block(seed: int, fmt: int, n_subbands: int, n_stations: int, n_channels
     C, T, S = n_channels, n_taps, n_spectra
     L = (S + T - 1) * C
     centres = subband_centres(n_subbands, centre_hz)
-    raw = np.empty((n_subbands, n_stations, L, n_pols, 2), FORMAT_DTYPE[fmt])
+    raw = np.empty((n_subbands, n_stations, L, n_pols, FORMAT_LAST[fmt]), FORMAT_DTYPE[fmt])
     for sb in range(n_subbands):
         z = (rng.standard_normal((n_stations, L, n_pols))
              + 1j * rng.standard_normal((n_stations, L, n_pols))) * sigma
@@ -184,10 +196,10 @@ def make_raw_torch(seed: int, fmt: int, n_subbands: int, n_stations: int, n_chan
     import torch
     C, T, S, N, P = n_channels, n_taps, n_spectra, n_stations, n_pols
     L = (S + T - 1) * C
-    dt = torch.int16 if fmt == CI16 else torch.int8
+    dt = {CI16: torch.int16, CI8: torch.int8, CI4: torch.uint8}[fmt]
     lim = FORMAT_MAX[fmt]
     if out is None:
-        out = torch.empty((n_subbands, N, L, P, 2), dtype=dt, device=device)
+        out = torch.empty((n_subbands, N, L, P, FORMAT_LAST[fmt]), dtype=dt, device=device)
     g = torch.Generator(device=device)
     centres = subband_centres(n_subbands, centre_hz)
     t = torch.arange(L, device=device, dtype=torch.int64)
@@ -213,5 +225,10 @@ def make_raw_torch(seed: int, fmt: int, n_subbands: int, n_stations: int, n_chan
             z[..., 0] += (a * torch.cos(ph)).to(torch.float32)
             z[..., 1] += (a * torch.sin(ph)).to(torch.float32)
             del ph
-        out[sb] = torch.clamp(torch.round(z), -lim, lim).to(dt)
+        q = torch.clamp(torch.round(z), -lim, lim)
+        if fmt == CI4:
+            qi = q.to(torch.int32) & 15
+            out[sb] = ((qi[..., 0] << 4) | qi[..., 1]).to(torch.uint8)[..., None]
+        else:
+            out[sb] = q.to(dt)
     return out

@@ -306,6 +306,34 @@ def pin_fx_chain(o):
     assert np.array_equal(v, v2)
 
 
+def pin_ci4_decode(o):
+    """int4 samples: hand-decoded bytes through an impulse (0x9A = -7 - 6i,
+    0x7F = 7 - i, 0x80 = -8, 0x05 = 5i, 0xFF = -1 - i), and random 4-bit values
+    give exactly the channelisation of the same values stored as int16."""
+    rng = np.random.default_rng(12)
+    C, T, S = 16, 4, 6
+    L = (S + T - 1) * C
+    taps = _random_taps(rng, T, C)
+    for byte, val in [(0x9A, -7 - 6j), (0x7F, 7 - 1j), (0x80, -8 + 0j), (0x05, 5j), (0xFF, -1 - 1j)]:
+        s0, c0 = 5, 3
+        raw = np.zeros((1, 1, L, 2, 1), np.uint8)
+        raw[0, 0, s0 * C + c0, 1, 0] = byte
+        chan = cplx(o.channelize(synth.CI4, raw, T, C, S, taps))[0, 0, 1]      # pol 1
+        for s in range(S):
+            k = s0 - s
+            exp = val * taps[k * C + c0] if 0 <= k < T else 0.0
+            m = (0 - C // 2) % C            # output channel 0 holds DFT bin -C/2
+            got = chan[s, 0] * np.exp(2j * np.pi * c0 * m / C)
+            assert abs(got - exp) < 1e-12, (hex(byte), s)
+    re = rng.integers(-7, 8, size=(2, 3, L, 2))
+    im = rng.integers(-7, 8, size=(2, 3, L, 2))
+    raw4 = synth.pack_ci4(re, im)[..., None]
+    raw16 = np.stack([re, im], -1).astype(np.int16)
+    a = o.channelize(synth.CI4, raw4, T, C, S, taps)
+    b = o.channelize(synth.CI16, raw16, T, C, S, taps)
+    assert np.array_equal(a, b), "int4 and int16 encodings of the same samples"
+
+
 ALL_PINS = [pin_fir_delta, pin_tone, pin_dft_vs_numpy, pin_point_source, pin_bandpass,
             pin_delay_ramp, pin_correlate_einsum, pin_hermitian, pin_linearity,
-            pin_gradient_fd, pin_gradient_truth, pin_fx_chain]
+            pin_gradient_fd, pin_gradient_truth, pin_fx_chain, pin_ci4_decode]

@@ -80,3 +80,25 @@ def test_fused_end_to_end_vs_oracle(precision, bound):
         vis = c.correlate(c.channelize_correct(torch.from_numpy(blk.raw).cuda(), t, t))
         e = per_subband_rel(vis.cpu().numpy().astype(np.float64), ref)
         assert np.all(e < bound), (precision, N, e)
+
+
+@pytest.mark.parametrize("precision,bound", [(0, 1e-5), (1, 5e-3)])
+@pytest.mark.parametrize("C,S", [(16, 40), (64, 33), (256, 17)])
+def test_ci4_end_to_end(precision, bound, C, S):
+    """4-bit mode: packed int4 samples through the two-call and fused paths
+    against the FP64 oracle (which decodes the nibbles itself)."""
+    N, SB = 6, 2
+    rng = np.random.default_rng(C + S)
+    tau = rng.uniform(-5e-6, 5e-6, N)
+    tone = synth.Tone(amp=3.0, channel=int(rng.integers(1, C)), delays=tau)
+    blk = synth.make_block(77 + C, synth.CI4, SB, N, C, S, sigma=2.5, tones=[tone])
+    ref = oracle.fx(blk.fmt, blk.raw, 16, C, S, blk.taps, FS, blk.centres, tau, tau)
+    c = make_corr(blk, precision=precision)
+    raw = torch.from_numpy(blk.raw).cuda()
+    t = d(tau, torch.float64)
+    chan_ref = oracle.channelize(blk.fmt, blk.raw, 16, C, S, blk.taps)
+    chan = c.channelize(raw).cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(chan - chan_ref) / np.linalg.norm(chan_ref) < 2e-6
+    for vis in (c.correlate(c.correct(c.channelize(raw), t, t)), c.correlate(c.channelize_correct(raw, t, t))):
+        e = per_subband_rel(vis.cpu().numpy().astype(np.float64), ref)
+        assert np.all(e < bound), e

@@ -10,6 +10,9 @@ import oracle_pins
 
 # (name, original text, mutated text)
 MUTANTS = [
+    ("ci4_nibble_order", "const unsigned nib = (idx % 2 == 0) ? (byte >> 4) : (byte & 15u);",
+     "const unsigned nib = (idx % 2 == 0) ? (byte & 15u) : (byte >> 4);"),
+    ("ci4_sign", "return (nib >= 8) ? (double)nib - 16.0 : (double)nib;", "return (double)nib;"),
     ("dft_sign", "wim[r] = -sin(TWO_PI * r / C);", "wim[r] = sin(TWO_PI * r / C);"),
     ("fir_tap_order", "const double h = taps[(size_t)k * C + c];",
      "const double h = taps[(size_t)(T - 1 - k) * C + c];"),
