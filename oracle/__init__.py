@@ -53,7 +53,9 @@ class Oracle:
         L = ctypes.CDLL(path)
         P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
         L.fxo_channelize.argtypes = [I, P, I, I, I, I, I, I, P, P]
-        L.fxo_correct.argtypes = [P, I, I, I, I, I, D, P, P, P, P, P, P]
+        L.fxo_correct.argtypes = [P, I, I, I, I, I, D, P, P, P, P, P, P, P]
+        L.fxo_baseline_counts.argtypes = [P, I, I, P]
+        L.fxo_baseline_counts.restype = I
         L.fxo_correlate.argtypes = [P, I, I, I, I, I, P]
         L.fxo_fx.argtypes = [I, P, I, I, I, I, I, I, P, D, P, P, P, P, P, P]
         L.fxo_vjp.argtypes = [P, I, I, I, I, I, D, P, P, P, P, P, P, P]
@@ -80,15 +82,22 @@ class Oracle:
                                            n_spectra, _ptr(_f64(taps)), _ptr(out)), "channelize")
         return out
 
-    def correct(self, chan, fs, centres, tau_begin, tau_end, bandpass=None, gains=None):
-        """chan [SB][N][P][S][C][2] -> corr [SB][C][S][N][P][2]."""
+    def correct(self, chan, fs, centres, tau_begin, tau_end, bandpass=None, gains=None, flags=None):
+        """chan [SB][N][P][S][C][2] -> corr [SB][C][S][N][P][2]; flags [N][S] weights."""
         chan = _f64(chan)
         SB, N, P, S, C, _ = chan.shape
         out = np.empty((SB, C, S, N, P, 2))
         self._check(self._L.fxo_correct(_ptr(chan), SB, N, P, C, S, fs, _ptr(_f64(centres)),
                                         _ptr(_f64(tau_begin)), _ptr(_f64(tau_end)),
-                                        _ptr(_f64(bandpass)), _ptr(_f64(gains)), _ptr(out)),
+                                        _ptr(_f64(bandpass)), _ptr(_f64(gains)), _ptr(_f64(flags)),
+                                        _ptr(out)),
                     "correct")
+        return out
+
+    def baseline_counts(self, flags, N, S):
+        """counts [B]: spectra valid for both stations of each baseline."""
+        out = np.empty(N * (N + 1) // 2)
+        self._check(self._L.fxo_baseline_counts(_ptr(_f64(flags)), N, S, _ptr(out)), "baseline_counts")
         return out
 
     def correlate(self, corr):
@@ -144,6 +153,10 @@ def channelize(*a, **k):
 
 def correct(*a, **k):
     return default().correct(*a, **k)
+
+
+def baseline_counts(*a, **k):
+    return default().baseline_counts(*a, **k)
 
 
 def correlate(*a, **k):

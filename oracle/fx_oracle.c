@@ -128,10 +128,11 @@ static double channel_freq(const double *centres, int sb, int k, int C, double f
 /* Fine delay compensation + bandpass correction (Sec. "Signal processing with
  * GPU kernels": phase from begin/end delays, linear in time within a block),
  * with the transposing write-back to the per-channel, all-stations layout.
- * bandpass [N][C] real or NULL (= 1); gains [N][P] complex or NULL (= 1). */
+ * bandpass [N][C] real or NULL (= 1); gains [N][P] complex or NULL (= 1);
+ * flags [N][S] real weights marking lost data (0 = lost) or NULL (= 1). */
 int fxo_correct(const double *chan, int SB, int N, int P, int C, int S, double fs,
                 const double *centres, const double *tau_begin, const double *tau_end,
-                const double *bandpass, const double *gains, double *corr)
+                const double *bandpass, const double *gains, const double *flags, double *corr)
 {
 #pragma omp parallel for collapse(2) schedule(dynamic)
     for (int sb = 0; sb < SB; ++sb)
@@ -151,8 +152,10 @@ int fxo_correct(const double *chan, int SB, int N, int P, int C, int S, double f
                         const double xgre = x[0] * gre - x[1] * gim;
                         const double xgim = x[0] * gim + x[1] * gre;
                         double *y = corr + (((((size_t)sb * C + k) * S + s) * N + n) * P + p) * 2;
-                        y[0] = xgre * rre - xgim * rim;
-                        y[1] = xgre * rim + xgim * rre;
+                        /* lost-data weight of (station, spectrum), 1 when no flags */
+                        const double w = flags ? flags[(size_t)n * S + s] : 1.0;
+                        y[0] = (xgre * rre - xgim * rim) * w;
+                        y[1] = (xgre * rim + xgim * rre) * w;
                     }
                 }
         }
@@ -190,6 +193,20 @@ int fxo_correlate(const double *corr, int SB, int N, int P, int C, int S, double
     return 0;
 }
 
+/* Number of spectra that count for each baseline when per-(station, spectrum)
+ * weights flag lost data: counts[b(i,j)] = sum_s w_i(s) w_j(s), i <= j. */
+int fxo_baseline_counts(const double *flags, int N, int S, double *counts)
+{
+    for (int j = 0; j < N; ++j)
+        for (int i = 0; i <= j; ++i) {
+            double c = 0.0;
+            for (int s = 0; s < S; ++s)
+                c += (flags ? flags[(size_t)i * S + s] : 1.0) * (flags ? flags[(size_t)j * S + s] : 1.0);
+            counts[(size_t)j * (j + 1) / 2 + i] = c;
+        }
+    return 0;
+}
+
 /* Whole hot path, raw samples to visibilities. Scratch is allocated here. */
 int fxo_fx(int fmt, const void *raw, int SB, int N, int P, int C, int T, int S,
            const double *taps, double fs, const double *centres, const double *tau_begin,
@@ -200,7 +217,7 @@ int fxo_fx(int fmt, const void *raw, int SB, int N, int P, int C, int T, int S,
     int rc = (!chan || !corr) ? -3 : 0;
     if (!rc) rc = fxo_channelize(fmt, raw, SB, N, P, C, T, S, taps, chan);
     if (!rc) rc = fxo_correct(chan, SB, N, P, C, S, fs, centres, tau_begin, tau_end,
-                              bandpass, gains, corr);
+                              bandpass, gains, NULL, corr);
     if (!rc) rc = fxo_correlate(corr, SB, N, P, C, S, vis);
     free(chan);
     free(corr);

@@ -20,6 +20,8 @@ What pins what:
   linearity          sums over two halves of the block add up to the whole
   gradient_fd        vjp vs central finite differences of the loss
   gradient_truth     zero loss and zero gradient at the true parameters
+  ci4_decode         4-bit nibble decoding (hand-decoded bytes, int16 equivalence)
+  flags              lost-data weights and per-baseline valid-spectrum counts
 """
 from __future__ import annotations
 
@@ -334,6 +336,36 @@ def pin_ci4_decode(o):
     assert np.array_equal(a, b), "int4 and int16 encodings of the same samples"
 
 
+def pin_flags(o):
+    """Lost-data weights: a station flagged for the whole block leaves exactly
+    zero on all its baselines; flagging the second part of the block for every
+    station gives the correlation of the first part alone (constant delays);
+    counts are S for unflagged baselines and the overlap of valid spectra."""
+    rng = np.random.default_rng(13)
+    SB, N, C, S, S1 = 2, 4, 8, 10, 6
+    chan = synth.noise(14, (SB, N, 2, S, C, 2))
+    centres = synth.subband_centres(SB)
+    tau = rng.uniform(-5e-6, 5e-6, N)
+    w = np.ones((N, S))
+    w[2] = 0.0
+    v = cplx(o.correlate(o.correct(chan, FS, centres, tau, tau, flags=w)))
+    for j in range(N):
+        for i in range(j + 1):
+            if 2 in (i, j):
+                assert np.all(v[:, :, bidx(i, j)] == 0), "flagged station must vanish"
+    w2 = np.ones((N, S))
+    w2[:, S1:] = 0.0
+    va = o.correlate(o.correct(chan, FS, centres, tau, tau, flags=w2))
+    vb = o.correlate(o.correct(np.ascontiguousarray(chan[:, :, :, :S1]), FS, centres, tau, tau))
+    assert np.allclose(va, vb, rtol=1e-12, atol=1e-12), "flags = shorter block"
+    cnt = o.baseline_counts(w2, N, S)
+    assert np.all(cnt == S1)
+    assert np.all(o.baseline_counts(None, N, S) == S)
+    w3 = np.ones((N, S)); w3[0, :3] = 0.0; w3[1, 5:] = 0.0
+    c3 = o.baseline_counts(w3, N, S)
+    assert c3[bidx(0, 1)] == 2 and c3[bidx(0, 0)] == S - 3 and c3[bidx(1, 1)] == 5 and c3[bidx(2, 3)] == S
+
+
 ALL_PINS = [pin_fir_delta, pin_tone, pin_dft_vs_numpy, pin_point_source, pin_bandpass,
             pin_delay_ramp, pin_correlate_einsum, pin_hermitian, pin_linearity,
-            pin_gradient_fd, pin_gradient_truth, pin_fx_chain, pin_ci4_decode]
+            pin_gradient_fd, pin_gradient_truth, pin_fx_chain, pin_ci4_decode, pin_flags]

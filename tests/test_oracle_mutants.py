@@ -13,6 +13,9 @@ MUTANTS = [
     ("ci4_nibble_order", "const unsigned nib = (idx % 2 == 0) ? (byte >> 4) : (byte & 15u);",
      "const unsigned nib = (idx % 2 == 0) ? (byte & 15u) : (byte >> 4);"),
     ("ci4_sign", "return (nib >= 8) ? (double)nib - 16.0 : (double)nib;", "return (double)nib;"),
+    ("flags_ignored", "const double w = flags ? flags[(size_t)n * S + s] : 1.0;", "const double w = 1.0;"),
+    ("counts_one_station", "c += (flags ? flags[(size_t)i * S + s] : 1.0) * (flags ? flags[(size_t)j * S + s] : 1.0);",
+     "c += (flags ? flags[(size_t)i * S + s] : 1.0);"),
     ("dft_sign", "wim[r] = -sin(TWO_PI * r / C);", "wim[r] = sin(TWO_PI * r / C);"),
     ("fir_tap_order", "const double h = taps[(size_t)k * C + c];",
      "const double h = taps[(size_t)(T - 1 - k) * C + c];"),
