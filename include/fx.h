@@ -90,7 +90,14 @@ typedef struct {
     int host_chunk_subbands;     /* > 0: allocate the double-buffered workspaces of
                                     fx_process_host for chunks of this many
                                     subbands; 0: no host pipeline */
+    int max_coarse_shift;        /* with FX_FLAG_STREAMING: largest integer-sample
+                                    coarse delay per station (>= 0) */
 } fx_params;
+
+/* Streaming form (fx_stream_block): the handle keeps the FIR history of every
+ * (subband, station) and room for coarse delays of up to max_coarse_shift
+ * samples, and allocates one assembled raw block as workspace. */
+#define FX_FLAG_STREAMING 0x1u
 
 /* Failure-detection test hook: the tensor-core X-stage issues no operand
  * loads, so its consumer waits run out after about a millisecond; the call
@@ -189,6 +196,38 @@ fx_status fx_correlate(fx_handle *h, const void *d_corr, float *d_vis, fx_stream
 fx_status fx_process_host(fx_handle *h, const void *h_raw, const double *h_delay_begin,
                           const double *h_delay_end, const float *h_bandpass, const float *h_gains,
                           float *h_vis, fx_stream stream);
+
+/* ---- streaming form --------------------------------------------------------
+ * Consecutive blocks of a continuous stream (Sec. "Signal processing with GPU
+ * kernels": FIR history is carried to the next block; Sec. "Software
+ * architecture": the transpose stage applies the coarse, whole-sample delay
+ * with a circular buffer and lost data is recorded as metadata).
+ *
+ * Each call brings S*C new samples per (subband, station, pol):
+ * d_new [SB][N][S*C][P] in the handle's format. Station n is read d_n samples
+ * late (integer coarse delay, d_coarse_shift [N] int in [0, max_coarse_shift],
+ * NULL = 0): the block's spectra use its stream samples
+ * [t0 - (T-1)*C - d_n, t0 + S*C - d_n), t0 = first new sample, with samples
+ * before the first call taken as zero. The residual (fine) delay is the
+ * caller's d_delay_begin/d_delay_end, corrected as in fx_correct. d_flags
+ * [N][S] float weights (0 = lost spectrum, NULL = all 1) multiply the
+ * corrected samples. Writes d_corr (corr layout of the precision), d_vis (vis
+ * layout; NULL = skip the X-stage) and d_counts [B] float = sum_s w_i(s) w_j(s)
+ * per baseline (NULL = skip). A coarse shift outside [0, max] is clamped and
+ * recorded: fx_poll_status then returns FX_ERR_INVALID. The history advances
+ * by one block per call: each call also switches host-side state (which of
+ * two history buffers is current), so it must not be captured in a CUDA
+ * graph, and consecutive calls must be ordered (same stream, or events).
+ * Allocation free; buffers are caller-owned and only read (d_new, delays,
+ * bandpass, gains, flags, shifts) or written (d_corr, d_vis, d_counts).
+ * Handle needs FX_FLAG_STREAMING; otherwise FX_ERR_INVALID. */
+fx_status fx_stream_block(fx_handle *h, const void *d_new, const int *d_coarse_shift,
+                          const double *d_delay_begin, const double *d_delay_end,
+                          const float *d_bandpass, const float *d_gains, const float *d_flags,
+                          void *d_corr, float *d_vis, float *d_counts, fx_stream stream);
+
+/* Zero the streaming history (the stream restarts with zeros before it). */
+fx_status fx_stream_reset(fx_handle *h, fx_stream stream);
 
 /* ---- differentiation form ------------------------------------------------
  * With the delay held constant over the block (tau_begin = tau_end = tau) the

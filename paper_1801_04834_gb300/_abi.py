@@ -32,7 +32,7 @@ class fx_params(ctypes.Structure):
                 ("h_subband_centre_hz", ctypes.POINTER(ctypes.c_double)),
                 ("h_taps", ctypes.POINTER(ctypes.c_float)),
                 ("operand_scale", ctypes.c_float), ("flags", ctypes.c_uint),
-                ("host_chunk_subbands", ctypes.c_int)]
+                ("host_chunk_subbands", ctypes.c_int), ("max_coarse_shift", ctypes.c_int)]
 
 
 class fx_sizes(ctypes.Structure):
@@ -55,6 +55,8 @@ SIGNATURES = {
     "fx_correlate": (I, [P, P, P, P]),
     "fx_channelize_correct": (I, [P, P, P, P, P, P, P, P]),
     "fx_process_host": (I, [P, P, P, P, P, P, P, P]),
+    "fx_stream_block": (I, [P, P, P, P, P, P, P, P, P, P, P, P]),
+    "fx_stream_reset": (I, [P, P]),
     "fx_poll_status": (I, [P, ctypes.POINTER(ctypes.c_int)]),
     "fx_apply_gains": (I, [P, P, P, P, P, P]),
     "fx_batch_create": (I, [P, I, I, ctypes.c_float, ctypes.POINTER(P)]),
@@ -68,6 +70,7 @@ SIGNATURES = {
 }
 FX_NOALLOC_MAX_PHASES = 1 << 20
 FX_FLAG_TEST_NO_LOADS = 0x80000000
+FX_FLAG_STREAMING = 0x1
 
 _lib = None
 

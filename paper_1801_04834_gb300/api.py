@@ -31,7 +31,7 @@ class Correlator:
     def __init__(self, n_stations: int, n_subbands: int, n_channels: int, n_spectra: int,
                  taps, centres, n_taps: int = 16, fmt: int = FX_CI16, precision: int = FX_F32,
                  sample_rate_hz: float = SAMPLE_RATE_HZ, operand_scale: float = 0.0, device=None,
-                 host_chunk_subbands: int = 0):
+                 host_chunk_subbands: int = 0, streaming: bool = False, max_coarse_shift: int = 0):
         self.lib = _abi.load()
         if device is not None:
             torch.cuda.set_device(device)
@@ -53,8 +53,9 @@ class Correlator:
         p.h_subband_centre_hz = centres.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         p.h_taps = taps.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         p.operand_scale = operand_scale
-        p.flags = 0
+        p.flags = _abi.FX_FLAG_STREAMING if streaming else 0
         p.host_chunk_subbands = host_chunk_subbands
+        p.max_coarse_shift = max_coarse_shift
         h = ctypes.c_void_p()
         check(self.lib.fx_create(ctypes.byref(p), ctypes.byref(h)), "fx_create")
         self.handle = h
@@ -71,6 +72,10 @@ class Correlator:
 
     def raw_dtype(self):
         return {FX_CI16: torch.int16, FX_CI8: torch.int8, FX_CI4: torch.uint8}[self.fmt]
+
+    def new_shape(self):
+        # streaming: the S*C new samples of one block per (subband, station, pol)
+        return (self.SB, self.N, self.S * self.C, 2, 1 if self.fmt == FX_CI4 else 2)
 
     def chan_shape(self):
         return (self.SB, self.N, 2, self.S, self.C, 2)
@@ -184,6 +189,36 @@ class Correlator:
                                     self._dev(out, "vis", torch.float32, self.sizes.vis_bytes),
                                     _stream_ptr(stream)), "fx_correlate")
         return out
+
+    # -- streaming form ---------------------------------------------------------
+    def stream_block(self, new, delay_begin, delay_end, coarse_shift=None, bandpass=None, gains=None,
+                     flags=None, corr=None, vis=None, counts=None, want_vis=True, stream=None):
+        """fx_stream_block: one block of a continuous stream (history kept in
+        the handle). Returns (corr, vis or None, counts or None); counts are
+        produced when `flags` is given or `counts` is passed."""
+        N, C, S = self.N, self.C, self.S
+        new_bytes = int(np.prod(self.new_shape())) * (2 if self.fmt == FX_CI16 else 1)
+        if corr is None:
+            corr = torch.empty(self.corr_shape(), dtype=self.corr_dtype(), device=self.device)
+        if vis is None and want_vis:
+            vis = torch.empty(self.vis_shape(), dtype=torch.float32, device=self.device)
+        if counts is None and flags is not None:
+            counts = torch.empty(self.B, dtype=torch.float32, device=self.device)
+        check(self.lib.fx_stream_block(
+            self.handle, self._dev(new, "new", self.raw_dtype(), new_bytes),
+            self._opt(coarse_shift, "coarse_shift", torch.int32, 4 * N),
+            self._dev(delay_begin, "delay_begin", torch.float64, 8 * N),
+            self._dev(delay_end, "delay_end", torch.float64, 8 * N),
+            self._opt(bandpass, "bandpass", torch.float32, 4 * N * C),
+            self._opt(gains, "gains", torch.float32, 16 * N),
+            self._opt(flags, "flags", torch.float32, 4 * N * S),
+            self._dev(corr, "corr", self.corr_dtype(), self.sizes.corr_bytes),
+            self._opt(vis, "vis", torch.float32, self.sizes.vis_bytes),
+            self._opt(counts, "counts", torch.float32, 4 * self.B), _stream_ptr(stream)), "fx_stream_block")
+        return corr, vis, counts
+
+    def stream_reset(self, stream=None):
+        check(self.lib.fx_stream_reset(self.handle, _stream_ptr(stream)), "fx_stream_reset")
 
     # -- differentiation form -------------------------------------------------
     def raw_vis(self, chan, bandpass=None, stream=None):

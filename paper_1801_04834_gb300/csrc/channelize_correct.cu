@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(PpfCfg<C>::NT, PpfCfg<C>::NT >= 512 ? 1 : 2)
 ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const float *__restrict__ taps,
                    const float2 *__restrict__ twiddle, const float2 *__restrict__ phase,
                    const float *__restrict__ bandpass, const float2 *__restrict__ gains, int N, int S, int I_pad,
-                   int S_pad, float scale, int rounds_per_cta)
+                   int S_pad, float scale, int rounds_per_cta, const float *__restrict__ flags)
 {
     using Cfg = PpfCfg<C>;
     constexpr int R = Cfg::R, NPC = Cfg::NPC, NT = Cfg::NT, ROW = Cfg::ROW;
@@ -208,10 +208,15 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
             const int j = tr % kRound;
             const int pp = (tr / kRound) % kPols;
             const int tnl = tr / (kRound * kPols);
+            // lost-data weight of (station, spectrum); 1 without flags
+            float fw = 1.f;
+            if (flags && n0 + tnl < N && sr + j < S) fw = flags[(long long)(n0 + tnl) * S + sr + j];
 #pragma unroll
             for (int k2 = 0; k2 < R; ++k2) {
                 const int kout = k1 + R * ((k2 + R / 2) % R);
-                const float2 w = cmul(bg[(tnl * kPols + pp) * C + kout], ph[j * PHROW + tnl * C + kout]);
+                float2 w = cmul(bg[(tnl * kPols + pp) * C + kout], ph[j * PHROW + tnl * C + kout]);
+                w.x *= fw;
+                w.y *= fw;
                 y[it][k2] = cmul(y[it][k2], w);
             }
         }
@@ -312,6 +317,7 @@ __global__ void planar_pad_kernel(unsigned short *__restrict__ corr, long long n
 
 template <int C, int T, typename TIn, int OUT>
 cudaError_t launch_t(const Handle &h, const void *raw, void *corr, const float *bandpass, const float2 *gains,
+                     const float *flags,
                      cudaStream_t st)
 {
     using Cfg = PpfCfg<C>;
@@ -328,7 +334,7 @@ cudaError_t launch_t(const Handle &h, const void *raw, void *corr, const float *
     if (e != cudaSuccess) return e;
     const float scale = (OUT == 1) ? 1.f : h.operand_scale;
     kern<<<grid, Cfg::NT, smem, st>>>(reinterpret_cast<const TIn *>(raw), corr, h.d_taps, h.d_twiddle, h.d_phase,
-                                      bandpass, gains, N, S, h.I_pad, h.S_pad, scale, rpc);
+                                      bandpass, gains, N, S, h.I_pad, h.S_pad, scale, rpc, flags);
     e = cudaGetLastError();
     if (e != cudaSuccess || OUT == 1) return e;
     const int S16 = rounds_total * kRound;
@@ -343,35 +349,35 @@ cudaError_t launch_t(const Handle &h, const void *raw, void *corr, const float *
 }
 
 template <int C, int T, typename TIn>
-cudaError_t launch_out(const Handle &h, const void *raw, void *corr, const float *bp, const float2 *g, cudaStream_t st)
+cudaError_t launch_out(const Handle &h, const void *raw, void *corr, const float *bp, const float2 *g, const float *fl, cudaStream_t st)
 {
     switch (h.p.precision) {
-    case FX_F32: return launch_t<C, T, TIn, 1>(h, raw, corr, bp, g, st);
-    case FX_F16: return launch_t<C, T, TIn, 2>(h, raw, corr, bp, g, st);
-    case FX_BF16: return launch_t<C, T, TIn, 3>(h, raw, corr, bp, g, st);
-    default: return launch_t<C, T, TIn, 4>(h, raw, corr, bp, g, st);
+    case FX_F32: return launch_t<C, T, TIn, 1>(h, raw, corr, bp, g, fl, st);
+    case FX_F16: return launch_t<C, T, TIn, 2>(h, raw, corr, bp, g, fl, st);
+    case FX_BF16: return launch_t<C, T, TIn, 3>(h, raw, corr, bp, g, fl, st);
+    default: return launch_t<C, T, TIn, 4>(h, raw, corr, bp, g, fl, st);
     }
 }
 
 template <int C, typename TIn>
 cudaError_t launch_taps(const Handle &h, const void *raw, void *corr, const float *bp, const float2 *g,
-                        cudaStream_t st)
+                        const float *fl, cudaStream_t st)
 {
     switch (h.p.n_taps) {
-    case 4: return launch_out<C, 4, TIn>(h, raw, corr, bp, g, st);
-    case 8: return launch_out<C, 8, TIn>(h, raw, corr, bp, g, st);
-    case 16: return launch_out<C, 16, TIn>(h, raw, corr, bp, g, st);
+    case 4: return launch_out<C, 4, TIn>(h, raw, corr, bp, g, fl, st);
+    case 8: return launch_out<C, 8, TIn>(h, raw, corr, bp, g, fl, st);
+    case 16: return launch_out<C, 16, TIn>(h, raw, corr, bp, g, fl, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <typename TIn>
-cudaError_t launch_fmt(const Handle &h, const void *raw, void *corr, const float *bp, const float2 *g, cudaStream_t st)
+cudaError_t launch_fmt(const Handle &h, const void *raw, void *corr, const float *bp, const float2 *g, const float *fl, cudaStream_t st)
 {
     switch (h.p.n_channels) {
-    case 16: return launch_taps<16, TIn>(h, raw, corr, bp, g, st);
-    case 64: return launch_taps<64, TIn>(h, raw, corr, bp, g, st);
-    case 256: return launch_taps<256, TIn>(h, raw, corr, bp, g, st);
+    case 16: return launch_taps<16, TIn>(h, raw, corr, bp, g, fl, st);
+    case 64: return launch_taps<64, TIn>(h, raw, corr, bp, g, fl, st);
+    case 256: return launch_taps<256, TIn>(h, raw, corr, bp, g, fl, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -379,11 +385,11 @@ cudaError_t launch_fmt(const Handle &h, const void *raw, void *corr, const float
 }  // namespace
 
 cudaError_t launch_channelize_correct(const Handle &h, const void *raw, const float *bandpass, const float2 *gains,
-                                      void *corr, cudaStream_t st)
+                                      void *corr, cudaStream_t st, const float *flags)
 {
-    if (h.p.format == FX_CI16) return launch_fmt<short2>(h, raw, corr, bandpass, gains, st);
-    if (h.p.format == FX_CI8) return launch_fmt<char2>(h, raw, corr, bandpass, gains, st);
-    return launch_fmt<ppf::ci4_t>(h, raw, corr, bandpass, gains, st);
+    if (h.p.format == FX_CI16) return launch_fmt<short2>(h, raw, corr, bandpass, gains, flags, st);
+    if (h.p.format == FX_CI8) return launch_fmt<char2>(h, raw, corr, bandpass, gains, flags, st);
+    return launch_fmt<ppf::ci4_t>(h, raw, corr, bandpass, gains, flags, st);
 }
 
 }  // namespace fxi

@@ -66,7 +66,10 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
     if (!(p.sample_rate_hz > 0)) return fail(FX_ERR_INVALID, "sample_rate_hz must be > 0");
     if (!p.h_subband_centre_hz) return fail(FX_ERR_INVALID, "h_subband_centre_hz is NULL");
     if (!p.h_taps) return fail(FX_ERR_INVALID, "h_taps is NULL");
-    if ((p.flags & ~FX_FLAG_TEST_NO_LOADS) != 0) return fail(FX_ERR_INVALID, "unknown flags 0x%x", p.flags);
+    if ((p.flags & ~(FX_FLAG_TEST_NO_LOADS | FX_FLAG_STREAMING)) != 0)
+        return fail(FX_ERR_INVALID, "unknown flags 0x%x", p.flags);
+    if (p.max_coarse_shift < 0 || p.max_coarse_shift > (1 << 24))
+        return fail(FX_ERR_INVALID, "max_coarse_shift out of range");
     if (p.host_chunk_subbands < 0) return fail(FX_ERR_INVALID, "host_chunk_subbands must be >= 0");
     float scale = p.operand_scale == 0.f ? 1.f : p.operand_scale;
     if (!is_pow2(scale)) return fail(FX_ERR_INVALID, "operand_scale must be a power of two");
@@ -131,6 +134,16 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
     FX_TRY(cudaMemcpy(h->d_xf32_tiles, tiles.data(), sizeof(int2) * ntiles, cudaMemcpyHostToDevice));
     FX_TRY(cudaMemset(h->d_status, 0, sizeof(int) * 4));
     if (p.host_chunk_subbands > 0) FX_TRY(fxi::pipe_create(*h, p.host_chunk_subbands));
+    if (p.flags & FX_FLAG_STREAMING) {
+        h->hist_len = (T - 1) * C + p.max_coarse_shift;
+        const size_t hist_bytes = (size_t)SB * N * h->hist_len * fxi::raw_sample_bytes(*h);
+        const size_t block_bytes = (size_t)SB * N * (size_t)(p.n_spectra + T - 1) * C * fxi::raw_sample_bytes(*h);
+        FX_TRY(cudaMalloc(&h->d_hist[0], hist_bytes));
+        FX_TRY(cudaMalloc(&h->d_hist[1], hist_bytes));
+        FX_TRY(cudaMalloc(&h->d_block, block_bytes));
+        FX_TRY(cudaMemset(h->d_hist[0], 0, hist_bytes));
+        FX_TRY(cudaMemset(h->d_hist[1], 0, hist_bytes));
+    }
 #undef FX_TRY
     *out = h;
     g_err[0] = 0;
@@ -148,6 +161,9 @@ extern "C" void fx_destroy(fx_handle *h)
     cudaFree(h->d_status);
     cudaFree(h->d_xf32_tiles);
     cudaFree(h->d_adj_partial);
+    cudaFree(h->d_hist[0]);
+    cudaFree(h->d_hist[1]);
+    cudaFree(h->d_block);
     fxi::pipe_destroy(*h);
     delete h;
 }
@@ -261,6 +277,54 @@ extern "C" fx_status fx_process_host(fx_handle *h, const void *h_raw, const doub
                         who);
 }
 
+extern "C" fx_status fx_stream_reset(fx_handle *h, fx_stream stream)
+{
+    fx_status st = check_handle(h, "fx_stream_reset");
+    if (st) return st;
+    if (!h->d_block) return fail(FX_ERR_INVALID, "fx_stream_reset: handle was created without FX_FLAG_STREAMING");
+    const size_t hist_bytes =
+        (size_t)h->p.n_subbands * h->p.n_stations * h->hist_len * fxi::raw_sample_bytes(*h);
+    cudaError_t e = cudaMemsetAsync(h->d_hist[0], 0, hist_bytes, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_hist[1], 0, hist_bytes, (cudaStream_t)stream);
+    return after_launch(e, "fx_stream_reset");
+}
+
+extern "C" fx_status fx_stream_block(fx_handle *h, const void *d_new, const int *d_coarse_shift,
+                                     const double *d_delay_begin, const double *d_delay_end,
+                                     const float *d_bandpass, const float *d_gains, const float *d_flags,
+                                     void *d_corr, float *d_vis, float *d_counts, fx_stream stream)
+{
+    const char *who = "fx_stream_block";
+    fx_status st = check_handle(h, who);
+    if (st) return st;
+    if (!h->d_block) return fail(FX_ERR_INVALID, "%s: handle was created without FX_FLAG_STREAMING", who);
+    if (!d_new || !d_corr || !d_delay_begin || !d_delay_end) return fail(FX_ERR_INVALID, "%s: NULL buffer", who);
+    if (((uintptr_t)d_new & 15) || ((uintptr_t)d_corr & 15) || ((uintptr_t)d_vis & 15) ||
+        ((uintptr_t)d_coarse_shift & 3) || ((uintptr_t)d_flags & 3) || ((uintptr_t)d_counts & 3) ||
+        ((uintptr_t)d_gains & 7) || ((uintptr_t)d_bandpass & 3) || ((uintptr_t)d_delay_begin & 7) ||
+        ((uintptr_t)d_delay_end & 7))
+        return fail(FX_ERR_INVALID, "%s: misaligned buffer", who);
+    if (d_vis && h->p.precision != FX_F32) {
+        int rl, stg;
+        unsigned sb;
+        if (!fxi::xtc_plan(*h, &rl, &stg, &sb)) return fail(FX_ERR_UNSUPPORTED, "%s: no tensor-core plan", who);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = fxi::launch_stream_assemble(*h, d_new, d_coarse_shift, s);
+    if (e == cudaSuccess) e = fxi::launch_phase_table(*h, d_delay_begin, d_delay_end, s);
+    if (e == cudaSuccess)
+        e = fxi::launch_channelize_correct(*h, h->d_block, d_bandpass, reinterpret_cast<const float2 *>(d_gains),
+                                           d_corr, s, d_flags);
+    if (e == cudaSuccess && d_vis) {
+        float2 *vis = reinterpret_cast<float2 *>(d_vis);
+        e = h->p.precision == FX_F32 ? fxi::launch_xcorr_f32(*h, reinterpret_cast<const float2 *>(d_corr), vis, s)
+                                     : fxi::launch_xcorr_tc(*h, d_corr, vis, s);
+    }
+    if (e == cudaSuccess && d_counts) e = fxi::launch_baseline_counts(*h, d_flags, d_counts, s);
+    if (e == cudaSuccess) e = fxi::launch_stream_history(*h, d_new, s);
+    return after_launch(e, who);
+}
+
 extern "C" fx_status fx_poll_status(fx_handle *h, int *code)
 {
     fx_status st = check_handle(h, "fx_poll_status");
@@ -274,6 +338,7 @@ extern "C" fx_status fx_poll_status(fx_handle *h, int *code)
     if (w[0] != 0) {
         cudaMemset(h->d_status, 0, sizeof(int) * 4);
         if (code) *code = w[0];
+        if (w[0] == 5) return fail(FX_ERR_INVALID, "a coarse shift was outside [0, max_coarse_shift] and was clamped");
         return fail(FX_ERR_TIMEOUT, "device-side wait gave up (role %d, CTA %d)", w[0], w[1]);
     }
     return FX_OK;

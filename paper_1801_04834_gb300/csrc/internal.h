@@ -27,6 +27,11 @@ struct Handle {
     int2 *d_xf32_tiles = nullptr;      // tile list of the FP32 correlator
     int xf32_ntiles = 0;
     double *d_adj_partial = nullptr;   // [adjoint CTAs][I][3] per-CTA gradient sums
+    // streaming (FX_FLAG_STREAMING): FIR history ping-pong + assembled block
+    int hist_len = 0;                  // samples of history per (subband, station)
+    void *d_hist[2] = {nullptr, nullptr};
+    int hist_cur = 0;
+    void *d_block = nullptr;
     // host pipeline (fx_process_host), when host_chunk_subbands > 0
     struct HostPipe *pipe = nullptr;
     int num_sms = 0;
@@ -38,9 +43,15 @@ struct Handle {
 cudaError_t launch_ppf(const Handle &h, const void *raw, float2 *chan, cudaStream_t st);
 bool ppf_supported(int C, int T);
 
-// channelize_correct.cu
+// channelize_correct.cu (flags: [N][S] lost-data weights or null)
 cudaError_t launch_channelize_correct(const Handle &h, const void *raw, const float *bandpass, const float2 *gains,
-                                      void *corr, cudaStream_t st);
+                                      void *corr, cudaStream_t st, const float *flags = nullptr);
+
+// stream.cu
+int raw_sample_bytes(const Handle &h);   // bytes of one time sample of one station (both pols)
+cudaError_t launch_stream_assemble(const Handle &h, const void *d_new, const int *shift, cudaStream_t st);
+cudaError_t launch_stream_history(Handle &h, const void *d_new, cudaStream_t st);
+cudaError_t launch_baseline_counts(const Handle &h, const float *flags, float *counts, cudaStream_t st);
 
 // correct.cu
 cudaError_t launch_phase_table(const Handle &h, const double *tau_b, const double *tau_e,
