@@ -13,19 +13,23 @@
 // in-register FFT). After FFT pass 2 each output X(n, p, s, k) is multiplied
 // by bandpass(n, k) * gain(n, p) * exp(i phi), phi = phi0(n, k) + s * step(n, k)
 // (phi0 reduced mod 2 pi and step formed in FP64 by the phase-table kernel,
-// as in fx_correct). Per 16-spectrum round the CTA tabulates exp(i phi) for
-// its (station, channel, spectrum) triples once (both pols share them): phi
-// is reduced to [-pi, pi] in FP32 with a two-constant Cody-Waite split of
-// 2 pi and passed to __sincosf, whose absolute error on that interval is
-// about 4e-7.
+// as in fx_correct). Per 16-spectrum round the CTA tabulates the whole
+// per-sample factor w(n, p, k, s) = flag(n, s) * bandpass(n, k) * gain(n, p)
+// * exp(i phi) once: one thread per (station, channel) evaluates exp(i phi)
+// (phi reduced to [-pi, pi] in FP32 with a two-constant Cody-Waite split of
+// 2 pi, then __sincosf, absolute error about 4e-7 on that interval) and
+// multiplies in its two pols' bandpass x gain, kept in registers. FFT pass 2
+// then needs one shared load and one complex multiply per output.
 //
-// The corrected round is turned in shared memory (reusing the FFT buffer) and
-// written as
-//   FP32   [SB][C][S][I]: per (channel, spectrum) a run of 2*NPC inputs;
+// Transforms are stored spectrum-major (row j * IC + input), which keeps the
+// FIR stores and both FFT passes free of bank conflicts. Output:
+//   FP32   [SB][C][S][I]: written from the pass-2 registers; a warp store
+//          covers whole 32-byte runs of inputs of one (channel, spectrum);
 //          the grid walks station groups fastest so neighbouring CTAs fill
 //          the same lines while they are in L2;
-//   planar [SB][C][planes][I_pad][S_pad]: per (channel, plane, input) a run of
-//          16 spectra (32 bytes), FP16/BF16 (x operand_scale) or hi/lo FP16.
+//   planar [SB][C][planes][I_pad][S_pad]: turned in shared memory (reusing
+//          the FFT buffer) into per (channel, plane, input) runs of 16
+//          spectra (32 bytes), FP16/BF16 (x operand_scale) or hi/lo FP16.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -39,12 +43,16 @@ namespace {
 using namespace ppf;
 
 // OUT: 1 FP32 interleaved, 2 FP16 planar, 3 BF16 planar, 4 split FP16 planar
+// per-round factor table: [kRound][IC inputs][PHC], rows padded so that FFT
+// pass 2 (lanes = 8 or 16 consecutive channels x inputs) reads it conflict free
+template <int C>
+constexpr int fused_phc() { return C + (C == 16 ? 4 : 8); }
+
 template <int C, typename TIn>
 constexpr size_t fused_smem_bytes()
 {
     using Cfg = PpfCfg<C>;
-    return ppf_smem_bytes<C, TIn>() + (size_t)kRound * (Cfg::NPC * C + 8) * sizeof(float2)   // phasors
-           + (size_t)Cfg::NPC * kPols * C * sizeof(float2);                              // bandpass x gain
+    return ppf_smem_bytes<C, TIn>() + (size_t)kRound * Cfg::NPC * kPols * fused_phc<C>() * sizeof(float2);
 }
 
 __device__ __forceinline__ unsigned short to_bits(float x, int out)
@@ -65,19 +73,22 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
     constexpr int ROW_BYTES = C * kPols * (int)sizeof(TIn);
     constexpr int BUF_BYTES = kRound * NPC * ROW_BYTES;
     constexpr int IC = NPC * kPols;                 // inputs of this CTA
-    // staging: FP32 out [C][16][IC] with a 16-byte pad per channel; planar out
-    // [C][IC][17] (odd rows, so the read-out of 16 spectra per input is conflict free)
-    constexpr int SROW = (OUT == 1) ? kRound * IC + 2 : IC * (kRound + 1);
-    constexpr int PHROW = NPC * C + 8;              // phasor row per spectrum (padded)
-    static_assert(C * SROW <= Cfg::NTR * ROW, "staging fits in the FFT buffer");
+    // planar staging [C][IC][17] (odd rows, so the read-out of 16 spectra per
+    // input is conflict free)
+    constexpr int SROW = IC * (kRound + 1);         // planar staging row per channel
+    constexpr int PHC = fused_phc<C>();
+    constexpr int PHROW = IC * PHC;                 // factor-table row per spectrum
+    static_assert(OUT == 1 || C * SROW <= Cfg::NTR * ROW, "staging fits in the FFT buffer");
+    static_assert(NT >= 512 ? fused_smem_bytes<C, TIn>() <= 227 * 1024
+                            : 2 * (fused_smem_bytes<C, TIn>() + 1024) <= 228 * 1024,
+                  "two CTAs per SM (one at 512 threads)");
     static_assert(ROW_BYTES % 16 == 0, "rows must be whole 16-byte chunks");
 
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *tw = reinterpret_cast<float2 *>(smem);
     unsigned char *inbuf = smem + C * sizeof(float2);
     float2 *u = reinterpret_cast<float2 *>(inbuf + 2 * BUF_BYTES);
-    float2 *ph = u + Cfg::NTR * ROW;                // [kRound][NPC][C]
-    float2 *bg = ph + kRound * PHROW;               // [NPC][P][C]
+    float2 *ph = u + Cfg::NTR * ROW;                // [kRound][IC][PHC] per-sample factors
 
     const int tid = threadIdx.x;
     const int sb = blockIdx.z;
@@ -108,18 +119,19 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
     const int nl = tid / (kPols * C);
 
     for (int i = tid; i < C; i += NT) tw[i] = twiddle[i];
-    for (int i = tid; i < NPC * kPols * C; i += NT) {
-        const int k = i % C, pp = (i / C) % kPols, st = i / (kPols * C);
-        const int n = min(n0 + st, N - 1);
-        const float b = bandpass ? bandpass[(long long)n * C + k] : 1.f;
-        const float2 g = gains ? gains[n * kPols + pp] : make_float2(1.f, 0.f);
-        bg[i] = make_float2(b * g.x * scale, b * g.y * scale);
-    }
-    // phasor ownership: (station, channel) = tid mod NPC*C, spectra j = j0, j0+2, ...
+    // factor ownership: (station, channel) = tid mod NPC*C, spectra j = j0, j0+2, ...
     constexpr int OWN = NPC * C;                    // = NT / 2
     const int own_nc = tid % OWN, own_j0 = tid / OWN;
-    const int own_n = min(n0 + own_nc / C, N - 1), own_k = own_nc % C;
+    const int own_nl = own_nc / C, own_k = own_nc % C;
+    const int own_n = min(n0 + own_nl, N - 1);
     const float2 pst = phase[((long long)sb * N + own_n) * C + own_k];   // (phi0, step)
+    float2 bgr[kPols];                              // bandpass x gain x scale of both pols
+#pragma unroll
+    for (int pp = 0; pp < kPols; ++pp) {
+        const float b = bandpass ? bandpass[(long long)own_n * C + own_k] : 1.f;
+        const float2 g = gains ? gains[own_n * kPols + pp] : make_float2(1.f, 0.f);
+        bgr[pp] = make_float2(b * g.x * scale, b * g.y * scale);
+    }
 
     // taps duplicated into (h, h) pairs: one packed FMA filters re and im
     float2 h[T];
@@ -156,9 +168,9 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
             for (int k = 0; k < T; ++k) {
                 acc = __ffma2_rn(h[k], win[(j + k) % T], acc);
             }
-            u[((nl * kPols + p) * kRound + j) * ROW + c] = acc;
+            u[(j * IC + nl * kPols + p) * ROW + c] = acc;
         }
-        // ---- phasors exp(i phi) of this round ----
+        // ---- per-sample factors flag * bandpass * gain * exp(i phi) of this round ----
 #pragma unroll
         for (int q = 0; q < kRound / 2; ++q) {
             const int j = own_j0 + 2 * q;
@@ -168,7 +180,14 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
             r = fmaf(-kq, 1.9353071795864769e-3f, r);
             float sn, cs;
             __sincosf(r, &sn, &cs);
-            ph[j * PHROW + own_nc] = make_float2(cs, sn);
+            // lost-data weight of (station, spectrum); 1 without flags
+            const float fw = flags ? flags[(long long)own_n * S + min(sr + j, S - 1)] : 1.f;
+            cs *= fw;
+            sn *= fw;
+#pragma unroll
+            for (int pp = 0; pp < kPols; ++pp)
+                ph[j * PHROW + (own_nl * kPols + pp) * PHC + own_k] =
+                    make_float2(bgr[pp].x * cs - bgr[pp].y * sn, bgr[pp].x * sn + bgr[pp].y * cs);
         }
         __syncthreads();
         if (b + 2 < nrounds) stage(b & 1, s0 + T - 1 + (b + 2) * kRound, kRound);
@@ -200,62 +219,52 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
 #pragma unroll
         for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
             const int task = it * NT + tid;
-            const int tr = task / R, k1 = task % R;
+            const int tr = task / R, k1 = task % R;  // transform tr = j * IC + il
             const float2 *row = u + tr * ROW;
 #pragma unroll
             for (int n2 = 0; n2 < R; ++n2) y[it][n2] = row[(R + 1) * k1 + n2];
             fft_reg<R>(y[it]);
-            const int j = tr % kRound;
-            const int pp = (tr / kRound) % kPols;
-            const int tnl = tr / (kRound * kPols);
-            // lost-data weight of (station, spectrum); 1 without flags
-            float fw = 1.f;
-            if (flags && n0 + tnl < N && sr + j < S) fw = flags[(long long)(n0 + tnl) * S + sr + j];
+            const int j = tr / IC, il = tr % IC;
 #pragma unroll
             for (int k2 = 0; k2 < R; ++k2) {
                 const int kout = k1 + R * ((k2 + R / 2) % R);
-                float2 w = cmul(bg[(tnl * kPols + pp) * C + kout], ph[j * PHROW + tnl * C + kout]);
-                w.x *= fw;
-                w.y *= fw;
-                y[it][k2] = cmul(y[it][k2], w);
+                y[it][k2] = cmul(y[it][k2], ph[j * PHROW + il * PHC + kout]);
             }
         }
+        if constexpr (OUT == 1) {
+            // ---- write out from registers: 2*NPC consecutive inputs per (channel, spectrum) ----
+            float2 *out = reinterpret_cast<float2 *>(corr);
+#pragma unroll
+            for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
+                const int task = it * NT + tid;
+                const int tr = task / R, k1 = task % R;
+                const int s = sr + tr / IC, i = 2 * n0 + tr % IC;
+                if (s < S && i < I) {
+#pragma unroll
+                    for (int k2 = 0; k2 < R; ++k2) {
+                        const int kout = k1 + R * ((k2 + R / 2) % R);
+                        out[(((long long)sb * C + kout) * S + s) * I + i] = y[it][k2];
+                    }
+                }
+            }
+            // the next round's first barrier orders these reads of u before its FIR stores
+        } else {
         __syncthreads();                             // every read of u is done
         // ---- stage the corrected round in u, in the output's order (padded rows) ----
 #pragma unroll
         for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
             const int task = it * NT + tid;
             const int tr = task / R, k1 = task % R;
-            const int j = tr % kRound;
-            const int il = (tr / kRound) % kPols + kPols * (tr / (kRound * kPols));
+            const int j = tr / IC, il = tr % IC;
 #pragma unroll
             for (int k2 = 0; k2 < R; ++k2) {
                 const int kout = k1 + R * ((k2 + R / 2) % R);
-                if constexpr (OUT == 1)
-                    u[kout * SROW + j * IC + il] = y[it][k2];        // [C][16][IC] + pad
-                else
-                    u[kout * SROW + il * (kRound + 1) + j] = y[it][k2];   // [C][IC][17]
+                u[kout * SROW + il * (kRound + 1) + j] = y[it][k2];   // [C][IC][17]
             }
         }
         __syncthreads();
         // ---- write out ----
-        if constexpr (OUT == 1) {
-            float2 *out = reinterpret_cast<float2 *>(corr);
-            // float4 = two consecutive inputs of one (channel, spectrum)
-            for (int e = tid; e < C * kRound * (IC / 2); e += NT) {
-                const int ip = e % (IC / 2);
-                const int j = (e / (IC / 2)) % kRound;
-                const int kout = e / ((IC / 2) * kRound);
-                const int s = sr + j;
-                const int i = 2 * n0 + 2 * ip;        // = input index of pol 0 of station n0 + ip
-                if (s < S && i < I) {
-                    const float4 a = *reinterpret_cast<const float4 *>(u + kout * SROW + j * IC + 2 * ip);
-                    const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
-                    *reinterpret_cast<float4 *>(out + (((long long)sb * C + kout) * S + s) * I + i) =
-                        make_float4(a0.x, a0.y, a1.x, a1.y);
-                }
-            }
-        } else {
+        {
             constexpr int planes = (OUT == 4) ? 4 : 2;
             unsigned short *out = reinterpret_cast<unsigned short *>(corr);
             const long long pstride = (long long)I_pad * S_pad;
@@ -297,6 +306,7 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
                     put(base + 3 * pstride, iml);
                 }
             }
+        }
         }
     }
     cp_async_wait<0>();
