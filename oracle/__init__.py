@@ -59,8 +59,9 @@ class Oracle:
         L.fxo_correlate.argtypes = [P, I, I, I, I, I, P]
         L.fxo_fx.argtypes = [I, P, I, I, I, I, I, I, P, D, P, P, P, P, P, P]
         L.fxo_vjp.argtypes = [P, I, I, I, I, I, D, P, P, P, P, P, P, P]
+        L.fxo_beamform.argtypes = [P, I, I, I, I, I, D, P, I, P, P, I, I, P]
         for f in (L.fxo_channelize, L.fxo_correct, L.fxo_correlate, L.fxo_fx, L.fxo_vjp,
-                  L.fxo_threads):
+                  L.fxo_beamform, L.fxo_threads):
             f.restype = I
         self._L = L
 
@@ -132,6 +133,21 @@ class Oracle:
                                     _ptr(_f64(grad_vis)), _ptr(gg), _ptr(gt)), "vjp")
         return gg, gt
 
+    def beamform(self, corr, fs, centres, delays, weights=None, mode=0, tint=1):
+        """Coherent beams from corr [SB][C][S][N][P][2]; delays [NB][N] seconds,
+        weights [N] real. mode 0: voltages [SB][NB][C][S][4]; 1: Stokes I
+        [SB][NB][C][S/tint]; 2: Stokes IQUV [SB][NB][C][S/tint][4]."""
+        corr = _f64(corr)
+        SB, C, S, N, P, _ = corr.shape
+        delays = _f64(delays).reshape(-1, N)
+        NB = delays.shape[0]
+        shape = {0: (SB, NB, C, S, 4), 1: (SB, NB, C, S // tint), 2: (SB, NB, C, S // tint, 4)}[mode]
+        out = np.empty(shape)
+        self._check(self._L.fxo_beamform(_ptr(corr), SB, N, P, C, S, fs, _ptr(_f64(centres)), NB,
+                                         _ptr(delays), _ptr(_f64(weights)), mode, tint, _ptr(out)),
+                    "beamform")
+        return out
+
 
 _default = None
 
@@ -169,3 +185,7 @@ def fx(*a, **k):
 
 def vjp(*a, **k):
     return default().vjp(*a, **k)
+
+
+def beamform(*a, **k):
+    return default().beamform(*a, **k)

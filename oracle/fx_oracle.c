@@ -15,6 +15,8 @@
  *   fxo_correlate   explicit sum over time of Y_ip * conj(Y_jq), i <= j
  *   fxo_vjp         gradient of a real loss through correct + correlate,
  *                   by the chain rule entry by entry (constant delays)
+ *   fxo_beamform    coherent beams: per-sample phase-shifted station sum,
+ *                   then complex voltages or Stokes I / IQUV
  * OpenMP splits independent outer loops (subbands, stations, channels) across
  * host threads, as the paper's host code does over subbands (Sec. "Parallelization
  * libraries"); it does not change any arithmetic.
@@ -319,6 +321,75 @@ int fxo_vjp(const double *chan, int SB, int N, int P, int C, int S, double fs,
     }
     free(gg);
     free(gt);
+    return 0;
+}
+
+/* Coherent beamformer (Sec. "Signal processing with GPU kernels": after
+ * delay and bandpass correction each beam is steered by a phase shift and
+ * summed over antenna fields, then optionally converted to Stokes
+ * parameters). For beam b, pol p, spectrum s, channel k:
+ *   B_bp(s, k) = sum_n a_n exp(+2 pi i f_k delta[b][n]) Y_np(s, k)
+ * with delta[b][n] the beam's extra delay for station n (seconds, constant
+ * over the block), a_n a real station weight (NULL = 1) and f_k the channel's
+ * sky frequency. Output, with X = B_b0 and Y = B_b1:
+ *   mode 0  complex voltages  out [SB][NB][C][S][4] = (Re X, Im X, Re Y, Im Y)
+ *   mode 1  Stokes I          out [SB][NB][C][S/tint]
+ *   mode 2  Stokes IQUV       out [SB][NB][C][S/tint][4]
+ *           I = |X|^2 + |Y|^2, Q = |X|^2 - |Y|^2, U = 2 Re(X conj Y),
+ *           V = 2 Im(X conj Y), each summed over tint consecutive spectra.
+ * corr is the corrected block [SB][C][S][N][P]. */
+int fxo_beamform(const double *corr, int SB, int N, int P, int C, int S, double fs, const double *centres,
+                 int NB, const double *delays, const double *weights, int mode, int tint, double *out)
+{
+    if (P != 2 || NB < 1 || mode < 0 || mode > 2 || tint < 1 || S % tint != 0) return -1;
+    if (mode == 0 && tint != 1) return -1;
+    const int SO = S / tint;
+#pragma omp parallel for collapse(3) schedule(dynamic)
+    for (int sb = 0; sb < SB; ++sb)
+        for (int b = 0; b < NB; ++b)
+            for (int k = 0; k < C; ++k) {
+                const double f = channel_freq(centres, sb, k, C, fs);
+                for (int so = 0; so < SO; ++so) {
+                    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+                    for (int t = 0; t < tint; ++t) {
+                        const int s = so * tint + t;
+                        double bx[2][2] = {{0.0, 0.0}, {0.0, 0.0}};   /* [pol][re, im] */
+                        for (int n = 0; n < N; ++n) {
+                            const double a = weights ? weights[n] : 1.0;
+                            const double phi = TWO_PI * f * delays[(size_t)b * N + n];
+                            const double wre = a * cos(phi), wim = a * sin(phi);
+                            for (int p = 0; p < 2; ++p) {
+                                const double *y = corr + (((((size_t)sb * C + k) * S + s) * N + n) * P + p) * 2;
+                                bx[p][0] += wre * y[0] - wim * y[1];
+                                bx[p][1] += wre * y[1] + wim * y[0];
+                            }
+                        }
+                        if (mode == 0) {
+                            double *o = out + ((((size_t)sb * NB + b) * C + k) * S + s) * 4;
+                            o[0] = bx[0][0];
+                            o[1] = bx[0][1];
+                            o[2] = bx[1][0];
+                            o[3] = bx[1][1];
+                            continue;
+                        }
+                        const double xx = bx[0][0] * bx[0][0] + bx[0][1] * bx[0][1];
+                        const double yy = bx[1][0] * bx[1][0] + bx[1][1] * bx[1][1];
+                        /* X conj(Y) */
+                        const double cre = bx[0][0] * bx[1][0] + bx[0][1] * bx[1][1];
+                        const double cim = bx[0][1] * bx[1][0] - bx[0][0] * bx[1][1];
+                        acc[0] += xx + yy;
+                        acc[1] += xx - yy;
+                        acc[2] += 2.0 * cre;
+                        acc[3] += 2.0 * cim;
+                    }
+                    if (mode == 1) {
+                        out[(((size_t)sb * NB + b) * C + k) * SO + so] = acc[0];
+                    } else if (mode == 2) {
+                        double *o = out + ((((size_t)sb * NB + b) * C + k) * SO + so) * 4;
+                        for (int q = 0; q < 4; ++q) o[q] = acc[q];
+                    }
+                }
+            }
     return 0;
 }
 

@@ -22,6 +22,12 @@ What pins what:
   gradient_truth     zero loss and zero gradient at the true parameters
   ci4_decode         4-bit nibble decoding (hand-decoded bytes, int16 equivalence)
   flags              lost-data weights and per-baseline valid-spectrum counts
+  beam_point_source  beam steered at a plane wave sums in phase (closed form);
+                     phase-centre beam gives the closed-form array factor
+  beam_station_sum   zero delays = numpy station sum; one-hot weight = that
+                     station rotated by exp(+2 pi i f_k delay)
+  stokes             Stokes closed forms for Y = X, X = iY, Y = 0; integration
+                     = sum of per-spectrum values; I^2 >= Q^2 + U^2 + V^2
 """
 from __future__ import annotations
 
@@ -366,6 +372,96 @@ def pin_flags(o):
     assert c3[bidx(0, 1)] == 2 and c3[bidx(0, 0)] == S - 3 and c3[bidx(1, 1)] == 5 and c3[bidx(2, 3)] == S
 
 
+def _plane_wave(seed, SB, N, C, S, centres, delays0, amp=(3.0, 2.0)):
+    """corr block of a plane wave whose signal reaches station n delays0[n]
+    late: Y_np(s, k) = amp_p exp(i theta_s) exp(-2 pi i f_k delays0[n])."""
+    rng = np.random.default_rng(seed)
+    theta = rng.uniform(0, 2 * np.pi, S)
+    y = np.zeros((SB, C, S, N, 2), dtype=complex)
+    for sb in range(SB):
+        for k in range(C):
+            f = centres[sb] + (k - C / 2) * FS / C
+            for p in range(2):
+                y[sb, k, :, :, p] = amp[p] * np.exp(1j * theta)[:, None] * np.exp(-2j * np.pi * f * delays0)[None, :]
+    return np.stack([y.real, y.imag], axis=-1), theta
+
+
+def pin_beam_point_source(o):
+    """A beam steered at a plane wave adds the stations in phase: voltage
+    = amp_p exp(i theta_s) sum_n a_n exactly; a beam at the phase centre sees
+    the closed-form array factor |sum_n a_n exp(-2 pi i f_k d_n)|."""
+    SB, N, C, S = 2, 5, 8, 6
+    rng = np.random.default_rng(21)
+    centres = synth.subband_centres(SB)
+    d0 = rng.uniform(-3e-6, 3e-6, N)
+    a = rng.uniform(0.5, 1.5, N)
+    corr, theta = _plane_wave(22, SB, N, C, S, centres, d0)
+    v = o.beamform(corr, FS, centres, np.stack([d0, np.zeros(N)]), a, mode=0)
+    X = v[..., 0] + 1j * v[..., 1]
+    Y = v[..., 2] + 1j * v[..., 3]
+    want = np.exp(1j * theta)[None, None, :] * a.sum()
+    assert np.allclose(X[:, 0], 3.0 * want, rtol=1e-12, atol=1e-9), "coherent sum, pol X"
+    assert np.allclose(Y[:, 0], 2.0 * want, rtol=1e-12, atol=1e-9), "coherent sum, pol Y"
+    for sb in range(SB):
+        for k in range(C):
+            f = centres[sb] + (k - C / 2) * FS / C
+            af = abs(np.sum(a * np.exp(-2j * np.pi * f * d0)))
+            assert np.allclose(np.abs(X[sb, 1, k]), 3.0 * af, rtol=1e-10), "array factor"
+            assert af < a.sum() * 0.999
+
+
+def pin_beam_station_sum(o):
+    """Zero beam delays and unit weights: the beam is the plain station sum;
+    a one-hot weight with a beam delay gives that station rotated by
+    exp(+2 pi i f_k delay) (channel frequency f_sb + (k - C/2) fs / C)."""
+    SB, N, C, S = 2, 3, 4, 5
+    corr = synth.noise(23, (SB, C, S, N, 2, 2))
+    centres = synth.subband_centres(SB)
+    v = o.beamform(corr, FS, centres, np.zeros((1, N)), None, mode=0)
+    z = cplx(corr).sum(axis=3)                        # [SB][C][S][P]
+    assert np.allclose(v[:, 0, ..., 0] + 1j * v[:, 0, ..., 1], z[..., 0], rtol=1e-12, atol=1e-12)
+    assert np.allclose(v[:, 0, ..., 2] + 1j * v[:, 0, ..., 3], z[..., 1], rtol=1e-12, atol=1e-12)
+    dl = np.array([[0.0, 2.5e-6, 0.0]])
+    w = np.array([0.0, 1.0, 0.0])
+    v1 = o.beamform(corr, FS, centres, dl, w, mode=0)
+    ym = cplx(corr)[:, :, :, 1, 0]
+    for sb in range(SB):
+        for k in range(C):
+            f = centres[sb] + (k - C / 2) * FS / C
+            rot = np.exp(2j * np.pi * f * 2.5e-6)
+            got = v1[sb, 0, k, :, 0] + 1j * v1[sb, 0, k, :, 1]
+            assert np.allclose(got, rot * ym[sb, k], rtol=1e-10, atol=1e-10)
+
+
+def pin_stokes(o):
+    """Stokes closed forms: Y = X gives Q = V = 0, U = I; X = i Y gives
+    Q = U = 0, V = I; Y = 0 gives Q = I, U = V = 0. I^2 = Q^2 + U^2 + V^2 for a
+    single spectrum, I^2 >= Q^2 + U^2 + V^2 after integration, and the
+    integrated value is the sum of the per-spectrum values."""
+    SB, N, C, S = 1, 3, 4, 8
+    centres = synth.subband_centres(SB)
+    base = cplx(synth.noise(24, (SB, C, S, N, 2)))           # one pol of noise
+    dl = np.random.default_rng(25).uniform(-1e-6, 1e-6, (2, N))
+    for rel, want in (((1.0, 1.0), "U"), ((1j, 1.0), "V"), ((1.0, 0.0), "Q")):
+        y = np.stack([rel[0] * base, rel[1] * base], axis=-1)     # pol X = rel0 * b, pol Y = rel1 * b
+        corr = np.stack([y.real, y.imag], axis=-1)
+        st = o.beamform(corr, FS, centres, dl, None, mode=2, tint=1)
+        I, Q, U, V = (st[..., q] for q in range(4))
+        assert np.all(I > 0)
+        z = {"U": (Q, V), "V": (Q, U), "Q": (U, V)}[want]
+        assert np.allclose(z[0], 0, atol=1e-9 * I.max()) and np.allclose(z[1], 0, atol=1e-9 * I.max())
+        assert np.allclose({"U": U, "V": V, "Q": Q}[want], I, rtol=1e-12)
+    corr = synth.noise(26, (SB, C, S, N, 2, 2))
+    s1 = o.beamform(corr, FS, centres, dl, None, mode=2, tint=1)
+    assert np.allclose(s1[..., 0] ** 2, (s1[..., 1:] ** 2).sum(-1), rtol=1e-10)
+    s4 = o.beamform(corr, FS, centres, dl, None, mode=2, tint=4)
+    assert np.allclose(s4, s1.reshape(SB, 2, C, S // 4, 4, 4).sum(axis=4), rtol=1e-12)
+    assert np.all(s4[..., 0] ** 2 >= (s4[..., 1:] ** 2).sum(-1) * (1 - 1e-12))
+    i4 = o.beamform(corr, FS, centres, dl, None, mode=1, tint=4)
+    assert np.allclose(i4, s4[..., 0], rtol=1e-12)
+
+
 ALL_PINS = [pin_fir_delta, pin_tone, pin_dft_vs_numpy, pin_point_source, pin_bandpass,
             pin_delay_ramp, pin_correlate_einsum, pin_hermitian, pin_linearity,
-            pin_gradient_fd, pin_gradient_truth, pin_fx_chain, pin_ci4_decode, pin_flags]
+            pin_gradient_fd, pin_gradient_truth, pin_fx_chain, pin_ci4_decode, pin_flags,
+            pin_beam_point_source, pin_beam_station_sum, pin_stokes]

@@ -42,6 +42,17 @@ MUTANTS = [
     ("vjp_tau_sign", "my_gt[j] -= Gre * dtre + Gim * dtim;", "my_gt[j] += Gre * dtre + Gim * dtim;"),
     ("vjp_imag_gain_sign", "my_gg[((size_t)i * P + p) * 2 + 1] += Gre * (-d1im) + Gim * d1re;",
      "my_gg[((size_t)i * P + p) * 2 + 1] += Gre * d1im + Gim * d1re;"),
+    ("beam_phase_sign", "const double wre = a * cos(phi), wim = a * sin(phi);",
+     "const double wre = a * cos(phi), wim = -a * sin(phi);"),
+    ("beam_weight_dropped", "const double a = weights ? weights[n] : 1.0;", "const double a = 1.0;"),
+    ("beam_pol_swap", "const double *y = corr + (((((size_t)sb * C + k) * S + s) * N + n) * P + p) * 2;\n"
+     "                                bx[p][0]",
+     "const double *y = corr + (((((size_t)sb * C + k) * S + s) * N + n) * P + (1 - p)) * 2;\n"
+     "                                bx[p][0]"),
+    ("stokes_v_sign", "acc[3] += 2.0 * cim;", "acc[3] -= 2.0 * cim;"),
+    ("stokes_u_from_imag", "acc[2] += 2.0 * cre;", "acc[2] += 2.0 * cim;"),
+    ("stokes_q_sign", "acc[1] += xx - yy;", "acc[1] += yy - xx;"),
+    ("stokes_tint_index", "const int s = so * tint + t;", "const int s = so + t * SO;"),
 ]
 
 
