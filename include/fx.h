@@ -86,12 +86,15 @@ typedef struct {
                                     k*C + c; copied at fx_create */
     float operand_scale;         /* power of two multiplied into FP16/BF16
                                     operands and divided out of vis; 0 means 1 */
-    unsigned flags;              /* 0, or FX_FLAG_TEST_NO_LOADS */
+    unsigned flags;              /* 0 or a set of FX_FLAG_* bits */
     int host_chunk_subbands;     /* > 0: allocate the double-buffered workspaces of
                                     fx_process_host for chunks of this many
                                     subbands; 0: no host pipeline */
     int max_coarse_shift;        /* with FX_FLAG_STREAMING: largest integer-sample
                                     coarse delay per station (>= 0) */
+    int max_beams;               /* > 0: allocate the beamformer's weight table for
+                                    up to this many beams (fx_beamform); needs
+                                    precision FX_F16 or FX_BF16 and n_stations <= 64 */
 } fx_params;
 
 /* Streaming form (fx_stream_block): the handle keeps the FIR history of every
@@ -228,6 +231,32 @@ fx_status fx_stream_block(fx_handle *h, const void *d_new, const int *d_coarse_s
 
 /* Zero the streaming history (the stream restarts with zeros before it). */
 fx_status fx_stream_reset(fx_handle *h, fx_stream stream);
+
+/* ---- coherent beamformer -------------------------------------------------
+ * Sec. "Signal processing with GPU kernels": after delay compensation and
+ * bandpass correction, coherent beamforming steers each beam with a phase
+ * shift and sums over antenna fields, then optionally computes Stokes
+ * parameters (otherwise complex voltages are kept). For beam b, pol p,
+ * spectrum s, channel k (sky frequency f_k = centre + (k - C/2) fs / C):
+ *   B_bp(s, k) = sum_n a_n exp(+2 pi i f_k delta[b][n]) Y_np(s, k)
+ * Y = d_corr, the corrected block of fx_channelize_correct / fx_correct in
+ * the handle's FP16/BF16 planar layout (divided by operand_scale on output).
+ * d_beam_delays [n_beams][N] double: each beam's extra delay per station in
+ * seconds, constant over the block; d_station_weights [N] float a_n or NULL
+ * (= 1). n_beams in [1, max_beams]. With X = B_b0, Y = B_b1:
+ *   FX_BEAM_VOLTAGES     d_out [SB][n_beams][C][S][4] float (Re X, Im X, Re Y, Im Y); tint = 1
+ *   FX_BEAM_STOKES_I     d_out [SB][n_beams][C][S/tint] float, I = |X|^2 + |Y|^2
+ *   FX_BEAM_STOKES_IQUV  d_out [SB][n_beams][C][S/tint][4] float, Q = |X|^2 - |Y|^2,
+ *                        U = 2 Re(X conj Y), V = 2 Im(X conj Y)
+ * Stokes values are summed over tint consecutive spectra: tint a power of two
+ * <= 32 dividing S. Operands are FP16/BF16 with FP32 accumulation on the
+ * tensor cores. Uses the handle's weight table (rewritten every call, so two
+ * calls on one handle must be stream-ordered). FX_ERR_INVALID for bad
+ * arguments or a handle without max_beams; asynchronous and graph-capturable.
+ * A device-side wait that gives up is reported by fx_poll_status. */
+typedef enum { FX_BEAM_VOLTAGES = 0, FX_BEAM_STOKES_I = 1, FX_BEAM_STOKES_IQUV = 2 } fx_beam_output;
+fx_status fx_beamform(fx_handle *h, const void *d_corr, int n_beams, const double *d_beam_delays,
+                      const float *d_station_weights, int output, int tint, float *d_out, fx_stream stream);
 
 /* ---- differentiation form ------------------------------------------------
  * With the delay held constant over the block (tau_begin = tau_end = tau) the

@@ -32,7 +32,8 @@ class fx_params(ctypes.Structure):
                 ("h_subband_centre_hz", ctypes.POINTER(ctypes.c_double)),
                 ("h_taps", ctypes.POINTER(ctypes.c_float)),
                 ("operand_scale", ctypes.c_float), ("flags", ctypes.c_uint),
-                ("host_chunk_subbands", ctypes.c_int), ("max_coarse_shift", ctypes.c_int)]
+                ("host_chunk_subbands", ctypes.c_int), ("max_coarse_shift", ctypes.c_int),
+                ("max_beams", ctypes.c_int)]
 
 
 class fx_sizes(ctypes.Structure):
@@ -57,6 +58,7 @@ SIGNATURES = {
     "fx_process_host": (I, [P, P, P, P, P, P, P, P]),
     "fx_stream_block": (I, [P, P, P, P, P, P, P, P, P, P, P, P]),
     "fx_stream_reset": (I, [P, P]),
+    "fx_beamform": (I, [P, P, I, P, P, I, I, P, P]),
     "fx_poll_status": (I, [P, ctypes.POINTER(ctypes.c_int)]),
     "fx_apply_gains": (I, [P, P, P, P, P, P]),
     "fx_batch_create": (I, [P, I, I, ctypes.c_float, ctypes.POINTER(P)]),
@@ -71,6 +73,7 @@ SIGNATURES = {
 FX_NOALLOC_MAX_PHASES = 1 << 20
 FX_FLAG_TEST_NO_LOADS = 0x80000000
 FX_FLAG_STREAMING = 0x1
+FX_BEAM_VOLTAGES, FX_BEAM_STOKES_I, FX_BEAM_STOKES_IQUV = 0, 1, 2
 
 _lib = None
 

@@ -31,13 +31,15 @@ class Correlator:
     def __init__(self, n_stations: int, n_subbands: int, n_channels: int, n_spectra: int,
                  taps, centres, n_taps: int = 16, fmt: int = FX_CI16, precision: int = FX_F32,
                  sample_rate_hz: float = SAMPLE_RATE_HZ, operand_scale: float = 0.0, device=None,
-                 host_chunk_subbands: int = 0, streaming: bool = False, max_coarse_shift: int = 0):
+                 host_chunk_subbands: int = 0, streaming: bool = False, max_coarse_shift: int = 0,
+                 max_beams: int = 0):
         self.lib = _abi.load()
         if device is not None:
             torch.cuda.set_device(device)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.N, self.SB, self.C, self.S, self.T = n_stations, n_subbands, n_channels, n_spectra, n_taps
         self.fmt, self.precision = fmt, precision
+        self.operand_scale = operand_scale if operand_scale else 1.0
         taps = np.ascontiguousarray(np.asarray(taps, dtype=np.float32).reshape(-1))
         centres = np.ascontiguousarray(np.asarray(centres, dtype=np.float64).reshape(-1))
         if taps.size != n_taps * n_channels:
@@ -56,6 +58,7 @@ class Correlator:
         p.flags = _abi.FX_FLAG_STREAMING if streaming else 0
         p.host_chunk_subbands = host_chunk_subbands
         p.max_coarse_shift = max_coarse_shift
+        p.max_beams = max_beams
         h = ctypes.c_void_p()
         check(self.lib.fx_create(ctypes.byref(p), ctypes.byref(h)), "fx_create")
         self.handle = h
@@ -216,6 +219,26 @@ class Correlator:
             self._opt(vis, "vis", torch.float32, self.sizes.vis_bytes),
             self._opt(counts, "counts", torch.float32, 4 * self.B), _stream_ptr(stream)), "fx_stream_block")
         return corr, vis, counts
+
+    # -- coherent beamformer ----------------------------------------------------
+    def beam_shape(self, n_beams, output=0, tint=1):
+        SB, C, S = self.SB, self.C, self.S
+        return {0: (SB, n_beams, C, S, 4), 1: (SB, n_beams, C, S // tint),
+                2: (SB, n_beams, C, S // tint, 4)}[output]
+
+    def beamform(self, corr, beam_delays, station_weights=None, output=0, tint=1, out=None, stream=None):
+        """fx_beamform: coherent beams from the corrected FP16/BF16 block.
+        beam_delays [n_beams][N] float64 (seconds), station_weights [N] float32."""
+        nb = int(beam_delays.shape[0])
+        if out is None:
+            out = torch.empty(self.beam_shape(nb, output, tint), dtype=torch.float32, device=self.device)
+        check(self.lib.fx_beamform(
+            self.handle, self._dev(corr, "corr", self.corr_dtype(), self.sizes.corr_bytes), nb,
+            self._dev(beam_delays, "beam_delays", torch.float64, 8 * nb * self.N),
+            self._opt(station_weights, "station_weights", torch.float32, 4 * self.N), output, tint,
+            self._dev(out, "out", torch.float32, 4 * int(np.prod(self.beam_shape(nb, output, tint)))),
+            _stream_ptr(stream)), "fx_beamform")
+        return out
 
     def stream_reset(self, stream=None):
         check(self.lib.fx_stream_reset(self.handle, _stream_ptr(stream)), "fx_stream_reset")

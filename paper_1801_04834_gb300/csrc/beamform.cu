@@ -1,0 +1,471 @@
+// beamform.cu -- coherent beamformer on the tcgen05 tensor cores.
+//
+// Paper, Sec. "Signal processing with GPU kernels": after delay compensation
+// and bandpass correction (done at 256 channels per subband), coherent
+// beamforming steers each beam with a phase shift and sums over antenna
+// fields, then optionally forms Stokes parameters; without them the complex
+// voltages are kept. Per (subband, channel k) and pol this is a complex
+// matrix product over stations n:
+//   B[s][b] = sum_n Y[s][n] W[b][n],   W[b][n] = a_n exp(+2 pi i f_k delta[b][n])
+// done as four real GEMMs on planar operands (re plane r, im plane j):
+//   Re B = Yr Wr^T - Yj Wj^T          Im B = Yr Wj^T + Yj Wr^T
+// with the minus from the MMA's negate-A bit.
+//
+// Operands. A = data: M = 128 spectra x K = 64 stations of one (pol, plane),
+// read from the planar FP16/BF16 block the fused F-stage writes for the
+// X-stage ([SB][C][re/im][I_pad][S_pad], input i = 2n + p, spectra
+// contiguous). A 4-D TMA box {64 spectra, 1 pol, 64 stations} picks one pol
+// out of the interleaved inputs; two boxes give the 128 spectra. Spectra are
+// contiguous, so A is MN-major (128-byte swizzle: 8 station rows of 64
+// spectra per 1024-byte atom, the two 64-spectrum halves 8 KB apart).
+// B = weights: N = 64 beams x K = 64 stations, K-major, from a table the
+// weight kernel writes each call ([SB][C][re/im][NB_pad][64]); its phase per
+// (subband, beam, station) is formed in FP64 at the channel-0 frequency and
+// per-channel step, reduced mod 2 pi, then stepped over channels in FP32 (as
+// the paper does for delay compensation).
+//
+// Work item = (subband, channel, 128-spectrum tile). The CTA loads the four
+// data planes of an item once (64 KB, ring of 2) and walks the beams in
+// quarters of 64: a 16 KB weight tile per quarter (ring of 4), 32 MMAs
+// (4 K-steps x 2 pols x 4 products, M = 128, N = 64, K = 16) into Re X, Im X,
+// Re Y, Im Y (4 x 64 TMEM columns, double buffered: all 512 columns).
+// Warp roles (persistent, one CTA per SM): warp 0 TMA producer, warp 1 TMEM
+// allocator + MMA issuer, warps 2-5 epilogue (TMEM lane = spectrum): complex
+// voltages, or Stokes I / IQUV summed over tint consecutive spectra with warp
+// shuffles. Every mbarrier wait is bounded; on expiry the role is recorded in
+// the status word, all roles leave, in-flight copies and MMAs are drained
+// (bounded) and TMEM is freed, as in the X-stage.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+#include "tc_ptx.cuh"
+
+namespace fxi {
+namespace {
+
+using namespace tc;
+
+constexpr int kBfThreads = 192;
+constexpr int kDS = 2;                               // data stages
+constexpr int kWS = 4;                               // weight stages
+constexpr unsigned kHalfBytes = 64u * 128u;          // 64 stations x 64 spectra x 2 B
+constexpr unsigned kPlaneBytes = 2u * kHalfBytes;    // 128 spectra of one (pol, plane)
+constexpr unsigned kDataBytes = 4u * kPlaneBytes;    // (pol, plane) = 4 planes: 64 KB
+constexpr unsigned kWPlane = 64u * 128u;             // 64 beams x 64 stations x 2 B
+constexpr unsigned kWBytes = 2u * kWPlane;           // re + im: 16 KB
+constexpr int kAccCols = 256;                        // Re X, Im X, Re Y, Im Y x 64 beams
+constexpr int kTmemCols = 512;
+constexpr int kNumBars = 17;                         // dfull 2, dempty 2, wfull 4, wempty 4, accf 2, acce 2, drain
+
+struct BfParams {
+    CUtensorMap mapY;        // 4-D (spectrum, pol, station, sb*C*2 + plane)
+    CUtensorMap mapW;        // 3-D (station, beam, sb*C*2 + plane)
+    float *out;
+    int *status;
+    long long n_items;       // SB * C * ntile
+    int ntile;               // 128-spectrum tiles per channel
+    int C, S, NB, NBQ;       // channels, spectra, beams, beam quarters
+    int mode, tint;
+    unsigned bf16;
+    float inv_scale, inv_scale2;
+    long long timeout_cycles;
+};
+
+// Bounded wait: false on timeout (sets abort + status) or when another role aborted.
+__device__ __forceinline__ bool bwait(unsigned bar, unsigned parity, volatile int *abort_flag, const BfParams &P,
+                                      int code)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > P.timeout_cycles) {
+            *abort_flag = 1;
+            atomicCAS(P.status, 0, code);
+            atomicExch(P.status + 1, (int)blockIdx.x);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ unsigned short weight_bits(float x, unsigned bf16)
+{
+    return bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(x)) : __half_as_ushort(__float2half_rn(x));
+}
+
+// Weight table W[sb][k][re/im][NB_pad][64]: one thread per (subband, beam,
+// station slot), looping over channels. Padding beams and stations are zero.
+__global__ void bf_weight_kernel(const double *__restrict__ delays, const float *__restrict__ weights,
+                                 const double *__restrict__ centres, unsigned short *__restrict__ W, int SB, int C,
+                                 int N, int NB, int NB_pad, double fs, unsigned bf16)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)SB * NB_pad * 64) return;
+    const int n = (int)(idx % 64);
+    const int b = (int)((idx / 64) % NB_pad);
+    const int sb = (int)(idx / (64LL * NB_pad));
+    const long long plane = (long long)NB_pad * 64;
+    unsigned short *w = W + (long long)sb * C * 2 * plane + (long long)b * 64 + n;
+    if (b >= NB || n >= N) {
+        for (int k = 0; k < C; ++k) {
+            w[(2LL * k) * plane] = 0;
+            w[(2LL * k + 1) * plane] = 0;
+        }
+        return;
+    }
+    const double two_pi = 6.283185307179586476925286766559;
+    const double d = delays[(long long)b * N + n];
+    // phase at channel 0 (frequency centre - fs/2) and step per channel (fs / C), mod 2 pi
+    double p0 = two_pi * (centres[sb] - 0.5 * fs) * d;
+    p0 -= two_pi * rint(p0 / two_pi);
+    double dp = two_pi * (fs / C) * d;
+    dp -= two_pi * rint(dp / two_pi);
+    const float a = weights ? weights[n] : 1.f;
+    const float p0f = (float)p0, dpf = (float)dp;
+    for (int k = 0; k < C; ++k) {
+        const float phi = fmaf((float)k, dpf, p0f);
+        const float kq = rintf(phi * 0.15915494309189535f);           // phi / (2 pi)
+        float r = fmaf(-kq, 6.28125f, phi);                           // 2 pi = 6.28125 + 1.9353...e-3
+        r = fmaf(-kq, 1.9353071795864769e-3f, r);
+        float sn, cs;
+        __sincosf(r, &sn, &cs);
+        w[(2LL * k) * plane] = weight_bits(a * cs, bf16);
+        w[(2LL * k + 1) * plane] = weight_bits(a * sn, bf16);
+    }
+}
+
+__global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_constant__ BfParams P)
+{
+    extern __shared__ unsigned char smem_raw[];
+    // 1024-byte alignment for the 128-byte-swizzled tiles
+    const unsigned base_u32 = smem_u32(smem_raw);
+    const unsigned pad = (1024 - (base_u32 & 1023)) & 1023;
+    const unsigned data_u32 = base_u32 + pad;
+    const unsigned w_u32 = data_u32 + kDS * kDataBytes;
+    unsigned char *ctrl = smem_raw + pad + kDS * kDataBytes + kWS * kWBytes;
+    const unsigned bar0 = smem_u32(ctrl);
+    auto dfull = [&](int s) { return bar0 + 8u * s; };
+    auto dempty = [&](int s) { return bar0 + 8u * (kDS + s); };
+    auto wfull = [&](int s) { return bar0 + 8u * (2 * kDS + s); };
+    auto wempty = [&](int s) { return bar0 + 8u * (2 * kDS + kWS + s); };
+    auto accf = [&](int b) { return bar0 + 8u * (2 * kDS + 2 * kWS + b); };
+    auto acce = [&](int b) { return bar0 + 8u * (2 * kDS + 2 * kWS + 2 + b); };
+    const unsigned drain_bar = bar0 + 8u * (kNumBars - 1);
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(ctrl + 8 * kNumBars);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kDS; ++s) {
+            mbar_init(dfull(s), 1);
+            mbar_init(dempty(s), 1);
+        }
+        for (int s = 0; s < kWS; ++s) {
+            mbar_init(wfull(s), 1);
+            mbar_init(wempty(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf(b), 1);
+            mbar_init(acce(b), 4);
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ================= TMA producer =================
+        if (lane == 0) {
+            long long d_issued = 0, w_issued = 0;
+            bool ok = true;
+            for (long long w = blockIdx.x; w < P.n_items && ok; w += gridDim.x) {
+                const long long gch = w / P.ntile;
+                const int st = (int)(w % P.ntile);
+                const int ds = (int)(d_issued % kDS);
+                if (!bwait(dempty(ds), (unsigned)((d_issued / kDS) & 1) ^ 1u, abort_flag, P, 1)) {
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(dfull(ds), kDataBytes);
+                const unsigned dst = data_u32 + (unsigned)ds * kDataBytes;
+                for (int p = 0; p < 2; ++p)
+                    for (int pl = 0; pl < 2; ++pl)
+                        for (int hh = 0; hh < 2; ++hh)
+                            tma_load_4d(dst + (unsigned)(p * 2 + pl) * kPlaneBytes + (unsigned)hh * kHalfBytes,
+                                        &P.mapY, dfull(ds), st * 128 + hh * 64, p, 0, (int)(gch * 2 + pl));
+                ++d_issued;
+                for (int q = 0; q < P.NBQ; ++q) {
+                    const int ws = (int)(w_issued % kWS);
+                    if (!bwait(wempty(ws), (unsigned)((w_issued / kWS) & 1) ^ 1u, abort_flag, P, 1)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(wfull(ws), kWBytes);
+                    for (int pl = 0; pl < 2; ++pl)
+                        tma_load_3d(w_u32 + (unsigned)ws * kWBytes + (unsigned)pl * kWPlane, &P.mapW, wfull(ws), 0,
+                                    q * 64, (int)(gch * 2 + pl));
+                    ++w_issued;
+                }
+            }
+            if (!ok) {
+                // the last loads issued into each ring may still be in flight
+                for (long long u = d_issued > kDS ? d_issued - kDS : 0; u < d_issued; ++u)
+                    drain_wait(dfull((int)(u % kDS)), (unsigned)((u / kDS) & 1), P.timeout_cycles);
+                for (long long u = w_issued > kWS ? w_issued - kWS : 0; u < w_issued; ++u)
+                    drain_wait(wfull((int)(u % kWS)), (unsigned)((u / kWS) & 1), P.timeout_cycles);
+            }
+        }
+    } else if (warp == 1) {
+        // ================= MMA issuer =================
+        if (lane == 0) {
+            long long dit = 0, wit = 0, ait = 0;
+            bool ok = true, issued = false;
+            const unsigned idesc = make_idesc_major(P.bf16, 64, false, true, false);
+            const unsigned idesc_neg = make_idesc_major(P.bf16, 64, true, true, false);
+            for (long long w = blockIdx.x; w < P.n_items && ok; w += gridDim.x, ++dit) {
+                const int ds = (int)(dit % kDS);
+                if (!bwait(dfull(ds), (unsigned)((dit / kDS) & 1), abort_flag, P, 2)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const unsigned dtile = data_u32 + (unsigned)ds * kDataBytes;
+                for (int q = 0; q < P.NBQ; ++q, ++wit, ++ait) {
+                    const int ws = (int)(wit % kWS);
+                    if (!bwait(wfull(ws), (unsigned)((wit / kWS) & 1), abort_flag, P, 2)) {
+                        ok = false;
+                        break;
+                    }
+                    const int ab = (int)(ait & 1);
+                    if (!bwait(acce(ab), (unsigned)((ait >> 1) & 1) ^ 1u, abort_flag, P, 2)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const unsigned wt = w_u32 + (unsigned)ws * kWBytes;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {          // 16 stations per K-step
+                        const unsigned acc = kk ? 1u : 0u;
+                        const unsigned long long bwr = smem_desc(wt + kk * 32);
+                        const unsigned long long bwj = smem_desc(wt + kWPlane + kk * 32);
+#pragma unroll
+                        for (int p = 0; p < 2; ++p) {
+                            const unsigned at = dtile + (unsigned)(p * 2) * kPlaneBytes + (unsigned)kk * 2048u;
+                            const unsigned long long ayr = smem_desc_mn(at, kHalfBytes, 1024);
+                            const unsigned long long ayj = smem_desc_mn(at + kPlaneBytes, kHalfBytes, 1024);
+                            const unsigned d_re = tmem_base + (unsigned)(ab * kAccCols + p * 128);
+                            const unsigned d_im = d_re + 64;
+                            mma_f16(d_re, ayr, bwr, idesc, acc);
+                            mma_f16(d_re, ayj, bwj, idesc_neg, 1u);
+                            mma_f16(d_im, ayr, bwj, idesc, acc);
+                            mma_f16(d_im, ayj, bwr, idesc, 1u);
+                        }
+                    }
+                    issued = true;
+                    mma_commit(wempty(ws));                   // weight tile free once read
+                    mma_commit(accf(ab));                     // accumulators ready for the epilogue
+                }
+                if (!ok) break;
+                mma_commit(dempty(ds));                       // data stage free after the last quarter
+            }
+            if (!ok && issued) {
+                mma_commit(drain_bar);
+                drain_wait(drain_bar, 0, P.timeout_cycles);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ================= epilogue (warps 2..5) =================
+        const int qd = warp & 3;                              // TMEM lane quadrant of this warp
+        const unsigned lane_off = (unsigned)(32 * qd) << 16;
+        long long ait = 0;
+        bool live = true;
+        for (long long w = blockIdx.x; w < P.n_items && live; w += gridDim.x) {
+            const long long gch = w / P.ntile;
+            const int st = (int)(w % P.ntile);
+            const long long sb = gch / P.C;
+            const int c = (int)(gch % P.C);
+            const int s = st * 128 + 32 * qd + lane;          // this lane's spectrum
+            for (int q = 0; q < P.NBQ; ++q, ++ait) {
+                const int ab = (int)(ait & 1);
+                const bool got = bwait(accf(ab), (unsigned)((ait >> 1) & 1), abort_flag, P, 3);
+                if (!__all_sync(0xffffffffu, got)) {
+                    live = false;
+                    break;
+                }
+                tc_fence_after();
+                const unsigned t0 = tmem_base + lane_off + (unsigned)(ab * kAccCols);
+#pragma unroll 1
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int b0 = q * 64 + cc * 16;
+                    if (b0 >= P.NB) break;
+                    float xr[16], xj[16], yr[16], yj[16];
+                    tmem_ld16(t0 + 16 * cc, xr);
+                    tmem_ld16(t0 + 64 + 16 * cc, xj);
+                    tmem_ld16(t0 + 128 + 16 * cc, yr);
+                    tmem_ld16(t0 + 192 + 16 * cc, yj);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) {
+                        const int b = b0 + jj;
+                        if (b >= P.NB) break;
+                        const long long row = (sb * P.NB + b) * P.C + c;
+                        if (P.mode == 0) {
+                            if (s < P.S) {
+                                const float is = P.inv_scale;
+                                *reinterpret_cast<float4 *>(P.out + (row * P.S + s) * 4) =
+                                    make_float4(xr[jj] * is, xj[jj] * is, yr[jj] * is, yj[jj] * is);
+                            }
+                            continue;
+                        }
+                        // Stokes of this spectrum (padded spectra are zero), then sum over tint lanes
+                        const float xx = xr[jj] * xr[jj] + xj[jj] * xj[jj];
+                        const float yy = yr[jj] * yr[jj] + yj[jj] * yj[jj];
+                        float st4[4];
+                        st4[0] = xx + yy;
+                        st4[1] = xx - yy;
+                        st4[2] = 2.f * (xr[jj] * yr[jj] + xj[jj] * yj[jj]);   // 2 Re(X conj Y)
+                        st4[3] = 2.f * (xj[jj] * yr[jj] - xr[jj] * yj[jj]);   // 2 Im(X conj Y)
+                        const int nq = P.mode == 1 ? 1 : 4;
+                        for (int k = 0; k < nq; ++k)
+                            for (int off = 1; off < P.tint; off <<= 1)
+                                st4[k] += __shfl_xor_sync(0xffffffffu, st4[k], off);
+                        if (s < P.S && (lane % P.tint) == 0) {
+                            const long long so = row * (P.S / P.tint) + s / P.tint;
+                            const float is2 = P.inv_scale2;
+                            if (P.mode == 1)
+                                P.out[so] = st4[0] * is2;
+                            else
+                                *reinterpret_cast<float4 *>(P.out + so * 4) =
+                                    make_float4(st4[0] * is2, st4[1] * is2, st4[2] * is2, st4[3] * is2);
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce(ab));
+            }
+        }
+    }
+
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+// ---- host side ----------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+EncodeTiledFn bf_encode_fn()
+{
+    static EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            return reinterpret_cast<EncodeTiledFn>(p);
+        return static_cast<EncodeTiledFn>(nullptr);
+    }();
+    return fn;
+}
+
+constexpr size_t bf_smem_bytes() { return 1024 + (size_t)kDS * kDataBytes + (size_t)kWS * kWBytes + 8 * kNumBars + 16; }
+
+}  // namespace
+
+size_t bf_weight_bytes(const Handle &h, int n_beams)
+{
+    const size_t nb_pad = (size_t)(n_beams + 63) / 64 * 64;
+    return (size_t)h.p.n_subbands * h.p.n_channels * 2 * nb_pad * 64 * sizeof(unsigned short);
+}
+
+cudaError_t launch_beamform(const Handle &h, const void *corr, int NB, const double *delays, const float *weights,
+                            int mode, int tint, float *out, cudaStream_t st)
+{
+    EncodeTiledFn enc = bf_encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const int SB = h.p.n_subbands, C = h.p.n_channels, N = h.p.n_stations, S = h.p.n_spectra;
+    const int NB_pad = (NB + 63) / 64 * 64;
+    const unsigned bf16 = h.p.precision == FX_BF16 ? 1u : 0u;
+    const long long planes = (long long)SB * C * 2;
+    if (planes > 0x7fffffffLL) return cudaErrorInvalidValue;
+
+    // weight table for this call
+    const long long wthreads = (long long)SB * NB_pad * 64;
+    bf_weight_kernel<<<(unsigned)((wthreads + 255) / 256), 256, 0, st>>>(
+        delays, weights, h.d_centres, h.d_bfw, SB, C, N, NB, NB_pad, h.p.sample_rate_hz, bf16);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+
+    BfParams P;
+    memset(&P, 0, sizeof(P));
+    // data: (spectrum, pol, station, plane row) over [SB][C][2][I_pad][S_pad], input i = 2n + p
+    {
+        const cuuint64_t gdim[4] = {(cuuint64_t)h.S_pad, 2, (cuuint64_t)(h.I_pad / 2), (cuuint64_t)planes};
+        const cuuint64_t gstride[3] = {(cuuint64_t)h.S_pad * 2, (cuuint64_t)h.S_pad * 4,
+                                       (cuuint64_t)h.S_pad * 2 * h.I_pad};
+        const cuuint32_t box[4] = {64, 1, 64, 1};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (enc(&P.mapY, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<void *>(corr), gdim, gstride, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    // weights: (station, beam, plane row) over [SB][C][2][NB_pad][64]
+    {
+        const cuuint64_t gdim[3] = {64, (cuuint64_t)NB_pad, (cuuint64_t)planes};
+        const cuuint64_t gstride[2] = {64 * 2, (cuuint64_t)NB_pad * 64 * 2};
+        const cuuint32_t box[3] = {64, 64, 1};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        if (enc(&P.mapW, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, h.d_bfw, gdim, gstride, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    P.out = out;
+    P.status = h.d_status;
+    P.ntile = (S + 127) / 128;
+    P.n_items = planes / 2 * P.ntile;
+    P.C = C;
+    P.S = S;
+    P.NB = NB;
+    P.NBQ = NB_pad / 64;
+    P.mode = mode;
+    P.tint = tint;
+    P.bf16 = bf16;
+    P.inv_scale = 1.0f / h.operand_scale;
+    P.inv_scale2 = 1.0f / (h.operand_scale * h.operand_scale);
+    P.timeout_cycles = h.tc_timeout_cycles;
+    constexpr size_t smem = bf_smem_bytes();
+    e = cudaFuncSetAttribute(beamform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long grid = std::min<long long>(P.n_items, h.num_sms);
+    if (grid <= 0) return cudaSuccess;
+    beamform_kernel<<<(unsigned)grid, kBfThreads, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace fxi

@@ -71,6 +71,9 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
     if (p.max_coarse_shift < 0 || p.max_coarse_shift > (1 << 24))
         return fail(FX_ERR_INVALID, "max_coarse_shift out of range");
     if (p.host_chunk_subbands < 0) return fail(FX_ERR_INVALID, "host_chunk_subbands must be >= 0");
+    if (p.max_beams < 0 || p.max_beams > 4096) return fail(FX_ERR_INVALID, "max_beams must be in [0, 4096]");
+    if (p.max_beams > 0 && ((p.precision != FX_F16 && p.precision != FX_BF16) || p.n_stations > 64))
+        return fail(FX_ERR_UNSUPPORTED, "the beamformer needs FX_F16 or FX_BF16 operands and at most 64 stations");
     float scale = p.operand_scale == 0.f ? 1.f : p.operand_scale;
     if (!is_pow2(scale)) return fail(FX_ERR_INVALID, "operand_scale must be a power of two");
     if (p.precision == FX_F32 && scale != 1.f)
@@ -134,6 +137,7 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
     FX_TRY(cudaMemcpy(h->d_xf32_tiles, tiles.data(), sizeof(int2) * ntiles, cudaMemcpyHostToDevice));
     FX_TRY(cudaMemset(h->d_status, 0, sizeof(int) * 4));
     if (p.host_chunk_subbands > 0) FX_TRY(fxi::pipe_create(*h, p.host_chunk_subbands));
+    if (p.max_beams > 0) FX_TRY(cudaMalloc(&h->d_bfw, fxi::bf_weight_bytes(*h, p.max_beams)));
     if (p.flags & FX_FLAG_STREAMING) {
         h->hist_len = (T - 1) * C + p.max_coarse_shift;
         const size_t hist_bytes = (size_t)SB * N * h->hist_len * fxi::raw_sample_bytes(*h);
@@ -164,6 +168,7 @@ extern "C" void fx_destroy(fx_handle *h)
     cudaFree(h->d_hist[0]);
     cudaFree(h->d_hist[1]);
     cudaFree(h->d_block);
+    cudaFree(h->d_bfw);
     fxi::pipe_destroy(*h);
     delete h;
 }
@@ -274,6 +279,28 @@ extern "C" fx_status fx_process_host(fx_handle *h, const void *h_raw, const doub
     }
     return after_launch(fxi::pipe_run(*h, h_raw, h_delay_begin, h_delay_end, h_bandpass, h_gains, h_vis,
                                       (cudaStream_t)stream),
+                        who);
+}
+
+extern "C" fx_status fx_beamform(fx_handle *h, const void *d_corr, int n_beams, const double *d_beam_delays,
+                                 const float *d_station_weights, int output, int tint, float *d_out, fx_stream stream)
+{
+    const char *who = "fx_beamform";
+    fx_status st = check_handle(h, who);
+    if (st) return st;
+    if (!h->d_bfw) return fail(FX_ERR_INVALID, "%s: handle was created with max_beams = 0", who);
+    if (!d_corr || !d_beam_delays || !d_out) return fail(FX_ERR_INVALID, "%s: NULL buffer", who);
+    if (n_beams < 1 || n_beams > h->p.max_beams)
+        return fail(FX_ERR_INVALID, "%s: n_beams must be in [1, %d]", who, h->p.max_beams);
+    if (output < FX_BEAM_VOLTAGES || output > FX_BEAM_STOKES_IQUV) return fail(FX_ERR_INVALID, "%s: bad output", who);
+    if (tint < 1 || tint > 32 || !is_pow2(tint) || h->p.n_spectra % tint != 0 ||
+        (output == FX_BEAM_VOLTAGES && tint != 1))
+        return fail(FX_ERR_INVALID, "%s: tint must be a power of two <= 32 dividing S (1 for voltages)", who);
+    if (((uintptr_t)d_corr & 15) || ((uintptr_t)d_out & 15) || ((uintptr_t)d_beam_delays & 7) ||
+        ((uintptr_t)d_station_weights & 3))
+        return fail(FX_ERR_INVALID, "%s: misaligned buffer", who);
+    return after_launch(fxi::launch_beamform(*h, d_corr, n_beams, d_beam_delays, d_station_weights, output, tint,
+                                             d_out, (cudaStream_t)stream),
                         who);
 }
 

@@ -32,6 +32,8 @@ struct Handle {
     void *d_hist[2] = {nullptr, nullptr};
     int hist_cur = 0;
     void *d_block = nullptr;
+    // beamformer (max_beams > 0): weight table [SB][C][re/im][ceil64(max_beams)][64]
+    unsigned short *d_bfw = nullptr;
     // host pipeline (fx_process_host), when host_chunk_subbands > 0
     struct HostPipe *pipe = nullptr;
     int num_sms = 0;
@@ -79,6 +81,11 @@ cudaError_t launch_apply_gains(const Handle &h, const float2 *R, const float2 *g
                                float2 *V, cudaStream_t st);
 cudaError_t launch_adjoint(const Handle &h, const float2 *R, const float2 *G, const float2 *gains,
                            const double *tau, float2 *grad_gains, double *grad_tau, cudaStream_t st);
+
+// beamform.cu
+size_t bf_weight_bytes(const Handle &h, int n_beams);
+cudaError_t launch_beamform(const Handle &h, const void *corr, int n_beams, const double *delays,
+                            const float *weights, int mode, int tint, float *out, cudaStream_t st);
 
 // xcorr_tc.cu
 bool xtc_plan(const Handle &h, int *rload, int *stages, unsigned *stage_bytes);
