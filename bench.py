@@ -441,7 +441,7 @@ def run_fx(args, w):
     if not args.no_variants and w["precision"] == 0:
         ref_vis = vis.double()
         del corr
-        for name, prec in (("fp16", 1), ("split_fp16", 3), ("bf16", 2)):
+        for name, prec in (("fp16", 1), ("split_fp16", 3), ("bf16", 2), ("tf32_split", 4)):
             try:
                 cv = fxg.Correlator(w["N"], w["SB"], w["C"], w["S"], taps=taps, centres=centres,
                                     n_taps=w["T"], fmt=w["fmt"], precision=prec)
@@ -482,6 +482,11 @@ def run_fx(args, w):
             extras["differentiation"] = measure_adjoint(args, dev)
         except Exception as ex:
             extras["differentiation"] = {"error": str(ex)[:300]}
+        torch.cuda.empty_cache()
+        try:
+            extras["beamformer"] = measure_beamformer(args, dev)
+        except Exception as ex:
+            extras["beamformer"] = {"error": str(ex)[:300]}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -646,6 +651,62 @@ def measure_adjoint(args, dev):
             "train_step_ms_recompute": raw_ms + bwd_ms + fwd_ms}
 
 
+def measure_beamformer(args, dev):
+    """Beamformer workload (the paper's beamformer requirement): 48 stations x
+    2 pols, 244 subbands of complex int16 samples, 256 channels, 768 spectra
+    (1.00663 s), 127 coherent beams, Stokes I summed over 16 spectra. Step =
+    fused F-stage with FP16 operands + beamformer (weight table + tcgen05
+    kernel). Inputs (18.8 GB raw, 18.4 GB operands) are far larger than L2."""
+    import numpy as np
+    import torch
+
+    import paper_1801_04834_gb300 as fxg
+    import synth
+    N, SB, C, S, NB, tint = 48, args.beam_subbands, 256, 768, 127, 16
+    seed = synth.BASE_SEED + 5
+    rng = np.random.default_rng(seed)
+    tau = rng.uniform(-5e-6, 5e-6, N)
+    tones = [synth.Tone(amp=50.0, channel=int(rng.integers(1, C)), delays=tau)]
+    raw = synth.make_raw_torch(seed, 0, SB, N, C, S, n_taps=16, sigma=100.0, tones=tones, device=dev)
+    c = fxg.Correlator(N, SB, C, S, taps=synth.kaiser_sinc_taps(16, C), centres=synth.subband_centres(SB),
+                       fmt=0, precision=1, operand_scale=2.0 ** -6, max_beams=NB)
+    delays = torch.as_tensor(tau, device=dev)
+    corr = torch.empty(c.corr_shape(), dtype=c.corr_dtype(), device=dev)
+    bd = torch.as_tensor(rng.uniform(-2e-6, 2e-6, (NB, N)), device=dev)
+    out = torch.empty(c.beam_shape(NB, 1, tint), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def fstage():
+        c.channelize_correct(raw, delays, delays, out=corr)
+
+    def beams():
+        c.beamform(corr, bd, output=1, tint=tint, out=out)
+
+    for _ in range(max(args.warmup, 3)):
+        fstage()
+        beams()
+    step_ms = _time(lambda: (fstage(), beams()), args.steps, stream)
+    f_ms = _time(fstage, args.steps, stream)
+    b_ms = _time(beams, args.steps, stream)
+    peaks, _ = measured_peaks()
+    nb_pad = (NB + 63) // 64 * 64
+    wbytes = SB * C * 2 * nb_pad * 64 * 2
+    bf_bytes = c.sizes.corr_bytes + 2 * wbytes + out.numel() * 4     # operands + weight table + Stokes I
+    useful = 8.0 * NB * N * 2 * S * C * SB
+    sky_s = S * C / synth.SAMPLE_RATE_HZ
+    res = {"workload": f"48 stations x 2 pols, {SB} subbands, complex int16, 256 channels, 768 spectra, "
+                       "127 beams, coherent Stokes I / 16 spectra, FP16 operands",
+           "step_ms": step_ms, "rtf": sky_s / (step_ms * 1e-3),
+           "channelize_correct_ms": f_ms, "beamform_ms": b_ms,
+           "beamform_useful_TFLOPs": useful / (b_ms * 1e-3) / 1e12,
+           "beamform_hbm_GBps": bf_bytes / (b_ms * 1e-3) / 1e9,
+           "beamform_hbm_frac": bf_bytes / (b_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+           "beamform_algorithmic_bytes": bf_bytes}
+    c.close()
+    del raw, corr, out
+    return res
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -659,7 +720,9 @@ def main(argv=None):
     ap.add_argument("--host-chunk", type=int, default=16,
                     help="subbands per chunk of the host pipeline (e2e)")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batching and differentiation measurements")
+                    help="skip the batching, differentiation and beamformer measurements")
+    ap.add_argument("--beam-subbands", type=int, default=244,
+                    help="subbands of the beamformer measurement (244 = the paper's requirement)")
     args = ap.parse_args(argv)
     w = WORKLOADS[args.workload]
     if args.impl == "reference":

@@ -68,8 +68,12 @@ typedef enum {
 typedef enum { FX_CI16 = 0, FX_CI8 = 1, FX_CI4 = 2 } fx_format;
 
 /* Arithmetic type of the corrected samples and of the X-stage operands. The
- * FIR and FFT always run in FP32; the X-stage always accumulates in FP32. */
-typedef enum { FX_F32 = 0, FX_F16 = 1, FX_BF16 = 2, FX_F16_SPLIT = 3 } fx_precision;
+ * FIR and FFT always run in FP32; the X-stage always accumulates in FP32.
+ * FX_TF32_SPLIT: FP32 corrected samples in the planar layout; the X-stage
+ * splits each into hi + lo TF32 parts on the tensor cores (hi hi' + hi lo' +
+ * lo hi', FP32 accumulation), which holds FP32's error bound; at most 64
+ * stations, operand_scale must be 1. */
+typedef enum { FX_F32 = 0, FX_F16 = 1, FX_BF16 = 2, FX_F16_SPLIT = 3, FX_TF32_SPLIT = 4 } fx_precision;
 
 typedef struct {
     int n_stations;              /* N >= 1 (antenna fields) */

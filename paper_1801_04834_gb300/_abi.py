@@ -11,7 +11,7 @@ LIB_PATH = os.path.join(HERE, "libfx_gb300.so")
 
 FX_OK, FX_ERR_INVALID, FX_ERR_CUDA, FX_ERR_NOMEM, FX_ERR_TIMEOUT, FX_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 FX_CI16, FX_CI8, FX_CI4 = 0, 1, 2
-FX_F32, FX_F16, FX_BF16, FX_F16_SPLIT = 0, 1, 2, 3
+FX_F32, FX_F16, FX_BF16, FX_F16_SPLIT, FX_TF32_SPLIT = 0, 1, 2, 3, 4
 
 STATUS_NAMES = {0: "FX_OK", -1: "FX_ERR_INVALID", -2: "FX_ERR_CUDA", -3: "FX_ERR_NOMEM",
                 -4: "FX_ERR_TIMEOUT", -5: "FX_ERR_UNSUPPORTED"}

@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import FX_CI4, FX_CI8, FX_CI16, FX_F16, FX_F16_SPLIT, FX_F32, check
+from ._abi import FX_CI4, FX_CI8, FX_CI16, FX_F16, FX_F16_SPLIT, FX_F32, FX_TF32_SPLIT, check
 
 SAMPLE_RATE_HZ = 195312.5
 
@@ -89,7 +89,8 @@ class Correlator:
         return (self.SB, self.C, self.planes, self.I_pad, self.S_pad)
 
     def corr_dtype(self):
-        return {FX_F32: torch.float32, FX_F16: torch.float16, FX_F16_SPLIT: torch.float16}.get(
+        return {FX_F32: torch.float32, FX_F16: torch.float16, FX_F16_SPLIT: torch.float16,
+                FX_TF32_SPLIT: torch.float32}.get(
             self.precision, torch.bfloat16)
 
     def vis_shape(self):

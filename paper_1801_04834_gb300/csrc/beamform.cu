@@ -30,9 +30,9 @@
 // (4 K-steps x 2 pols x 4 products, M = 128, N = 64, K = 16) into Re X, Im X,
 // Re Y, Im Y (4 x 64 TMEM columns, double buffered: all 512 columns).
 // Warp roles (persistent, one CTA per SM): warp 0 TMA producer, warp 1 TMEM
-// allocator + MMA issuer, warps 2-5 epilogue (TMEM lane = spectrum): complex
-// voltages, or Stokes I / IQUV summed over tint consecutive spectra with warp
-// shuffles. Every mbarrier wait is bounded; on expiry the role is recorded in
+// allocator + MMA issuer, warps 2-9 epilogue (TMEM lane = spectrum; two warps
+// per lane quadrant, 32 beams each): complex voltages, or Stokes I / IQUV
+// summed over tint consecutive spectra by recursive halving across lanes. Every mbarrier wait is bounded; on expiry the role is recorded in
 // the status word, all roles leave, in-flight copies and MMAs are drained
 // (bounded) and TMEM is freed, as in the X-stage.
 #include <cuda.h>
@@ -50,7 +50,7 @@ namespace {
 
 using namespace tc;
 
-constexpr int kBfThreads = 192;
+constexpr int kBfThreads = 320;                      // TMA, MMA, 8 epilogue warps
 constexpr int kDS = 2;                               // data stages
 constexpr int kWS = 4;                               // weight stages
 constexpr unsigned kHalfBytes = 64u * 128u;          // 64 stations x 64 spectra x 2 B
@@ -70,7 +70,6 @@ struct BfParams {
     long long n_items;       // SB * C * ntile
     int ntile;               // 128-spectrum tiles per channel
     int C, S, NB, NBQ;       // channels, spectra, beams, beam quarters
-    int mode, tint;
     unsigned bf16;
     float inv_scale, inv_scale2;
     long long timeout_cycles;
@@ -139,6 +138,32 @@ __global__ void bf_weight_kernel(const double *__restrict__ delays, const float 
     }
 }
 
+// Sum v[0..M) over aligned groups of T lanes by recursive halving: at each
+// step a lane keeps half of its values (the upper half when the step's lane
+// bit is set) and adds its partner's copy of that half, so after the steps
+// over lane bits 1, 2, 4, ... (up to 8) lane l holds 16 / min(T, 16) sums, of
+// beams i + 8 b0 + 4 b1 + 2 b2 + b3 (b_k = bit k of l); a group of 32 adds a
+// final plain exchange across the half-warps.
+template <int M, int O, int T>
+__device__ __forceinline__ void halve(float (&v)[16], int lane)
+{
+    if constexpr (O < T && M > 1) {
+        const bool upper = (lane & O) != 0;
+#pragma unroll
+        for (int i = 0; i < M / 2; ++i) {
+            const float send = upper ? v[i] : v[i + M / 2];
+            const float keep = upper ? v[i + M / 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+        }
+        halve<M / 2, O * 2, T>(v, lane);
+    } else if constexpr (O < T) {
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], O);
+        halve<1, O * 2, T>(v, lane);
+    }
+}
+
+// MODE 0 voltages, 1 Stokes I, 2 Stokes IQUV; TINT spectra summed per output
+template <int MODE, int TINT>
 __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_constant__ BfParams P)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -171,7 +196,7 @@ __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_co
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(accf(b), 1);
-            mbar_init(acce(b), 4);
+            mbar_init(acce(b), 8);
         }
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
@@ -291,8 +316,9 @@ __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_co
         }
         __syncwarp();
     } else {
-        // ================= epilogue (warps 2..5) =================
+        // ================= epilogue (warps 2..9) =================
         const int qd = warp & 3;                              // TMEM lane quadrant of this warp
+        const int hf = (warp - 2) >> 2;                       // which 32 of the quarter's 64 beams
         const unsigned lane_off = (unsigned)(32 * qd) << 16;
         long long ait = 0;
         bool live = true;
@@ -312,7 +338,7 @@ __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_co
                 tc_fence_after();
                 const unsigned t0 = tmem_base + lane_off + (unsigned)(ab * kAccCols);
 #pragma unroll 1
-                for (int cc = 0; cc < 4; ++cc) {
+                for (int cc = 2 * hf; cc < 2 * hf + 2; ++cc) {
                     const int b0 = q * 64 + cc * 16;
                     if (b0 >= P.NB) break;
                     float xr[16], xj[16], yr[16], yj[16];
@@ -321,39 +347,57 @@ __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_co
                     tmem_ld16(t0 + 128 + 16 * cc, yr);
                     tmem_ld16(t0 + 192 + 16 * cc, yj);
                     tmem_ld_wait();
+                    if constexpr (MODE == 0) {
+                        if (s < P.S) {
+                            const float is = P.inv_scale;
 #pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) {
-                        const int b = b0 + jj;
-                        if (b >= P.NB) break;
-                        const long long row = (sb * P.NB + b) * P.C + c;
-                        if (P.mode == 0) {
-                            if (s < P.S) {
-                                const float is = P.inv_scale;
-                                *reinterpret_cast<float4 *>(P.out + (row * P.S + s) * 4) =
-                                    make_float4(xr[jj] * is, xj[jj] * is, yr[jj] * is, yj[jj] * is);
+                            for (int jj = 0; jj < 16; ++jj) {
+                                const int b = b0 + jj;
+                                if (b < P.NB)
+                                    *reinterpret_cast<float4 *>(P.out + (((sb * P.NB + b) * P.C + c) * P.S + s) * 4) =
+                                        make_float4(xr[jj] * is, xj[jj] * is, yr[jj] * is, yj[jj] * is);
                             }
-                            continue;
                         }
-                        // Stokes of this spectrum (padded spectra are zero), then sum over tint lanes
-                        const float xx = xr[jj] * xr[jj] + xj[jj] * xj[jj];
-                        const float yy = yr[jj] * yr[jj] + yj[jj] * yj[jj];
-                        float st4[4];
-                        st4[0] = xx + yy;
-                        st4[1] = xx - yy;
-                        st4[2] = 2.f * (xr[jj] * yr[jj] + xj[jj] * yj[jj]);   // 2 Re(X conj Y)
-                        st4[3] = 2.f * (xj[jj] * yr[jj] - xr[jj] * yj[jj]);   // 2 Im(X conj Y)
-                        const int nq = P.mode == 1 ? 1 : 4;
-                        for (int k = 0; k < nq; ++k)
-                            for (int off = 1; off < P.tint; off <<= 1)
-                                st4[k] += __shfl_xor_sync(0xffffffffu, st4[k], off);
-                        if (s < P.S && (lane % P.tint) == 0) {
-                            const long long so = row * (P.S / P.tint) + s / P.tint;
-                            const float is2 = P.inv_scale2;
-                            if (P.mode == 1)
-                                P.out[so] = st4[0] * is2;
+                    } else {
+                        // Stokes of this lane's spectrum for 16 beams (padded spectra are zero)
+                        float sI[16], sQ[16], sU[16], sV[16];
+#pragma unroll
+                        for (int jj = 0; jj < 16; ++jj) {
+                            const float xx = fmaf(xr[jj], xr[jj], xj[jj] * xj[jj]);
+                            const float yy = fmaf(yr[jj], yr[jj], yj[jj] * yj[jj]);
+                            sI[jj] = xx + yy;
+                            if constexpr (MODE == 2) {
+                                sQ[jj] = xx - yy;
+                                sU[jj] = 2.f * fmaf(xr[jj], yr[jj], xj[jj] * yj[jj]);    // 2 Re(X conj Y)
+                                sV[jj] = 2.f * fmaf(xj[jj], yr[jj], -xr[jj] * yj[jj]);   // 2 Im(X conj Y)
+                            }
+                        }
+                        // sum over the TINT spectra of each lane group; lane then holds kM beams
+                        halve<16, 1, TINT>(sI, lane);
+                        if constexpr (MODE == 2) {
+                            halve<16, 1, TINT>(sQ, lane);
+                            halve<16, 1, TINT>(sU, lane);
+                            halve<16, 1, TINT>(sV, lane);
+                        }
+                        constexpr int kG = TINT < 16 ? TINT : 16;       // lanes sharing one set of beams
+                        constexpr int kM = 16 / kG;                     // beams held per lane
+                        int boff = 0;                                   // first beam of this lane's share
+#pragma unroll
+                        for (int k = 0; (1 << k) < kG; ++k) boff += ((lane >> k) & 1) * (8 >> k);
+                        const int sg = s - lane % TINT;                 // first spectrum of the lane group
+                        const bool writer = sg < P.S && (TINT < 32 || lane < 16);
+                        const long long so = sg / TINT;
+                        const float is2 = P.inv_scale2;
+#pragma unroll
+                        for (int i = 0; i < kM; ++i) {
+                            const int b = b0 + boff + i;
+                            if (!writer || b >= P.NB) continue;
+                            const long long o = ((sb * P.NB + b) * P.C + c) * (P.S / TINT) + so;
+                            if constexpr (MODE == 1)
+                                P.out[o] = sI[i] * is2;
                             else
-                                *reinterpret_cast<float4 *>(P.out + so * 4) =
-                                    make_float4(st4[0] * is2, st4[1] * is2, st4[2] * is2, st4[3] * is2);
+                                *reinterpret_cast<float4 *>(P.out + o * 4) =
+                                    make_float4(sI[i] * is2, sQ[i] * is2, sU[i] * is2, sV[i] * is2);
                         }
                     }
                 }
@@ -393,6 +437,17 @@ EncodeTiledFn bf_encode_fn()
 }
 
 constexpr size_t bf_smem_bytes() { return 1024 + (size_t)kDS * kDataBytes + (size_t)kWS * kWBytes + 8 * kNumBars + 16; }
+
+template <int MODE, int TINT>
+cudaError_t bf_launch(const BfParams &P, unsigned grid, cudaStream_t st)
+{
+    constexpr size_t smem = bf_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(beamform_kernel<MODE, TINT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    beamform_kernel<MODE, TINT><<<grid, kBfThreads, smem, st>>>(P);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -453,19 +508,28 @@ cudaError_t launch_beamform(const Handle &h, const void *corr, int NB, const dou
     P.S = S;
     P.NB = NB;
     P.NBQ = NB_pad / 64;
-    P.mode = mode;
-    P.tint = tint;
     P.bf16 = bf16;
     P.inv_scale = 1.0f / h.operand_scale;
     P.inv_scale2 = 1.0f / (h.operand_scale * h.operand_scale);
     P.timeout_cycles = h.tc_timeout_cycles;
-    constexpr size_t smem = bf_smem_bytes();
-    e = cudaFuncSetAttribute(beamform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const long long grid = std::min<long long>(P.n_items, h.num_sms);
     if (grid <= 0) return cudaSuccess;
-    beamform_kernel<<<(unsigned)grid, kBfThreads, smem, st>>>(P);
-    return cudaGetLastError();
+    switch (mode * 64 + tint) {
+    case 0 * 64 + 1: return bf_launch<0, 1>(P, (unsigned)grid, st);
+    case 1 * 64 + 1: return bf_launch<1, 1>(P, (unsigned)grid, st);
+    case 1 * 64 + 2: return bf_launch<1, 2>(P, (unsigned)grid, st);
+    case 1 * 64 + 4: return bf_launch<1, 4>(P, (unsigned)grid, st);
+    case 1 * 64 + 8: return bf_launch<1, 8>(P, (unsigned)grid, st);
+    case 1 * 64 + 16: return bf_launch<1, 16>(P, (unsigned)grid, st);
+    case 1 * 64 + 32: return bf_launch<1, 32>(P, (unsigned)grid, st);
+    case 2 * 64 + 1: return bf_launch<2, 1>(P, (unsigned)grid, st);
+    case 2 * 64 + 2: return bf_launch<2, 2>(P, (unsigned)grid, st);
+    case 2 * 64 + 4: return bf_launch<2, 4>(P, (unsigned)grid, st);
+    case 2 * 64 + 8: return bf_launch<2, 8>(P, (unsigned)grid, st);
+    case 2 * 64 + 16: return bf_launch<2, 16>(P, (unsigned)grid, st);
+    case 2 * 64 + 32: return bf_launch<2, 32>(P, (unsigned)grid, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace fxi

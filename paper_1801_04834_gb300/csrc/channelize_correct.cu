@@ -42,7 +42,7 @@ namespace {
 
 using namespace ppf;
 
-// OUT: 1 FP32 interleaved, 2 FP16 planar, 3 BF16 planar, 4 split FP16 planar
+// OUT: 1 FP32 interleaved, 2 FP16 planar, 3 BF16 planar, 4 split FP16 planar, 5 FP32 planar
 // per-round factor table: [kRound][IC inputs][PHC], rows padded so that FFT
 // pass 2 (lanes = 8 or 16 consecutive channels x inputs) reads it conflict free
 template <int C>
@@ -264,7 +264,29 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
         }
         __syncthreads();
         // ---- write out ----
-        {
+        if constexpr (OUT == 5) {
+            // FP32 planar: per (channel, input) 16 spectra = 64 bytes per plane
+            float *out = reinterpret_cast<float *>(corr);
+            const long long pstride = (long long)I_pad * S_pad;
+            for (int e = tid; e < C * IC; e += NT) {
+                const int il = e % IC, kout = e / IC;
+                const int i = 2 * n0 + il;
+                if (i >= I) continue;
+                const float2 *src = u + kout * SROW + il * (kRound + 1);
+                float4 *re = reinterpret_cast<float4 *>(out + (((long long)sb * C + kout) * 2) * pstride +
+                                                        (long long)i * S_pad + sr);
+                float4 *im = re + pstride / 4;
+#pragma unroll
+                for (int q = 0; q < kRound / 4; ++q) {
+                    float2 v[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        v[t] = (sr + 4 * q + t < S) ? src[4 * q + t] : make_float2(0.f, 0.f);
+                    re[q] = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
+                    im[q] = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
+                }
+            }
+        } else {
             constexpr int planes = (OUT == 4) ? 4 : 2;
             unsigned short *out = reinterpret_cast<unsigned short *>(corr);
             const long long pstride = (long long)I_pad * S_pad;
@@ -342,7 +364,7 @@ cudaError_t launch_t(const Handle &h, const void *raw, void *corr, const float *
     auto kern = ppf_correct_kernel<C, T, TIn, OUT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const float scale = (OUT == 1) ? 1.f : h.operand_scale;
+    const float scale = (OUT == 1 || OUT == 5) ? 1.f : h.operand_scale;
     kern<<<grid, Cfg::NT, smem, st>>>(reinterpret_cast<const TIn *>(raw), corr, h.d_taps, h.d_twiddle, h.d_phase,
                                       bandpass, gains, N, S, h.I_pad, h.S_pad, scale, rpc, flags);
     e = cudaGetLastError();
@@ -351,8 +373,10 @@ cudaError_t launch_t(const Handle &h, const void *raw, void *corr, const float *
     if (h.I_pad > h.I || h.S_pad > S16) {
         const long long rows = (long long)SB * C * (OUT == 4 ? 4 : 2) * h.I_pad;
         if (rows > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+        // zero bits are zero in either element size: FP32 rows are twice as many 16-bit words
+        const int w = OUT == 5 ? 2 : 1;
         planar_pad_kernel<<<(unsigned)rows, 64, 0, st>>>(reinterpret_cast<unsigned short *>(corr), rows, h.I, h.I_pad,
-                                                          S16, h.S_pad);
+                                                          w * S16, w * h.S_pad);
         e = cudaGetLastError();
     }
     return e;
@@ -365,6 +389,7 @@ cudaError_t launch_out(const Handle &h, const void *raw, void *corr, const float
     case FX_F32: return launch_t<C, T, TIn, 1>(h, raw, corr, bp, g, fl, st);
     case FX_F16: return launch_t<C, T, TIn, 2>(h, raw, corr, bp, g, fl, st);
     case FX_BF16: return launch_t<C, T, TIn, 3>(h, raw, corr, bp, g, fl, st);
+    case FX_TF32_SPLIT: return launch_t<C, T, TIn, 5>(h, raw, corr, bp, g, fl, st);
     default: return launch_t<C, T, TIn, 4>(h, raw, corr, bp, g, fl, st);
     }
 }

@@ -94,7 +94,7 @@ correct_f32_kernel(const float2 *__restrict__ chan, const float2 *__restrict__ t
 constexpr int kPT_C = 8, kPT_S = 64, kPT_I = 8;
 constexpr int kPT_ROW = kPT_S + 2;   // float2 pad per (input, channel) row
 
-template <int MODE>  // 1: F16, 2: BF16, 3: F16 split
+template <int MODE>  // 1: F16, 2: BF16, 3: F16 split, 4: FP32 (TF32 split X-stage)
 __global__ void __launch_bounds__(kNT)
 correct_planar_kernel(const float2 *__restrict__ chan, const float2 *__restrict__ table,
                       const float *__restrict__ bandpass, const float2 *__restrict__ gains,
@@ -137,6 +137,15 @@ correct_planar_kernel(const float2 *__restrict__ chan, const float2 *__restrict_
         const float2 *src = tile + (il * kPT_C + c) * kPT_ROW + g8 * 8;
         const long long base = (((long long)sb * C + c0 + c) * planes) * plane_stride +
                                (long long)(i0 + il) * S_pad + s0 + g8 * 8;
+        if constexpr (MODE == 4) {
+            float4 *re = reinterpret_cast<float4 *>(reinterpret_cast<float *>(corr) + base);
+            float4 *im = reinterpret_cast<float4 *>(reinterpret_cast<float *>(corr) + base + plane_stride);
+            re[0] = make_float4(src[0].x, src[1].x, src[2].x, src[3].x);
+            re[1] = make_float4(src[4].x, src[5].x, src[6].x, src[7].x);
+            im[0] = make_float4(src[0].y, src[1].y, src[2].y, src[3].y);
+            im[1] = make_float4(src[4].y, src[5].y, src[6].y, src[7].y);
+            continue;
+        }
         unsigned short re_hi[8], im_hi[8], re_lo[8], im_lo[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -263,6 +272,10 @@ cudaError_t launch_correct(const Handle &h, const float2 *chan, const float *ban
     case FX_BF16:
         correct_planar_kernel<2><<<grid, kNT, 0, st>>>(chan, h.d_phase, bandpass, gains, corr, N, C, S,
                                                        h.I_pad, h.S_pad, h.operand_scale);
+        break;
+    case FX_TF32_SPLIT:
+        correct_planar_kernel<4><<<grid, kNT, 0, st>>>(chan, h.d_phase, bandpass, gains, corr, N, C, S,
+                                                       h.I_pad, h.S_pad, 1.f);
         break;
     default:
         correct_planar_kernel<3><<<grid, kNT, 0, st>>>(chan, h.d_phase, bandpass, gains, corr, N, C, S,

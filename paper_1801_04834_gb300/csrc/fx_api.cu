@@ -42,6 +42,28 @@ bool is_pow2(float x)
 
 struct fx_handle : fxi::Handle {};
 
+namespace fxi {
+
+bool xstage_supported(const Handle &h)
+{
+    if (h.p.precision == FX_F32) return true;
+    if (h.p.precision == FX_TF32_SPLIT) return h.I_pad <= 128;
+    int rl, stg;
+    unsigned sb;
+    return xtc_plan(h, &rl, &stg, &sb);
+}
+
+cudaError_t launch_xstage(const Handle &h, const void *corr, float2 *vis, cudaStream_t st)
+{
+    switch (h.p.precision) {
+    case FX_F32: return launch_xcorr_f32(h, static_cast<const float2 *>(corr), vis, st);
+    case FX_TF32_SPLIT: return launch_xcorr_tf32(h, static_cast<const float *>(corr), vis, st);
+    default: return launch_xcorr_tc(h, corr, vis, st);
+    }
+}
+
+}  // namespace fxi
+
 extern "C" const char *fx_last_error(void) { return g_err; }
 
 extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
@@ -61,7 +83,7 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
                     p.n_channels, p.n_taps);
     if (p.format != FX_CI16 && p.format != FX_CI8 && p.format != FX_CI4)
         return fail(FX_ERR_INVALID, "bad format %d", p.format);
-    if (p.precision < FX_F32 || p.precision > FX_F16_SPLIT)
+    if (p.precision < FX_F32 || p.precision > FX_TF32_SPLIT)
         return fail(FX_ERR_INVALID, "bad precision %d", p.precision);
     if (!(p.sample_rate_hz > 0)) return fail(FX_ERR_INVALID, "sample_rate_hz must be > 0");
     if (!p.h_subband_centre_hz) return fail(FX_ERR_INVALID, "h_subband_centre_hz is NULL");
@@ -76,8 +98,10 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
         return fail(FX_ERR_UNSUPPORTED, "the beamformer needs FX_F16 or FX_BF16 operands and at most 64 stations");
     float scale = p.operand_scale == 0.f ? 1.f : p.operand_scale;
     if (!is_pow2(scale)) return fail(FX_ERR_INVALID, "operand_scale must be a power of two");
-    if (p.precision == FX_F32 && scale != 1.f)
+    if ((p.precision == FX_F32 || p.precision == FX_TF32_SPLIT) && scale != 1.f)
         return fail(FX_ERR_INVALID, "operand_scale applies to FP16/BF16 only");
+    if (p.precision == FX_TF32_SPLIT && p.n_stations > 64)
+        return fail(FX_ERR_UNSUPPORTED, "FX_TF32_SPLIT handles at most 64 stations");
     const long long I = 2LL * p.n_stations;
     const long long S = p.n_spectra;
     const long long SB = p.n_subbands;
@@ -186,6 +210,7 @@ extern "C" fx_status fx_query_sizes(const fx_handle *h, fx_sizes *o)
     case FX_F32: o->corr_bytes = SB * C * S * N * 2 * sizeof(float2); o->corr_planes = 0; break;
     case FX_F16:
     case FX_BF16: o->corr_bytes = SB * C * 2 * (size_t)h->I_pad * h->S_pad * 2; o->corr_planes = 2; break;
+    case FX_TF32_SPLIT: o->corr_bytes = SB * C * 2 * (size_t)h->I_pad * h->S_pad * 4; o->corr_planes = 2; break;
     default: o->corr_bytes = SB * C * 4 * (size_t)h->I_pad * h->S_pad * 2; o->corr_planes = 4; break;
     }
     o->vis_bytes = SB * C * (size_t)h->B * 4 * sizeof(float2);
@@ -272,11 +297,7 @@ extern "C" fx_status fx_process_host(fx_handle *h, const void *h_raw, const doub
     if (st) return st;
     if (!h->pipe) return fail(FX_ERR_INVALID, "%s: handle was created with host_chunk_subbands = 0", who);
     if (!h_raw || !h_vis || !h_delay_begin || !h_delay_end) return fail(FX_ERR_INVALID, "%s: NULL buffer", who);
-    if (h->p.precision != FX_F32) {
-        int rl, stg;
-        unsigned sb;
-        if (!fxi::xtc_plan(*h, &rl, &stg, &sb)) return fail(FX_ERR_UNSUPPORTED, "%s: no tensor-core plan", who);
-    }
+    if (!fxi::xstage_supported(*h)) return fail(FX_ERR_UNSUPPORTED, "%s: no tensor-core plan", who);
     return after_launch(fxi::pipe_run(*h, h_raw, h_delay_begin, h_delay_end, h_bandpass, h_gains, h_vis,
                                       (cudaStream_t)stream),
                         who);
@@ -331,11 +352,7 @@ extern "C" fx_status fx_stream_block(fx_handle *h, const void *d_new, const int 
         ((uintptr_t)d_gains & 7) || ((uintptr_t)d_bandpass & 3) || ((uintptr_t)d_delay_begin & 7) ||
         ((uintptr_t)d_delay_end & 7))
         return fail(FX_ERR_INVALID, "%s: misaligned buffer", who);
-    if (d_vis && h->p.precision != FX_F32) {
-        int rl, stg;
-        unsigned sb;
-        if (!fxi::xtc_plan(*h, &rl, &stg, &sb)) return fail(FX_ERR_UNSUPPORTED, "%s: no tensor-core plan", who);
-    }
+    if (d_vis && !fxi::xstage_supported(*h)) return fail(FX_ERR_UNSUPPORTED, "%s: no tensor-core plan", who);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = fxi::launch_stream_assemble(*h, d_new, d_coarse_shift, s);
     if (e == cudaSuccess) e = fxi::launch_phase_table(*h, d_delay_begin, d_delay_end, s);
@@ -344,8 +361,7 @@ extern "C" fx_status fx_stream_block(fx_handle *h, const void *d_new, const int 
                                            d_corr, s, d_flags);
     if (e == cudaSuccess && d_vis) {
         float2 *vis = reinterpret_cast<float2 *>(d_vis);
-        e = h->p.precision == FX_F32 ? fxi::launch_xcorr_f32(*h, reinterpret_cast<const float2 *>(d_corr), vis, s)
-                                     : fxi::launch_xcorr_tc(*h, d_corr, vis, s);
+        e = fxi::launch_xstage(*h, d_corr, vis, s);
     }
     if (e == cudaSuccess && d_counts) e = fxi::launch_baseline_counts(*h, d_flags, d_counts, s);
     if (e == cudaSuccess) e = fxi::launch_stream_history(*h, d_new, s);
@@ -380,18 +396,9 @@ extern "C" fx_status fx_correlate(fx_handle *h, const void *d_corr, float *d_vis
         return fail(FX_ERR_INVALID, "fx_correlate: corr must be 128-byte and vis 16-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     float2 *vis = reinterpret_cast<float2 *>(d_vis);
-    cudaError_t e;
-    if (h->p.precision == FX_F32) {
-        e = fxi::launch_xcorr_f32(*h, reinterpret_cast<const float2 *>(d_corr), vis, s);
-    } else {
-        int rl, stg;
-        unsigned sb;
-        if (!fxi::xtc_plan(*h, &rl, &stg, &sb))
-            return fail(FX_ERR_UNSUPPORTED,
-                        "fx_correlate: tensor-core X-stage needs <= 128 stations (<= 100 for split FP16)");
-        e = fxi::launch_xcorr_tc(*h, d_corr, vis, s);
-    }
-    return after_launch(e, "fx_correlate");
+    if (!fxi::xstage_supported(*h))
+        return fail(FX_ERR_UNSUPPORTED, "fx_correlate: tensor-core X-stage needs <= 128 stations (<= 100 for split FP16)");
+    return after_launch(fxi::launch_xstage(*h, d_corr, vis, s), "fx_correlate");
 }
 
 extern "C" fx_status fx_apply_gains(fx_handle *h, const float *d_raw_vis, const float *d_gains,

@@ -40,6 +40,7 @@ static size_t corr_bytes_per_subband(const Handle &h)
     case FX_F32: return C * S * h.I * sizeof(float2);
     case FX_F16:
     case FX_BF16: return C * 2 * (size_t)h.I_pad * h.S_pad * 2;
+    case FX_TF32_SPLIT: return C * 2 * (size_t)h.I_pad * h.S_pad * 4;
     default: return C * 4 * (size_t)h.I_pad * h.S_pad * 2;
     }
 }
@@ -154,10 +155,7 @@ cudaError_t pipe_run(Handle &h, const void *h_raw, const double *h_tb, const dou
         RUN_TRY(launch_phase_table(v, P.d_tau, P.d_tau + N, P.s_comp));
         RUN_TRY(launch_channelize_correct(v, P.d_raw[b], h_bp ? P.d_bp : nullptr, h_gains ? P.d_gain : nullptr,
                                           P.d_corr[b], P.s_comp));
-        if (h.p.precision == FX_F32)
-            RUN_TRY(launch_xcorr_f32(v, static_cast<const float2 *>(P.d_corr[b]), P.d_vis[b], P.s_comp));
-        else
-            RUN_TRY(launch_xcorr_tc(v, P.d_corr[b], P.d_vis[b], P.s_comp));
+        RUN_TRY(launch_xstage(v, P.d_corr[b], P.d_vis[b], P.s_comp));
         RUN_TRY(cudaEventRecord(P.comp_done[b], P.s_comp));
         // download
         RUN_TRY(cudaStreamWaitEvent(P.s_out, P.comp_done[b], 0));

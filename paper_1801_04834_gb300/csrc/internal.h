@@ -87,6 +87,13 @@ size_t bf_weight_bytes(const Handle &h, int n_beams);
 cudaError_t launch_beamform(const Handle &h, const void *corr, int n_beams, const double *delays,
                             const float *weights, int mode, int tint, float *out, cudaStream_t st);
 
+// xcorr_tf32.cu (FX_TF32_SPLIT)
+cudaError_t launch_xcorr_tf32(const Handle &h, const float *corr, float2 *vis, cudaStream_t st);
+
+// fx_api.cu: the X-stage of the handle's precision
+bool xstage_supported(const Handle &h);
+cudaError_t launch_xstage(const Handle &h, const void *corr, float2 *vis, cudaStream_t st);
+
 // xcorr_tc.cu
 bool xtc_plan(const Handle &h, int *rload, int *stages, unsigned *stage_bytes);
 cudaError_t launch_xcorr_tc(const Handle &h, const void *corr, float2 *vis, cudaStream_t st);

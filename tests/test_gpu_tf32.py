@@ -1,0 +1,94 @@
+"""FP32-accurate tensor-core X-stage (FX_TF32_SPLIT) against the FP64 oracle.
+
+Each FP32 corrected sample x is split in the kernel into hi = x with the 13
+low mantissa bits cleared (exactly a TF32 value) and lo = x - hi (exact in
+FP32); the MMAs form hi hi' + hi lo' + lo hi' with FP32 accumulation. The
+dropped lo lo' term and the TF32 rounding of lo are each below 2^-20 of a
+product, so the visibilities must meet the FP32 path's bound: normwise
+relative error per subband below 1e-5 against the oracle, and agreement with
+the FFMA X-stage on the same corrected block to the same level.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from test_gpu_parity import make_corr, per_subband_rel, tone_block
+
+pytestmark = pytest.mark.gpu
+FS = synth.SAMPLE_RATE_HZ
+
+
+def d(a, dt=torch.float32):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
+
+
+CASES = [  # (fmt, SB, N, C, S)
+    (synth.CI16, 1, 8, 64, 768),
+    (synth.CI16, 2, 5, 16, 33),
+    (synth.CI8, 2, 64, 64, 100),
+    (synth.CI8, 1, 48, 256, 64),
+    (synth.CI16, 2, 1, 16, 20),
+    (synth.CI4, 1, 17, 64, 96),
+]
+
+
+@pytest.mark.parametrize("fmt,SB,N,C,S", CASES)
+def test_tf32_split_vs_oracle(fmt, SB, N, C, S):
+    sigma = {synth.CI16: 100.0, synth.CI8: 20.0, synth.CI4: 2.5}[fmt]
+    if fmt == synth.CI4:
+        rng = np.random.default_rng(S)
+        tau = rng.uniform(-5e-6, 5e-6, N)
+        blk = synth.make_block(40 + N, fmt, SB, N, C, S, sigma=sigma,
+                               tones=[synth.Tone(amp=3.0, channel=5, delays=tau)])
+    else:
+        blk, tau, _ = tone_block(70 + N + C, fmt, SB, N, C, S, sigma=sigma)
+    ref = oracle.fx(blk.fmt, blk.raw, 16, C, S, blk.taps, FS, blk.centres, tau, tau)
+    c = make_corr(blk, precision=4)
+    c32 = make_corr(blk, precision=0)
+    raw = torch.from_numpy(blk.raw).cuda()
+    t = d(tau, torch.float64)
+    fused = c.correlate(c.channelize_correct(raw, t, t))
+    two = c.correlate(c.correct(c.channelize(raw), t, t))
+    ffma = c32.correlate(c32.channelize_correct(raw, t, t))
+    torch.cuda.synchronize()
+    for vis in (fused, two):
+        e = per_subband_rel(vis.cpu().numpy().astype(np.float64), ref)
+        assert np.all(e < 1e-5), e
+    e = per_subband_rel(fused.cpu().numpy().astype(np.float64), ffma.cpu().numpy().astype(np.float64))
+    assert np.all(e < 1e-5), e
+    c.close()
+    c32.close()
+
+
+def test_tf32_split_planar_operands_match_fp32_path():
+    """The FP32 planar operands equal the FP32 interleaved corrected block
+    (same fused kernel, same arithmetic, only the layout differs), and the
+    padding is zero."""
+    blk, tau, _ = tone_block(5, synth.CI16, 2, 7, 64, 50)
+    c = make_corr(blk, precision=4)
+    c32 = make_corr(blk, precision=0)
+    raw = torch.from_numpy(blk.raw).cuda()
+    t = d(tau, torch.float64)
+    p = torch.full(c.corr_shape(), float("nan"), dtype=torch.float32, device="cuda")
+    c.channelize_correct(raw, t, t, out=p)
+    f = c32.channelize_correct(raw, t, t)                      # [SB][C][S][N][2][2]
+    torch.cuda.synchronize()
+    I, S = c.I, c.S
+    re = p[:, :, 0, :I, :S].permute(0, 1, 3, 2)               # [SB][C][S][I]
+    im = p[:, :, 1, :I, :S].permute(0, 1, 3, 2)
+    f = f.reshape(c.SB, c.C, S, I, 2)
+    assert torch.equal(re, f[..., 0]) and torch.equal(im, f[..., 1])
+    assert torch.all(p[:, :, :, I:, :] == 0) and torch.all(p[:, :, :, :, S:] == 0)
+    c.close()
+    c32.close()
+
+
+def test_tf32_split_limits():
+    blk = synth.make_block(1, synth.CI16, 1, 65, 16, 8)
+    with pytest.raises(RuntimeError):
+        make_corr(blk, precision=4)                             # more than 64 stations
+    blk = synth.make_block(1, synth.CI16, 1, 4, 16, 8)
+    with pytest.raises(RuntimeError):
+        make_corr(blk, precision=4, operand_scale=0.5)          # no operand scaling in FP32
