@@ -25,8 +25,8 @@
 // the paper does for delay compensation).
 //
 // Work item = (subband, channel, 128-spectrum tile). The CTA loads the four
-// data planes of an item once (64 KB, ring of 2) and walks the beams in
-// quarters of 64: a 16 KB weight tile per quarter (ring of 4), 32 MMAs
+// data planes of an item once (64 KB, ring of 3) and walks the beams in
+// quarters of 64: a 16 KB weight tile per quarter (ring of 2), 32 MMAs
 // (4 K-steps x 2 pols x 4 products, M = 128, N = 64, K = 16) into Re X, Im X,
 // Re Y, Im Y (4 x 64 TMEM columns, double buffered: all 512 columns).
 // Warp roles (persistent, one CTA per SM): warp 0 TMA producer, warp 1 TMEM
@@ -51,8 +51,8 @@ namespace {
 using namespace tc;
 
 constexpr int kBfThreads = 320;                      // TMA, MMA, 8 epilogue warps
-constexpr int kDS = 2;                               // data stages
-constexpr int kWS = 4;                               // weight stages
+constexpr int kDS = 3;                               // data stages (two loads in flight while one computes)
+constexpr int kWS = 2;                               // weight stages
 constexpr unsigned kHalfBytes = 64u * 128u;          // 64 stations x 64 spectra x 2 B
 constexpr unsigned kPlaneBytes = 2u * kHalfBytes;    // 128 spectra of one (pol, plane)
 constexpr unsigned kDataBytes = 4u * kPlaneBytes;    // (pol, plane) = 4 planes: 64 KB
@@ -60,7 +60,7 @@ constexpr unsigned kWPlane = 64u * 128u;             // 64 beams x 64 stations x
 constexpr unsigned kWBytes = 2u * kWPlane;           // re + im: 16 KB
 constexpr int kAccCols = 256;                        // Re X, Im X, Re Y, Im Y x 64 beams
 constexpr int kTmemCols = 512;
-constexpr int kNumBars = 17;                         // dfull 2, dempty 2, wfull 4, wempty 4, accf 2, acce 2, drain
+constexpr int kNumBars = 2 * kDS + 2 * kWS + 5;      // dfull, dempty, wfull, wempty, accf 2, acce 2, drain
 
 struct BfParams {
     CUtensorMap mapY;        // 4-D (spectrum, pol, station, sb*C*2 + plane)
@@ -437,6 +437,7 @@ EncodeTiledFn bf_encode_fn()
 }
 
 constexpr size_t bf_smem_bytes() { return 1024 + (size_t)kDS * kDataBytes + (size_t)kWS * kWBytes + 8 * kNumBars + 16; }
+static_assert(bf_smem_bytes() <= 227 * 1024, "beamformer stages exceed the shared memory of one CTA");
 
 template <int MODE, int TINT>
 cudaError_t bf_launch(const BfParams &P, unsigned grid, cudaStream_t st)

@@ -29,6 +29,13 @@
 // Every mbarrier wait is bounded; on expiry the role is recorded in the status
 // word, all roles leave, in-flight copies and MMAs are drained (bounded) and
 // TMEM is freed.
+//
+// Accumulation. The tensor core's FP32 accumulator does not round each
+// addition to nearest, so a long chain of MMAs into one accumulator drifts
+// (measured: 2.5e-5 normwise after 768 spectra, growing with the chain). The
+// accumulator is therefore restarted every kChunk stages (64 spectra) and the
+// epilogue adds the chunk sums into the visibilities in IEEE FP32 (the rows
+// of one channel stay in L2 while its chunks are summed).
 #include <cuda.h>
 
 #include <algorithm>
@@ -50,13 +57,14 @@ constexpr unsigned kT3Hi = 2u * kT3Plane;             // re + im, hi (converted 
 constexpr unsigned kT3Stage = 2u * kT3Hi;             // hi + lo
 constexpr int kT3TmemCols = 512;
 constexpr int kT3Bars = 4 * kT3Stages + 5;            // full, conv, empty per stage; accf 2, acce 2, drain
+constexpr int kChunk = 2;                             // stages per accumulator chain (64 spectra)
 
 struct T3Params {
     CUtensorMap map;          // 3-D (spectrum, input, sb*C*2 + plane), box {32, 128, 1}
     float2 *vis;
     int *status;
     long long n_items;        // SB * C
-    int N, I_pad, nk;         // stations, padded inputs, stages per item
+    int N, I_pad, nk;         // stations, padded inputs, stages per item (a multiple of kChunk)
     long long B;              // baselines
     long long timeout_cycles;
 };
@@ -171,7 +179,8 @@ __global__ void __launch_bounds__(kT3Threads, 1) xcorr_tf32_kernel(const __grid_
             bool ok = true, issued = false;
             const unsigned idesc = idesc_tf32(ncols, false);
             const unsigned idesc_neg = idesc_tf32(ncols, true);
-            for (long long w = blockIdx.x; w < P.n_items && ok; w += gridDim.x, ++acc_it) {
+            for (long long w = blockIdx.x; w < P.n_items && ok; w += gridDim.x) {
+              for (int ch = 0; ch < P.nk / kChunk && ok; ++ch, ++acc_it) {
                 const int ab = (int)(acc_it & 1);
                 if (!t3wait(acce_bar(ab), (unsigned)((acc_it >> 1) & 1) ^ 1u, abort_flag, P, 2)) {
                     ok = false;
@@ -180,7 +189,7 @@ __global__ void __launch_bounds__(kT3Threads, 1) xcorr_tf32_kernel(const __grid_
                 tc_fence_after();
                 const unsigned d_re = tmem_base + (unsigned)(ab * 256);
                 const unsigned d_im = d_re + 128;
-                for (int kc = 0; kc < P.nk; ++kc, ++it) {
+                for (int kc = 0; kc < kChunk; ++kc, ++it) {
                     const int s = (int)(it % kT3Stages);
                     if (!t3wait(conv_bar(s), (unsigned)((it / kT3Stages) & 1), abort_flag, P, 2)) {
                         ok = false;
@@ -216,6 +225,7 @@ __global__ void __launch_bounds__(kT3Threads, 1) xcorr_tf32_kernel(const __grid_
                 }
                 if (!ok) break;
                 mma_commit(accf_bar(ab));
+              }
             }
             if (!ok && issued) {
                 mma_commit(drain_bar);
@@ -262,10 +272,15 @@ __global__ void __launch_bounds__(kT3Threads, 1) xcorr_tf32_kernel(const __grid_
         // ================= epilogue (warps 2..5) =================
         const int qd = warp & 3;
         long long acc_it = 0;
-        for (long long w = blockIdx.x; w < P.n_items; w += gridDim.x, ++acc_it) {
+        bool live = true;
+        for (long long w = blockIdx.x; w < P.n_items && live; w += gridDim.x) {
+          for (int ch = 0; ch < P.nk / kChunk; ++ch, ++acc_it) {
             const int ab = (int)(acc_it & 1);
             const bool got = t3wait(accf_bar(ab), (unsigned)((acc_it >> 1) & 1), abort_flag, P, 3);
-            if (!__all_sync(0xffffffffu, got)) break;
+            if (!__all_sync(0xffffffffu, got)) {
+                live = false;
+                break;
+            }
             tc_fence_after();
             const int ia = 32 * qd + lane;               // this lane's row input
             const int i = ia >> 1, p = ia & 1;
@@ -273,27 +288,54 @@ __global__ void __launch_bounds__(kT3Threads, 1) xcorr_tf32_kernel(const __grid_
             const unsigned t_re = tmem_base + ((unsigned)(32 * qd) << 16) + (unsigned)(ab * 256);
             const unsigned t_im = t_re + 128;
             float2 *vrow = P.vis + w * P.B * 4;
-            for (int cc = 0; cc < ncols / 16; ++cc) {
-                const int j0 = 8 * cc;                   // first station of this 16-column chunk
-                if (j0 >= P.N) break;
-                if (j0 + 7 < i_warp_min) continue;       // whole chunk below the diagonal for this warp
-                float re[16], im[16];
-                tmem_ld16(t_re + 16 * cc, re);
-                tmem_ld16(t_im + 16 * cc, im);
-                tmem_ld_wait();
+            // two 16-column chunks at a time: TMEM loads and the loads of the
+            // running sums are all issued before any add or store
+            const int ncc = ncols / 16;
+            for (int cc0 = 0; cc0 < ncc; cc0 += 2) {
+                if (8 * cc0 >= P.N) break;
+                if (8 * cc0 + 15 < i_warp_min) continue;    // both chunks below the diagonal for this warp
+                float re[2][16], im[2][16];
+                float4 old[2][8];
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    const int j = j0 + jj;
-                    if (i <= j && j < P.N) {
-                        const long long b = (long long)j * (j + 1) / 2 + i;
-                        *reinterpret_cast<float4 *>(vrow + b * 4 + 2 * p) =
-                            make_float4(re[2 * jj], im[2 * jj], re[2 * jj + 1], im[2 * jj + 1]);
+                for (int u = 0; u < 2; ++u) {
+                    if (cc0 + u < ncc) {
+                        tmem_ld16(t_re + 16 * (cc0 + u), re[u]);
+                        tmem_ld16(t_im + 16 * (cc0 + u), im[u]);
                     }
                 }
+                if (ch > 0) {
+#pragma unroll
+                    for (int u = 0; u < 2; ++u)
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) {
+                            const int j = 8 * (cc0 + u) + jj;
+                            if (cc0 + u < ncc && i <= j && j < P.N)
+                                old[u][jj] = *reinterpret_cast<const float4 *>(
+                                    vrow + ((long long)j * (j + 1) / 2 + i) * 4 + 2 * p);
+                        }
+                }
+                tmem_ld_wait();
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const int j = 8 * (cc0 + u) + jj;
+                        if (cc0 + u < ncc && i <= j && j < P.N) {
+                            float4 v = make_float4(re[u][2 * jj], im[u][2 * jj], re[u][2 * jj + 1], im[u][2 * jj + 1]);
+                            if (ch > 0) {                // add this chunk to the sum so far (FP32, RN)
+                                v.x += old[u][jj].x;
+                                v.y += old[u][jj].y;
+                                v.z += old[u][jj].z;
+                                v.w += old[u][jj].w;
+                            }
+                            *reinterpret_cast<float4 *>(vrow + ((long long)j * (j + 1) / 2 + i) * 4 + 2 * p) = v;
+                        }
+                    }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acce_bar(ab));
+          }
         }
     }
 
@@ -330,7 +372,7 @@ cudaError_t launch_xcorr_tf32(const Handle &h, const float *corr, float2 *vis, c
 {
     EncodeTiledFn enc = t3_encode_fn();
     if (!enc) return cudaErrorNotSupported;
-    if (h.I_pad > 128 || h.S_pad % kT3K != 0) return cudaErrorNotSupported;
+    if (h.I_pad > 128 || h.S_pad % (kT3K * kChunk) != 0) return cudaErrorNotSupported;
     const long long planes = (long long)h.p.n_subbands * h.p.n_channels * 2;
     if (planes > 0x7fffffffLL) return cudaErrorInvalidValue;
     T3Params P;

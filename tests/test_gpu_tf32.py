@@ -92,3 +92,47 @@ def test_tf32_split_limits():
     blk = synth.make_block(1, synth.CI16, 1, 4, 16, 8)
     with pytest.raises(RuntimeError):
         make_corr(blk, precision=4, operand_scale=0.5)          # no operand scaling in FP32
+
+
+def _einsum_vis(y):
+    """y [SB][C][S][N][2] complex128 -> vis [SB][C][B][4][2] (b = j(j+1)/2 + i, pq = 2p + q)."""
+    SB, C, S, N, _ = y.shape
+    v = np.einsum("bcsip,bcsjq->bcijpq", y, np.conj(y))
+    out = np.zeros((SB, C, N * (N + 1) // 2, 4, 2))
+    for j in range(N):
+        for i in range(j + 1):
+            b = j * (j + 1) // 2 + i
+            blk = v[:, :, i, j].reshape(SB, C, 4)
+            out[:, :, b, :, 0] = blk.real
+            out[:, :, b, :, 1] = blk.imag
+    return out
+
+
+@pytest.mark.parametrize("exact", [True, False])
+def test_tf32_split_kernel_on_given_operands(exact):
+    """fx_correlate alone on planar FP32 operands written here: values with
+    13 zero low mantissa bits (hi only, lo = 0) and arbitrary FP32 values
+    (lo carries the low bits) against an FP64 einsum. Bound: each TMEM
+    accumulator chain spans 64 spectra = 48 MMAs, and the tensor core's
+    accumulation may lose up to 2^-24 of the running sum per MMA (48 x 2^-24 =
+    2.9e-6), plus the dropped lo lo' term (below 2^-20); chains are summed in
+    IEEE FP32. So 4e-6 normwise, against 1e-5 for the FP32 path end to end."""
+    SB, N, C, S = 2, 24, 16, 96
+    blk = synth.make_block(1, synth.CI16, SB, N, C, S)
+    c = make_corr(blk, precision=4)
+    rng = np.random.default_rng(11 + exact)
+    y = (rng.normal(size=(SB, C, S, N, 2)) + 1j * rng.normal(size=(SB, C, S, N, 2))) * 100.0
+    y = y.astype(np.complex64)
+    if exact:
+        bits = y.view(np.float32).view(np.uint32) & np.uint32(0xFFFFE000)
+        y = bits.view(np.float32).view(np.complex64)
+    planar = np.zeros(c.corr_shape(), dtype=np.float32)          # [SB][C][2][I_pad][S_pad]
+    yi = y.reshape(SB, C, S, 2 * N).transpose(0, 1, 3, 2)         # [SB][C][I][S]
+    planar[:, :, 0, :2 * N, :S] = yi.real
+    planar[:, :, 1, :2 * N, :S] = yi.imag
+    vis = c.correlate(torch.from_numpy(planar).cuda())
+    torch.cuda.synchronize()
+    ref = _einsum_vis(y.astype(np.complex128))
+    e = per_subband_rel(vis.cpu().numpy().astype(np.float64), ref)
+    assert np.all(e < 4e-6), e
+    c.close()
