@@ -106,6 +106,11 @@ typedef struct {
  * samples, and allocates one assembled raw block as workspace. */
 #define FX_FLAG_STREAMING 0x1u
 
+/* Tuning hint for the FP32 X-stage: register tiles of 2 x 4 stations (more
+ * threads per SM) instead of the default 4 x 4 from 16 stations up. Results
+ * are identical up to FP32 rounding order. */
+#define FX_FLAG_XF32_SMALL_TILES 0x2u
+
 /* Failure-detection test hook: the tensor-core X-stage issues no operand
  * loads, so its consumer waits run out after about a millisecond; the call
  * itself succeeds and fx_poll_status() then reports FX_ERR_TIMEOUT. The GPU

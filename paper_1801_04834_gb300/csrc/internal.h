@@ -26,6 +26,7 @@ struct Handle {
     int *d_status = nullptr;           // device-side error word
     int2 *d_xf32_tiles = nullptr;      // tile list of the FP32 correlator
     int xf32_ntiles = 0;
+    int xf32_rs = 2;                   // its row-tile height in stations (2 or 4)
     double *d_adj_partial = nullptr;   // [adjoint CTAs][I][3] per-CTA gradient sums
     // streaming (FX_FLAG_STREAMING): FIR history ping-pong + assembled block
     int hist_len = 0;                  // samples of history per (subband, station)
@@ -66,7 +67,7 @@ cudaError_t launch_correct_f32_noalloc(int N, int SB, int C, int S, double fs, c
                                        const float2 *gains, const float2 *chan, float2 *corr, cudaStream_t st);
 
 // xcorr_f32.cu
-int xf32_build_tiles(int N, int2 *host_tiles /* may be null: count only */);
+int xf32_build_tiles(int N, int RS, int2 *host_tiles /* may be null: count only */);
 cudaError_t launch_xcorr_f32(const Handle &h, const float2 *corr, float2 *vis, cudaStream_t st);
 
 // host_pipeline.cu

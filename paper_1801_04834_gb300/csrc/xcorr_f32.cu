@@ -10,12 +10,14 @@
 // Input is the FP32 corrected layout [SB][C][S][I] (I = 2N interleaved complex),
 // so one channel's block is one contiguous [S][I] matrix.
 //
-// Register tiling over the station triangle: a thread owns 2 stations (rows,
-// 4 inputs) x 4 stations (columns, 8 inputs) = 32 complex accumulators, i.e.
-// 64 packed FP32 FMAs (FFMA2, 128 FMAs) per time sample against 6 shared-memory
-// vector loads. Tiles
-// (row pair r, column quad q) are kept only where some pair i <= j exists
-// (2r <= 4q+3): 272 tiles for 64 stations, 4.6% more MACs than the triangle.
+// Register tiling over the station triangle: a thread owns RS stations (rows,
+// 2 RS inputs) x 4 stations (columns, 8 inputs). RS = 2: 32 complex
+// accumulators, 64 packed FP32 FMAs (FFMA2) per time sample against 6
+// shared-memory vector loads; RS = 4: 64 accumulators, 128 FFMA2 against 8
+// loads (fewer loads and operand copies per FMA, fewer threads per SM). Tiles
+// (row block r, column quad q) are kept only where some pair i <= j exists
+// (RS r <= 4q+3): for 64 stations 272 (RS = 2) or 136 (RS = 4) tiles, 4.6%
+// more MACs than the triangle.
 //
 // Threads are numbered over the flattened (channel, tile) index, up to 512 per
 // CTA (16 warps, 4 per scheduler), so a CTA covers the tiles of one to a few
@@ -26,6 +28,7 @@
 // consecutive row-pair tiles fall on consecutive 16-byte words (no bank
 // conflicts); column loads are mostly broadcasts.
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -49,8 +52,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Thread g = blockIdx.x * blockDim.x + threadIdx.x works on tile g % ntiles of
 // channel g / ntiles; the CTA stages the rows of channels [ch_first, ch_first + max_ch).
 // kKC time samples per shared-memory chunk (32, or less for very many stations).
-template <int kKC>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+template <int kKC, int RS>
+__global__ void __launch_bounds__(RS == 4 ? 256 : kMaxThreads, 1)
 xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
                  const int2 *__restrict__ tiles, int ntiles, int N, int S, int IP, int max_ch,
                  long long total_ch)
@@ -105,9 +108,10 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
     // acc[a][b] = (re, im) of x_a conj(y_b), updated with packed FP32 FMAs:
     //   acc += (xr, xi) * (yr, yr);  acc += (xi, -xr) * (yi, yi)
     // (per component the same two FMAs in the same order as the scalar form)
-    float2 acc[4][8];
+    constexpr int RA = 2 * RS;                     // row inputs of a tile
+    float2 acc[RA][8];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < RA; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b) acc[a][b] = make_float2(0.f, 0.f);
 
@@ -124,17 +128,34 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
 #pragma unroll 2
             for (int s = 0; s < kKC; ++s) {
                 const float4 *rowp = base + s * row4;
-                // row stations 2r (even half) and 2r+1 (odd half)
-                const float4 x0 = rowp[r], x1 = rowp[half + r];
+                float2 xv[RA];
+                if constexpr (RS == 2) {
+                    // row stations 2r (even half) and 2r+1 (odd half)
+                    const float4 x0 = rowp[r], x1 = rowp[half + r];
+                    xv[0] = make_float2(x0.x, x0.y);
+                    xv[1] = make_float2(x0.z, x0.w);
+                    xv[2] = make_float2(x1.x, x1.y);
+                    xv[3] = make_float2(x1.z, x1.w);
+                } else {
+                    // row stations 4r .. 4r+3
+                    const float4 x0 = rowp[2 * r], x1 = rowp[half + 2 * r], x2 = rowp[2 * r + 1],
+                                 x3 = rowp[half + 2 * r + 1];
+                    xv[0] = make_float2(x0.x, x0.y);
+                    xv[1] = make_float2(x0.z, x0.w);
+                    xv[2] = make_float2(x1.x, x1.y);
+                    xv[3] = make_float2(x1.z, x1.w);
+                    xv[4] = make_float2(x2.x, x2.y);
+                    xv[5] = make_float2(x2.z, x2.w);
+                    xv[6] = make_float2(x3.x, x3.y);
+                    xv[7] = make_float2(x3.z, x3.w);
+                }
                 // column stations 4q, 4q+1, 4q+2, 4q+3
                 const float4 y0 = rowp[2 * q], y1 = rowp[half + 2 * q], y2 = rowp[2 * q + 1],
                              y3 = rowp[half + 2 * q + 1];
-                const float2 xv[4] = {make_float2(x0.x, x0.y), make_float2(x0.z, x0.w),
-                                      make_float2(x1.x, x1.y), make_float2(x1.z, x1.w)};
                 const float yr[8] = {y0.x, y0.z, y1.x, y1.z, y2.x, y2.z, y3.x, y3.z};
                 const float yi[8] = {y0.y, y0.w, y1.y, y1.w, y2.y, y2.w, y3.y, y3.w};
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
+                for (int a = 0; a < RA; ++a) {
                     const float2 xs = make_float2(xv[a].y, -xv[a].x);
 #pragma unroll
                     for (int b = 0; b < 8; ++b) {
@@ -150,8 +171,8 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
     if (!active) return;
     const long long B = (long long)N * (N + 1) / 2;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int i = 2 * r + a / 2, p = a % 2;
+    for (int a = 0; a < RA; ++a) {
+        const int i = RS * r + a / 2, p = a % 2;
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
             const int j = 4 * q + jj;
@@ -166,15 +187,16 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
 
 }  // namespace
 
-// Tiles (r, q): row stations 2r, 2r+1; column stations 4q..4q+3; kept where
-// 2r <= 4q + 3. Ordered by q, then r, so a warp mostly shares its column loads.
-int xf32_build_tiles(int N, int2 *out)
+// Tiles (r, q): row stations RS r .. RS r + RS - 1; column stations 4q..4q+3;
+// kept where RS r <= 4q + 3. Ordered by q, then r, so a warp mostly shares
+// its column loads.
+int xf32_build_tiles(int N, int RS, int2 *out)
 {
-    const int NR = (N + 1) / 2, NQ = (N + 3) / 4;
+    const int NR = (N + RS - 1) / RS, NQ = (N + 3) / 4;
     int n = 0;
     for (int q = 0; q < NQ; ++q)
         for (int r = 0; r < NR; ++r)
-            if (2 * r <= 4 * q + 3) {
+            if (RS * r <= 4 * q + 3) {
                 if (out) out[n] = make_int2(r, q);
                 ++n;
             }
@@ -183,12 +205,12 @@ int xf32_build_tiles(int N, int2 *out)
 
 // CTA size (largest of 512, 384, 256, 128, 96, 64, 32 threads) whose touched
 // channels fit in shared memory, shrunk while the grid would not fill the GPU.
-bool xf32_geometry(int N, long long total_ch, int ntiles, int kc, int *threads, int *max_ch)
+bool xf32_geometry(int N, long long total_ch, int ntiles, int kc, int RS, int *threads, int *max_ch)
 {
     const int IP = 8 * ((N + 3) / 4);
     const size_t row_bytes = (size_t)kc * IP * sizeof(float2);
     static const int cand[] = {512, 384, 256, 128, 96, 64, 32};
-    int t = 0, mc = 0, k = 0;
+    int t = 0, mc = 0, k = RS == 4 ? 2 : 0;          // 64 accumulators: at most 256 threads
     for (; k < 7; ++k) {
         mc = (cand[k] + ntiles - 1) / ntiles + 1;
         if (2 * mc * row_bytes <= kSmemBudget) {
@@ -211,17 +233,23 @@ cudaError_t launch_xcorr_f32(const Handle &h, const float2 *corr, float2 *vis, c
 {
     const int N = h.p.n_stations, S = h.p.n_spectra;
     const int IP = 8 * ((N + 3) / 4);
+    const int RS = h.xf32_rs;
     const int nt = h.xf32_ntiles;
     const long long total = (long long)h.p.n_subbands * h.p.n_channels;
     int threads = 0, max_ch = 0, kc = 32;
     for (; kc >= 4; kc /= 2)
-        if (xf32_geometry(N, total, nt, kc, &threads, &max_ch)) break;
+        if (xf32_geometry(N, total, nt, kc, RS, &threads, &max_ch)) break;
     if (kc < 4) return cudaErrorNotSupported;   // > ~800 stations
     const size_t smem = 2ull * max_ch * kc * IP * sizeof(float2);
     const long long blocks = (total * nt + threads - 1) / threads;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    auto kern = kc == 32 ? xcorr_f32_kernel<32> : kc == 16 ? xcorr_f32_kernel<16> : kc == 8 ? xcorr_f32_kernel<8>
-                                                                                            : xcorr_f32_kernel<4>;
+    auto pick = [&](auto rs) {
+        constexpr int R = decltype(rs)::value;
+        return kc == 32 ? xcorr_f32_kernel<32, R> : kc == 16 ? xcorr_f32_kernel<16, R>
+                                               : kc == 8     ? xcorr_f32_kernel<8, R>
+                                                             : xcorr_f32_kernel<4, R>;
+    };
+    auto kern = RS == 4 ? pick(std::integral_constant<int, 4>{}) : pick(std::integral_constant<int, 2>{});
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)blocks, threads, smem, st>>>(corr, vis, h.d_xf32_tiles, nt, N, S, IP, max_ch, total);
