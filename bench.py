@@ -24,6 +24,7 @@ cpu_baseline leg).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -408,6 +409,13 @@ def run_fx(args, w):
     if ms_x_small is not None:
         kernels["correlate_tiles"] = "4x4 stations" if w["N"] >= 16 else "2x4 stations"
         kernels["correlate_2x4_tiles_ms"] = ms_x_small
+    # measured FP32 FMA throughput (registers only) beside the derived ALU peak
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+    nblk, iters = 8 * torch.cuda.get_device_properties(dev).multi_processor_count, 4096
+    probe = lambda: c.lib.fx_ffma_probe(iters, nblk, ctypes.c_void_p(sink.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    probe()
+    ms_probe = _time(probe, 3, stream)
+    kernels["fp32_fma_probe_tflops"] = nblk * 256.0 * iters * 512 / (ms_probe * 1e-3) / 1e12
 
     # ---- end to end: pinned host raw in, visibilities out, copies timed ----
     # fx_process_host: host raw in, host visibilities out, subband chunks with

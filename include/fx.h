@@ -96,9 +96,10 @@ typedef struct {
                                     subbands; 0: no host pipeline */
     int max_coarse_shift;        /* with FX_FLAG_STREAMING: largest integer-sample
                                     coarse delay per station (>= 0) */
-    int max_beams;               /* > 0: allocate the beamformer's weight table for
-                                    up to this many beams (fx_beamform); needs
-                                    precision FX_F16 or FX_BF16 and n_stations <= 64 */
+    int max_beams;               /* in [0, 256]; > 0: allocate the beamformer's weight
+                                    table for up to this many beams (fx_beamform);
+                                    needs precision FX_F16 or FX_BF16 and
+                                    n_stations <= 64 */
 } fx_params;
 
 /* Streaming form (fx_stream_block): the handle keeps the FIR history of every
@@ -240,6 +241,15 @@ fx_status fx_stream_block(fx_handle *h, const void *d_new, const int *d_coarse_s
 
 /* Zero the streaming history (the stream restarts with zeros before it). */
 fx_status fx_stream_reset(fx_handle *h, fx_stream stream);
+
+/* ---- FP32 throughput probe ------------------------------------------------
+ * Launches `blocks` CTAs of 256 threads that each run `iterations` x 128
+ * packed FP32 FMAs (FFMA2) per thread on registers only: 512 flop per
+ * iteration per thread, blocks * 256 * iterations * 512 flop in total. The
+ * caller times it (events on `stream`) to measure the FP32 FMA peak that the
+ * FP32 X-stage's roofline derives from the unit counts. d_sink: one float the
+ * kernel may write (device memory, caller-owned). No handle needed. */
+fx_status fx_ffma_probe(int iterations, int blocks, float *d_sink, fx_stream stream);
 
 /* ---- coherent beamformer -------------------------------------------------
  * Sec. "Signal processing with GPU kernels": after delay compensation and

@@ -24,9 +24,12 @@
 // per-channel step, reduced mod 2 pi, then stepped over channels in FP32 (as
 // the paper does for delay compensation).
 //
-// Work item = (subband, channel, 128-spectrum tile). The CTA loads the four
-// data planes of an item once (64 KB, ring of 3) and walks the beams in
-// quarters of 64: a 16 KB weight tile per quarter (ring of 2), 32 MMAs
+// Work item = (subband, channel, 128-spectrum tile); each CTA takes whole
+// channels. A channel's weights (16 KB per quarter of 64 beams) are loaded
+// once and stay resident while its spectrum tiles stream through (two
+// channel slots when there are at most 128 beams, so the next channel's
+// weights load meanwhile). The CTA loads the four data planes of an item once
+// (64 KB, ring of 2) and walks the beams in quarters of 64: 32 MMAs
 // (4 K-steps x 2 pols x 4 products, M = 128, N = 64, K = 16) into Re X, Im X,
 // Re Y, Im Y (4 x 64 TMEM columns, double buffered: all 512 columns).
 // Warp roles (persistent, one CTA per SM): warp 0 TMA producer, warp 1 TMEM
@@ -51,13 +54,14 @@ namespace {
 using namespace tc;
 
 constexpr int kBfThreads = 320;                      // TMA, MMA, 8 epilogue warps
-constexpr int kDS = 3;                               // data stages (two loads in flight while one computes)
-constexpr int kWS = 2;                               // weight stages
+constexpr int kDS = 2;                               // data stages
+constexpr int kWS = 2;                               // weight slots (barrier pairs)
 constexpr unsigned kHalfBytes = 64u * 128u;          // 64 stations x 64 spectra x 2 B
 constexpr unsigned kPlaneBytes = 2u * kHalfBytes;    // 128 spectra of one (pol, plane)
 constexpr unsigned kDataBytes = 4u * kPlaneBytes;    // (pol, plane) = 4 planes: 64 KB
 constexpr unsigned kWPlane = 64u * 128u;             // 64 beams x 64 stations x 2 B
-constexpr unsigned kWBytes = 2u * kWPlane;           // re + im: 16 KB
+constexpr unsigned kWBytes = 2u * kWPlane;           // re + im: 16 KB per beam quarter
+constexpr unsigned kWRegion = 4u * kWBytes;          // up to 256 beams of one channel, or 2 x 128
 constexpr int kAccCols = 256;                        // Re X, Im X, Re Y, Im Y x 64 beams
 constexpr int kTmemCols = 512;
 constexpr int kNumBars = 2 * kDS + 2 * kWS + 5;      // dfull, dempty, wfull, wempty, accf 2, acce 2, drain
@@ -67,7 +71,7 @@ struct BfParams {
     CUtensorMap mapW;        // 3-D (station, beam, sb*C*2 + plane)
     float *out;
     int *status;
-    long long n_items;       // SB * C * ntile
+    long long n_ch;          // SB * C
     int ntile;               // 128-spectrum tiles per channel
     int C, S, NB, NBQ;       // channels, spectra, beams, beam quarters
     unsigned bf16;
@@ -172,7 +176,7 @@ __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_co
     const unsigned pad = (1024 - (base_u32 & 1023)) & 1023;
     const unsigned data_u32 = base_u32 + pad;
     const unsigned w_u32 = data_u32 + kDS * kDataBytes;
-    unsigned char *ctrl = smem_raw + pad + kDS * kDataBytes + kWS * kWBytes;
+    unsigned char *ctrl = smem_raw + pad + kDS * kDataBytes + kWRegion;
     const unsigned bar0 = smem_u32(ctrl);
     auto dfull = [&](int s) { return bar0 + 8u * s; };
     auto dempty = [&](int s) { return bar0 + 8u * (kDS + s); };
@@ -214,46 +218,50 @@ __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_co
     tc_fence_after();
     const unsigned tmem_base = *tmem_slot;
 
+    // weight slots: one channel's NBQ quarters each; two slots (next channel's
+    // weights load while this channel computes) when NBQ <= 2
+    const int nslots = P.NBQ <= 2 ? 2 : 1;
+    const unsigned slot_bytes = P.NBQ <= 2 ? 2u * kWBytes : 4u * kWBytes;
+
     if (warp == 0) {
         // ================= TMA producer =================
         if (lane == 0) {
             long long d_issued = 0, w_issued = 0;
             bool ok = true;
-            for (long long w = blockIdx.x; w < P.n_items && ok; w += gridDim.x) {
-                const long long gch = w / P.ntile;
-                const int st = (int)(w % P.ntile);
-                const int ds = (int)(d_issued % kDS);
-                if (!bwait(dempty(ds), (unsigned)((d_issued / kDS) & 1) ^ 1u, abort_flag, P, 1)) {
+            for (long long gch = blockIdx.x; gch < P.n_ch && ok; gch += gridDim.x) {
+                const int sl = (int)(w_issued % nslots);
+                if (!bwait(wempty(sl), (unsigned)((w_issued / nslots) & 1) ^ 1u, abort_flag, P, 1)) {
                     ok = false;
                     break;
                 }
-                mbar_arrive_expect_tx(dfull(ds), kDataBytes);
-                const unsigned dst = data_u32 + (unsigned)ds * kDataBytes;
-                for (int p = 0; p < 2; ++p)
+                mbar_arrive_expect_tx(wfull(sl), (unsigned)P.NBQ * kWBytes);
+                for (int q = 0; q < P.NBQ; ++q)
                     for (int pl = 0; pl < 2; ++pl)
-                        for (int hh = 0; hh < 2; ++hh)
-                            tma_load_4d(dst + (unsigned)(p * 2 + pl) * kPlaneBytes + (unsigned)hh * kHalfBytes,
-                                        &P.mapY, dfull(ds), st * 128 + hh * 64, p, 0, (int)(gch * 2 + pl));
-                ++d_issued;
-                for (int q = 0; q < P.NBQ; ++q) {
-                    const int ws = (int)(w_issued % kWS);
-                    if (!bwait(wempty(ws), (unsigned)((w_issued / kWS) & 1) ^ 1u, abort_flag, P, 1)) {
+                        tma_load_3d(w_u32 + (unsigned)sl * slot_bytes + (unsigned)q * kWBytes + (unsigned)pl * kWPlane,
+                                    &P.mapW, wfull(sl), 0, q * 64, (int)(gch * 2 + pl));
+                ++w_issued;
+                for (int st = 0; st < P.ntile; ++st) {
+                    const int ds = (int)(d_issued % kDS);
+                    if (!bwait(dempty(ds), (unsigned)((d_issued / kDS) & 1) ^ 1u, abort_flag, P, 1)) {
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(wfull(ws), kWBytes);
-                    for (int pl = 0; pl < 2; ++pl)
-                        tma_load_3d(w_u32 + (unsigned)ws * kWBytes + (unsigned)pl * kWPlane, &P.mapW, wfull(ws), 0,
-                                    q * 64, (int)(gch * 2 + pl));
-                    ++w_issued;
+                    mbar_arrive_expect_tx(dfull(ds), kDataBytes);
+                    const unsigned dst = data_u32 + (unsigned)ds * kDataBytes;
+                    for (int p = 0; p < 2; ++p)
+                        for (int pl = 0; pl < 2; ++pl)
+                            for (int hh = 0; hh < 2; ++hh)
+                                tma_load_4d(dst + (unsigned)(p * 2 + pl) * kPlaneBytes + (unsigned)hh * kHalfBytes,
+                                            &P.mapY, dfull(ds), st * 128 + hh * 64, p, 0, (int)(gch * 2 + pl));
+                    ++d_issued;
                 }
             }
             if (!ok) {
                 // the last loads issued into each ring may still be in flight
                 for (long long u = d_issued > kDS ? d_issued - kDS : 0; u < d_issued; ++u)
                     drain_wait(dfull((int)(u % kDS)), (unsigned)((u / kDS) & 1), P.timeout_cycles);
-                for (long long u = w_issued > kWS ? w_issued - kWS : 0; u < w_issued; ++u)
-                    drain_wait(wfull((int)(u % kWS)), (unsigned)((u / kWS) & 1), P.timeout_cycles);
+                for (long long u = w_issued > nslots ? w_issued - nslots : 0; u < w_issued; ++u)
+                    drain_wait(wfull((int)(u % nslots)), (unsigned)((u / nslots) & 1), P.timeout_cycles);
             }
         }
     } else if (warp == 1) {
@@ -263,51 +271,54 @@ __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_co
             bool ok = true, issued = false;
             const unsigned idesc = make_idesc_major(P.bf16, 64, false, true, false);
             const unsigned idesc_neg = make_idesc_major(P.bf16, 64, true, true, false);
-            for (long long w = blockIdx.x; w < P.n_items && ok; w += gridDim.x, ++dit) {
-                const int ds = (int)(dit % kDS);
-                if (!bwait(dfull(ds), (unsigned)((dit / kDS) & 1), abort_flag, P, 2)) {
+            for (long long gch = blockIdx.x; gch < P.n_ch && ok; gch += gridDim.x, ++wit) {
+                const int sl = (int)(wit % nslots);
+                if (!bwait(wfull(sl), (unsigned)((wit / nslots) & 1), abort_flag, P, 2)) {
                     ok = false;
                     break;
                 }
-                tc_fence_after();
-                const unsigned dtile = data_u32 + (unsigned)ds * kDataBytes;
-                for (int q = 0; q < P.NBQ; ++q, ++wit, ++ait) {
-                    const int ws = (int)(wit % kWS);
-                    if (!bwait(wfull(ws), (unsigned)((wit / kWS) & 1), abort_flag, P, 2)) {
-                        ok = false;
-                        break;
-                    }
-                    const int ab = (int)(ait & 1);
-                    if (!bwait(acce(ab), (unsigned)((ait >> 1) & 1) ^ 1u, abort_flag, P, 2)) {
+                for (int st = 0; st < P.ntile && ok; ++st, ++dit) {
+                    const int ds = (int)(dit % kDS);
+                    if (!bwait(dfull(ds), (unsigned)((dit / kDS) & 1), abort_flag, P, 2)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const unsigned wt = w_u32 + (unsigned)ws * kWBytes;
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {          // 16 stations per K-step
-                        const unsigned acc = kk ? 1u : 0u;
-                        const unsigned long long bwr = smem_desc(wt + kk * 32);
-                        const unsigned long long bwj = smem_desc(wt + kWPlane + kk * 32);
-#pragma unroll
-                        for (int p = 0; p < 2; ++p) {
-                            const unsigned at = dtile + (unsigned)(p * 2) * kPlaneBytes + (unsigned)kk * 2048u;
-                            const unsigned long long ayr = smem_desc_mn(at, kHalfBytes, 1024);
-                            const unsigned long long ayj = smem_desc_mn(at + kPlaneBytes, kHalfBytes, 1024);
-                            const unsigned d_re = tmem_base + (unsigned)(ab * kAccCols + p * 128);
-                            const unsigned d_im = d_re + 64;
-                            mma_f16(d_re, ayr, bwr, idesc, acc);
-                            mma_f16(d_re, ayj, bwj, idesc_neg, 1u);
-                            mma_f16(d_im, ayr, bwj, idesc, acc);
-                            mma_f16(d_im, ayj, bwr, idesc, 1u);
+                    const unsigned dtile = data_u32 + (unsigned)ds * kDataBytes;
+                    for (int q = 0; q < P.NBQ; ++q, ++ait) {
+                        const int ab = (int)(ait & 1);
+                        if (!bwait(acce(ab), (unsigned)((ait >> 1) & 1) ^ 1u, abort_flag, P, 2)) {
+                            ok = false;
+                            break;
                         }
+                        tc_fence_after();
+                        const unsigned wt = w_u32 + (unsigned)sl * slot_bytes + (unsigned)q * kWBytes;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {      // 16 stations per K-step
+                            const unsigned acc = kk ? 1u : 0u;
+                            const unsigned long long bwr = smem_desc(wt + kk * 32);
+                            const unsigned long long bwj = smem_desc(wt + kWPlane + kk * 32);
+#pragma unroll
+                            for (int p = 0; p < 2; ++p) {
+                                const unsigned at = dtile + (unsigned)(p * 2) * kPlaneBytes + (unsigned)kk * 2048u;
+                                const unsigned long long ayr = smem_desc_mn(at, kHalfBytes, 1024);
+                                const unsigned long long ayj = smem_desc_mn(at + kPlaneBytes, kHalfBytes, 1024);
+                                const unsigned d_re = tmem_base + (unsigned)(ab * kAccCols + p * 128);
+                                const unsigned d_im = d_re + 64;
+                                mma_f16(d_re, ayr, bwr, idesc, acc);
+                                mma_f16(d_re, ayj, bwj, idesc_neg, 1u);
+                                mma_f16(d_im, ayr, bwj, idesc, acc);
+                                mma_f16(d_im, ayj, bwr, idesc, 1u);
+                            }
+                        }
+                        issued = true;
+                        mma_commit(accf(ab));                 // accumulators ready for the epilogue
                     }
-                    issued = true;
-                    mma_commit(wempty(ws));                   // weight tile free once read
-                    mma_commit(accf(ab));                     // accumulators ready for the epilogue
+                    if (!ok) break;
+                    mma_commit(dempty(ds));                   // data stage free after the last quarter
                 }
                 if (!ok) break;
-                mma_commit(dempty(ds));                       // data stage free after the last quarter
+                mma_commit(wempty(sl));                       // weight slot free after the channel
             }
             if (!ok && issued) {
                 mma_commit(drain_bar);
@@ -322,9 +333,8 @@ __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_co
         const unsigned lane_off = (unsigned)(32 * qd) << 16;
         long long ait = 0;
         bool live = true;
-        for (long long w = blockIdx.x; w < P.n_items && live; w += gridDim.x) {
-            const long long gch = w / P.ntile;
-            const int st = (int)(w % P.ntile);
+        for (long long gch = blockIdx.x; gch < P.n_ch && live; gch += gridDim.x)
+          for (int st = 0; st < P.ntile && live; ++st) {
             const long long sb = gch / P.C;
             const int c = (int)(gch % P.C);
             const int s = st * 128 + 32 * qd + lane;          // this lane's spectrum
@@ -436,7 +446,7 @@ EncodeTiledFn bf_encode_fn()
     return fn;
 }
 
-constexpr size_t bf_smem_bytes() { return 1024 + (size_t)kDS * kDataBytes + (size_t)kWS * kWBytes + 8 * kNumBars + 16; }
+constexpr size_t bf_smem_bytes() { return 1024 + (size_t)kDS * kDataBytes + (size_t)kWRegion + 8 * kNumBars + 16; }
 static_assert(bf_smem_bytes() <= 227 * 1024, "beamformer stages exceed the shared memory of one CTA");
 
 template <int MODE, int TINT>
@@ -504,7 +514,7 @@ cudaError_t launch_beamform(const Handle &h, const void *corr, int NB, const dou
     P.out = out;
     P.status = h.d_status;
     P.ntile = (S + 127) / 128;
-    P.n_items = planes / 2 * P.ntile;
+    P.n_ch = planes / 2;
     P.C = C;
     P.S = S;
     P.NB = NB;
@@ -513,7 +523,7 @@ cudaError_t launch_beamform(const Handle &h, const void *corr, int NB, const dou
     P.inv_scale = 1.0f / h.operand_scale;
     P.inv_scale2 = 1.0f / (h.operand_scale * h.operand_scale);
     P.timeout_cycles = h.tc_timeout_cycles;
-    const long long grid = std::min<long long>(P.n_items, h.num_sms);
+    const long long grid = std::min<long long>(P.n_ch, h.num_sms);
     if (grid <= 0) return cudaSuccess;
     switch (mode * 64 + tint) {
     case 0 * 64 + 1: return bf_launch<0, 1>(P, (unsigned)grid, st);

@@ -93,7 +93,7 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
     if (p.max_coarse_shift < 0 || p.max_coarse_shift > (1 << 24))
         return fail(FX_ERR_INVALID, "max_coarse_shift out of range");
     if (p.host_chunk_subbands < 0) return fail(FX_ERR_INVALID, "host_chunk_subbands must be >= 0");
-    if (p.max_beams < 0 || p.max_beams > 4096) return fail(FX_ERR_INVALID, "max_beams must be in [0, 4096]");
+    if (p.max_beams < 0 || p.max_beams > 256) return fail(FX_ERR_INVALID, "max_beams must be in [0, 256]");
     if (p.max_beams > 0 && ((p.precision != FX_F16 && p.precision != FX_BF16) || p.n_stations > 64))
         return fail(FX_ERR_UNSUPPORTED, "the beamformer needs FX_F16 or FX_BF16 operands and at most 64 stations");
     float scale = p.operand_scale == 0.f ? 1.f : p.operand_scale;
@@ -303,6 +303,14 @@ extern "C" fx_status fx_process_host(fx_handle *h, const void *h_raw, const doub
     return after_launch(fxi::pipe_run(*h, h_raw, h_delay_begin, h_delay_end, h_bandpass, h_gains, h_vis,
                                       (cudaStream_t)stream),
                         who);
+}
+
+extern "C" fx_status fx_ffma_probe(int iterations, int blocks, float *d_sink, fx_stream stream)
+{
+    if (iterations < 1 || blocks < 1 || !d_sink) return fail(FX_ERR_INVALID, "fx_ffma_probe: bad arguments");
+    const cudaError_t e = fxi::launch_ffma_probe(iterations, blocks, d_sink, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fx_ffma_probe");
+    return FX_OK;
 }
 
 extern "C" fx_status fx_beamform(fx_handle *h, const void *d_corr, int n_beams, const double *d_beam_delays,

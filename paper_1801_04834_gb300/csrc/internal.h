@@ -91,6 +91,9 @@ cudaError_t launch_beamform(const Handle &h, const void *corr, int n_beams, cons
 // xcorr_tf32.cu (FX_TF32_SPLIT)
 cudaError_t launch_xcorr_tf32(const Handle &h, const float *corr, float2 *vis, cudaStream_t st);
 
+// probe.cu
+cudaError_t launch_ffma_probe(int iterations, int blocks, float *sink, cudaStream_t st);
+
 // fx_api.cu: the X-stage of the handle's precision
 bool xstage_supported(const Handle &h);
 cudaError_t launch_xstage(const Handle &h, const void *corr, float2 *vis, cudaStream_t st);

@@ -18,7 +18,9 @@
 //   * FFT: C = R*R. Pass 1: R threads per transform, each an R-point FFT over
 //     stride-R samples in registers, times the inter-pass twiddle (host-FP64
 //     table); pass 2: R threads per transform, R-point FFTs along the other
-//     index. Shared memory holds the 16-spectrum batch between passes.
+//     index. Shared memory holds the 16-spectrum batch between passes, one
+//     row per transform in spectrum-major order (row j * IC + input), which
+//     keeps the FIR stores and both passes free of bank conflicts.
 //   * Output channel k = (m + C/2) mod C (ascending sky frequency).
 #include "internal.h"
 #include "fft_reg.cuh"
@@ -38,6 +40,7 @@ ppf_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *
     constexpr int R = Cfg::R, NPC = Cfg::NPC, NT = Cfg::NT, ROW = Cfg::ROW;
     constexpr int ROW_BYTES = C * kPols * (int)sizeof(TIn);     // one time row of one station
     constexpr int BUF_BYTES = kRound * NPC * ROW_BYTES;
+    constexpr int IC = NPC * kPols;                                // inputs of this CTA
     static_assert(ROW_BYTES % 16 == 0, "rows must be whole 16-byte chunks");
 
     extern __shared__ __align__(16) unsigned char smem[];
@@ -110,7 +113,7 @@ ppf_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *
             for (int k = 0; k < T; ++k) {
                 acc = __ffma2_rn(h[k], win[(j + k) % T], acc);
             }
-            u[((nl * kPols + p) * kRound + j) * ROW + c] = acc;
+            u[(j * IC + nl * kPols + p) * ROW + c] = acc;     // transform row j * IC + input
         }
         __syncthreads();
         if (b + 2 < nrounds) stage(b & 1, s0 + T - 1 + (b + 2) * kRound, kRound);
@@ -150,9 +153,9 @@ ppf_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *
 #pragma unroll
             for (int n2 = 0; n2 < R; ++n2) v[n2] = row[(R + 1) * k1 + n2];
             fft_reg<R>(v);
-            const int j = tr % kRound;
-            const int pp = (tr / kRound) % kPols;
-            const int n = n0 + tr / (kRound * kPols);
+            const int j = tr / IC, il = tr % IC;
+            const int pp = il % kPols;
+            const int n = n0 + il / kPols;
             const int s = s0 + b * kRound + j;
             if (s < S && n < N) {
                 float2 *out = chan + ((((long long)blockIdx.z * N + n) * kPols + pp) * S + s) * C;

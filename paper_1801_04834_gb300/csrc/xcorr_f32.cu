@@ -24,9 +24,11 @@
 // channels whatever the station count; it streams the time samples of every
 // channel it touches through shared memory in chunks of KC samples with
 // double-buffered cp.async. Within a time row the 16-byte station entries are
-// stored as [even stations][odd stations], so the two row loads of
-// consecutive row-pair tiles fall on consecutive 16-byte words (no bank
-// conflicts); column loads are mostly broadcasts.
+// grouped by station index: RS = 2 stores
+// [even stations][odd stations], RS = 4 stores [stations = 0 mod 4][1 mod 4]
+// [2 mod 4][3 mod 4], so the row loads of consecutive row tiles fall on
+// consecutive 16-byte words (no bank conflicts); column loads are mostly
+// broadcasts.
 #include <algorithm>
 #include <type_traits>
 
@@ -61,7 +63,8 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
     extern __shared__ float4 sm[];   // [2][max_ch][KC][IP/2] float4
     const int I = 2 * N;
     const int row4 = IP / 2;                       // float4 (= station entries) per time row
-    const int half = IP / 4;                       // offset of the odd-station half
+    const int half = IP / 4;                       // RS = 2: offset of the odd-station half
+    const int quarter = IP / 8;                    // RS = 4: offset between the residue groups
     const int stage_f4 = max_ch * kKC * row4;
     const int tid = threadIdx.x;
     const long long g0 = (long long)blockIdx.x * blockDim.x;
@@ -85,7 +88,8 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
             const bool ok = (2 * x < I) && (s0 + s < S);
             const float2 *src = corr;
             if (ok) src = corr + (gch * S + s0 + s) * (long long)I + 2 * x;
-            const int xs = (x & 1) * half + (x >> 1);   // [even stations][odd stations]
+            const int xs = RS == 4 ? (x & 3) * quarter + (x >> 2)    // [0 mod 4][1][2][3]
+                                   : (x & 1) * half + (x >> 1);      // [even stations][odd stations]
             cp_async16(dst0 + rr * row4 + xs, src, ok ? 16 : 0);
             x += dx;
             rr += dr;
@@ -138,8 +142,8 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
                     xv[3] = make_float2(x1.z, x1.w);
                 } else {
                     // row stations 4r .. 4r+3
-                    const float4 x0 = rowp[2 * r], x1 = rowp[half + 2 * r], x2 = rowp[2 * r + 1],
-                                 x3 = rowp[half + 2 * r + 1];
+                    const float4 x0 = rowp[r], x1 = rowp[quarter + r], x2 = rowp[2 * quarter + r],
+                                 x3 = rowp[3 * quarter + r];
                     xv[0] = make_float2(x0.x, x0.y);
                     xv[1] = make_float2(x0.z, x0.w);
                     xv[2] = make_float2(x1.x, x1.y);
@@ -150,8 +154,18 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
                     xv[7] = make_float2(x3.z, x3.w);
                 }
                 // column stations 4q, 4q+1, 4q+2, 4q+3
-                const float4 y0 = rowp[2 * q], y1 = rowp[half + 2 * q], y2 = rowp[2 * q + 1],
-                             y3 = rowp[half + 2 * q + 1];
+                float4 y0, y1, y2, y3;
+                if constexpr (RS == 2) {
+                    y0 = rowp[2 * q];
+                    y1 = rowp[half + 2 * q];
+                    y2 = rowp[2 * q + 1];
+                    y3 = rowp[half + 2 * q + 1];
+                } else {
+                    y0 = rowp[q];
+                    y1 = rowp[quarter + q];
+                    y2 = rowp[2 * quarter + q];
+                    y3 = rowp[3 * quarter + q];
+                }
                 const float yr[8] = {y0.x, y0.z, y1.x, y1.z, y2.x, y2.z, y3.x, y3.z};
                 const float yi[8] = {y0.y, y0.w, y1.y, y1.w, y2.y, y2.w, y3.y, y3.w};
 #pragma unroll
