@@ -720,8 +720,8 @@ def measure_beamformer(args, dev):
     b_ms = _time(beams, args.steps, stream)
     peaks, _ = measured_peaks()
     nb_pad = (NB + 63) // 64 * 64
-    wbytes = SB * C * 2 * nb_pad * 64 * 2
-    bf_bytes = c.sizes.corr_bytes + 2 * wbytes + out.numel() * 4     # operands + weight table + Stokes I
+    wbytes = SB * C * 3 * nb_pad * 64 * 2                             # planes (im, re, -im) per beam quarter
+    bf_bytes = c.sizes.corr_bytes + 2 * wbytes + out.numel() * 4     # operands + weight table (write, read) + Stokes I
     useful = 8.0 * NB * N * 2 * S * C * SB
     sky_s = S * C / synth.SAMPLE_RATE_HZ
     res = {"workload": f"48 stations x 2 pols, {SB} subbands, complex int16, 256 channels, 768 spectra, "

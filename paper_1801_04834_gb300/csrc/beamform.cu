@@ -7,9 +7,13 @@
 // voltages are kept. Per (subband, channel k) and pol this is a complex
 // matrix product over stations n:
 //   B[s][b] = sum_n Y[s][n] W[b][n],   W[b][n] = a_n exp(+2 pi i f_k delta[b][n])
-// done as four real GEMMs on planar operands (re plane r, im plane j):
+// done as real GEMMs on planar operands (re plane r, im plane j):
 //   Re B = Yr Wr^T - Yj Wj^T          Im B = Yr Wj^T + Yj Wr^T
-// with the minus from the MMA's negate-A bit.
+// The weight table holds three 64-beam planes per quarter, [Wj; Wr; -Wj], so
+// that [Wr; -Wj] and [Wj; Wr] are contiguous 128-row B tiles: per pol two
+// MMAs of N = 128 give Re B in columns 0-63 and -Im B in columns 64-127,
+//   D = Yr [Wr; -Wj]^T - Yj [Wj; Wr]^T     (the minus by the negate-A bit),
+// which reads each data tile once per K-step instead of twice.
 //
 // Operands. A = data: M = 128 spectra x K = 64 stations of one (pol, plane),
 // read from the planar FP16/BF16 block the fused F-stage writes for the
@@ -18,8 +22,9 @@
 // out of the interleaved inputs; two boxes give the 128 spectra. Spectra are
 // contiguous, so A is MN-major (128-byte swizzle: 8 station rows of 64
 // spectra per 1024-byte atom, the two 64-spectrum halves 8 KB apart).
-// B = weights: N = 64 beams x K = 64 stations, K-major, from a table the
-// weight kernel writes each call ([SB][C][re/im][NB_pad][64]); its phase per
+// B = weights: N = 128 rows (two 64-beam planes) x K = 64 stations, K-major,
+// from a table the weight kernel writes each call ([SB][C][3][NB_pad][64]:
+// im, re, -im); its phase per
 // (subband, beam, station) is formed in FP64 at the channel-0 frequency and
 // per-channel step, reduced mod 2 pi, then stepped over channels in FP32 (as
 // the paper does for delay compensation).
@@ -29,9 +34,9 @@
 // once and stay resident while its spectrum tiles stream through (two
 // channel slots when there are at most 128 beams, so the next channel's
 // weights load meanwhile). The CTA loads the four data planes of an item once
-// (64 KB, ring of 2) and walks the beams in quarters of 64: 32 MMAs
-// (4 K-steps x 2 pols x 4 products, M = 128, N = 64, K = 16) into Re X, Im X,
-// Re Y, Im Y (4 x 64 TMEM columns, double buffered: all 512 columns).
+// (64 KB, ring of 2) and walks the beams in quarters of 64: 16 MMAs
+// (4 K-steps x 2 pols x 2, M = 128, N = 128, K = 16) into (Re X, -Im X),
+// (Re Y, -Im Y) (2 x 128 TMEM columns, double buffered: all 512 columns).
 // Warp roles (persistent, one CTA per SM): warp 0 TMA producer, warp 1 TMEM
 // allocator + MMA issuer, warps 2-9 epilogue (TMEM lane = spectrum; two warps
 // per lane quadrant, 32 beams each): complex voltages, or Stokes I / IQUV
@@ -60,7 +65,7 @@ constexpr unsigned kHalfBytes = 64u * 128u;          // 64 stations x 64 spectra
 constexpr unsigned kPlaneBytes = 2u * kHalfBytes;    // 128 spectra of one (pol, plane)
 constexpr unsigned kDataBytes = 4u * kPlaneBytes;    // (pol, plane) = 4 planes: 64 KB
 constexpr unsigned kWPlane = 64u * 128u;             // 64 beams x 64 stations x 2 B
-constexpr unsigned kWBytes = 2u * kWPlane;           // re + im: 16 KB per beam quarter
+constexpr unsigned kWBytes = 3u * kWPlane;           // im, re, -im: 24 KB per beam quarter
 constexpr unsigned kWRegion = 4u * kWBytes;          // up to 256 beams of one channel, or 2 x 128
 constexpr int kAccCols = 256;                        // Re X, Im X, Re Y, Im Y x 64 beams
 constexpr int kTmemCols = 512;
@@ -68,7 +73,7 @@ constexpr int kNumBars = 2 * kDS + 2 * kWS + 5;      // dfull, dempty, wfull, we
 
 struct BfParams {
     CUtensorMap mapY;        // 4-D (spectrum, pol, station, sb*C*2 + plane)
-    CUtensorMap mapW;        // 3-D (station, beam, sb*C*2 + plane)
+    CUtensorMap mapW;        // 3-D (station, beam, sb*C*3 + plane)
     float *out;
     int *status;
     long long n_ch;          // SB * C
@@ -101,8 +106,8 @@ __device__ __forceinline__ unsigned short weight_bits(float x, unsigned bf16)
     return bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(x)) : __half_as_ushort(__float2half_rn(x));
 }
 
-// Weight table W[sb][k][re/im][NB_pad][64]: one thread per (subband, beam,
-// station slot), looping over channels. Padding beams and stations are zero.
+// Weight table W[sb][k][3][NB_pad][64], planes (im, re, -im): one thread per
+// (subband, beam, station slot), looping over channels. Padding is zero.
 __global__ void bf_weight_kernel(const double *__restrict__ delays, const float *__restrict__ weights,
                                  const double *__restrict__ centres, unsigned short *__restrict__ W, int SB, int C,
                                  int N, int NB, int NB_pad, double fs, unsigned bf16)
@@ -113,11 +118,12 @@ __global__ void bf_weight_kernel(const double *__restrict__ delays, const float 
     const int b = (int)((idx / 64) % NB_pad);
     const int sb = (int)(idx / (64LL * NB_pad));
     const long long plane = (long long)NB_pad * 64;
-    unsigned short *w = W + (long long)sb * C * 2 * plane + (long long)b * 64 + n;
+    unsigned short *w = W + (long long)sb * C * 3 * plane + (long long)b * 64 + n;
     if (b >= NB || n >= N) {
         for (int k = 0; k < C; ++k) {
-            w[(2LL * k) * plane] = 0;
-            w[(2LL * k + 1) * plane] = 0;
+            w[(3LL * k) * plane] = 0;
+            w[(3LL * k + 1) * plane] = 0;
+            w[(3LL * k + 2) * plane] = 0;
         }
         return;
     }
@@ -137,8 +143,9 @@ __global__ void bf_weight_kernel(const double *__restrict__ delays, const float 
         r = fmaf(-kq, 1.9353071795864769e-3f, r);
         float sn, cs;
         __sincosf(r, &sn, &cs);
-        w[(2LL * k) * plane] = weight_bits(a * cs, bf16);
-        w[(2LL * k + 1) * plane] = weight_bits(a * sn, bf16);
+        w[(3LL * k) * plane] = weight_bits(a * sn, bf16);
+        w[(3LL * k + 1) * plane] = weight_bits(a * cs, bf16);
+        w[(3LL * k + 2) * plane] = weight_bits(-(a * sn), bf16);
     }
 }
 
@@ -236,9 +243,9 @@ __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_co
                 }
                 mbar_arrive_expect_tx(wfull(sl), (unsigned)P.NBQ * kWBytes);
                 for (int q = 0; q < P.NBQ; ++q)
-                    for (int pl = 0; pl < 2; ++pl)
+                    for (int pl = 0; pl < 3; ++pl)
                         tma_load_3d(w_u32 + (unsigned)sl * slot_bytes + (unsigned)q * kWBytes + (unsigned)pl * kWPlane,
-                                    &P.mapW, wfull(sl), 0, q * 64, (int)(gch * 2 + pl));
+                                    &P.mapW, wfull(sl), 0, q * 64, (int)(gch * 3 + pl));
                 ++w_issued;
                 for (int st = 0; st < P.ntile; ++st) {
                     const int ds = (int)(d_issued % kDS);
@@ -269,8 +276,8 @@ __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_co
         if (lane == 0) {
             long long dit = 0, wit = 0, ait = 0;
             bool ok = true, issued = false;
-            const unsigned idesc = make_idesc_major(P.bf16, 64, false, true, false);
-            const unsigned idesc_neg = make_idesc_major(P.bf16, 64, true, true, false);
+            const unsigned idesc = make_idesc_major(P.bf16, 128, false, true, false);
+            const unsigned idesc_neg = make_idesc_major(P.bf16, 128, true, true, false);
             for (long long gch = blockIdx.x; gch < P.n_ch && ok; gch += gridDim.x, ++wit) {
                 const int sl = (int)(wit % nslots);
                 if (!bwait(wfull(sl), (unsigned)((wit / nslots) & 1), abort_flag, P, 2)) {
@@ -296,19 +303,16 @@ __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_co
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {      // 16 stations per K-step
                             const unsigned acc = kk ? 1u : 0u;
-                            const unsigned long long bwr = smem_desc(wt + kk * 32);
-                            const unsigned long long bwj = smem_desc(wt + kWPlane + kk * 32);
+                            const unsigned long long b_jr = smem_desc(wt + kk * 32);             // [Wj; Wr]
+                            const unsigned long long b_rn = smem_desc(wt + kWPlane + kk * 32);   // [Wr; -Wj]
 #pragma unroll
                             for (int p = 0; p < 2; ++p) {
                                 const unsigned at = dtile + (unsigned)(p * 2) * kPlaneBytes + (unsigned)kk * 2048u;
                                 const unsigned long long ayr = smem_desc_mn(at, kHalfBytes, 1024);
                                 const unsigned long long ayj = smem_desc_mn(at + kPlaneBytes, kHalfBytes, 1024);
-                                const unsigned d_re = tmem_base + (unsigned)(ab * kAccCols + p * 128);
-                                const unsigned d_im = d_re + 64;
-                                mma_f16(d_re, ayr, bwr, idesc, acc);
-                                mma_f16(d_re, ayj, bwj, idesc_neg, 1u);
-                                mma_f16(d_im, ayr, bwj, idesc, acc);
-                                mma_f16(d_im, ayj, bwr, idesc, 1u);
+                                const unsigned d = tmem_base + (unsigned)(ab * kAccCols + p * 128);   // (Re, -Im)
+                                mma_f16(d, ayr, b_rn, idesc, acc);
+                                mma_f16(d, ayj, b_jr, idesc_neg, 1u);
                             }
                         }
                         issued = true;
@@ -357,6 +361,11 @@ __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_co
                     tmem_ld16(t0 + 128 + 16 * cc, yr);
                     tmem_ld16(t0 + 192 + 16 * cc, yj);
                     tmem_ld_wait();
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) {            // columns 64-127 of a pol hold -Im
+                        xj[jj] = -xj[jj];
+                        yj[jj] = -yj[jj];
+                    }
                     if constexpr (MODE == 0) {
                         if (s < P.S) {
                             const float is = P.inv_scale;
@@ -465,7 +474,7 @@ cudaError_t bf_launch(const BfParams &P, unsigned grid, cudaStream_t st)
 size_t bf_weight_bytes(const Handle &h, int n_beams)
 {
     const size_t nb_pad = (size_t)(n_beams + 63) / 64 * 64;
-    return (size_t)h.p.n_subbands * h.p.n_channels * 2 * nb_pad * 64 * sizeof(unsigned short);
+    return (size_t)h.p.n_subbands * h.p.n_channels * 3 * nb_pad * 64 * sizeof(unsigned short);
 }
 
 cudaError_t launch_beamform(const Handle &h, const void *corr, int NB, const double *delays, const float *weights,
@@ -477,7 +486,7 @@ cudaError_t launch_beamform(const Handle &h, const void *corr, int NB, const dou
     const int NB_pad = (NB + 63) / 64 * 64;
     const unsigned bf16 = h.p.precision == FX_BF16 ? 1u : 0u;
     const long long planes = (long long)SB * C * 2;
-    if (planes > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (planes / 2 * 3 > 0x7fffffffLL) return cudaErrorInvalidValue;
 
     // weight table for this call
     const long long wthreads = (long long)SB * NB_pad * 64;
@@ -500,9 +509,9 @@ cudaError_t launch_beamform(const Handle &h, const void *corr, int NB, const dou
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
-    // weights: (station, beam, plane row) over [SB][C][2][NB_pad][64]
+    // weights: (station, beam, plane row) over [SB][C][3][NB_pad][64]
     {
-        const cuuint64_t gdim[3] = {64, (cuuint64_t)NB_pad, (cuuint64_t)planes};
+        const cuuint64_t gdim[3] = {64, (cuuint64_t)NB_pad, (cuuint64_t)(planes / 2 * 3)};
         const cuuint64_t gstride[2] = {64 * 2, (cuuint64_t)NB_pad * 64 * 2};
         const cuuint32_t box[3] = {64, 64, 1};
         const cuuint32_t estr[3] = {1, 1, 1};
