@@ -489,7 +489,16 @@ def run_fx(args, w):
                 torch.cuda.synchronize()
                 vs = a.elapsed_time(b) / args.steps
                 xb = cv.sizes.corr_bytes + cv.sizes.vis_bytes
+                # executed tensor work: full I_pad x I_pad (both triangles) per spectrum and channel,
+                # 4 real products (x3 for the split forms); TF32 peak = half the BF16 peak
+                ip, sp = cv.I_pad, cv.S_pad
+                mult = {1: 4, 2: 4, 3: 12, 4: 12}[prec]
+                exec_fl = 2.0 * mult * ip * ip * sp * w["C"] * w["SB"]
+                tpeak = float(peaks.get("bf16_tflops", 1890.0)) * (0.5 if prec == 4 else 1.0)
                 variants[name] = {"correlate_ms": vx, "useful_TFLOPs": xflops / (vx * 1e-3) / 1e12,
+                                  "executed_TFLOPs": exec_fl / (vx * 1e-3) / 1e12,
+                                  "tensor_frac_executed": exec_fl / (vx * 1e-3) / 1e12 / tpeak,
+                                  "tensor_frac_useful": xflops / (vx * 1e-3) / 1e12 / tpeak,
                                   "speedup_vs_fp32_xstage": ms_x / vx,
                                   "hbm_GBps": xb / (vx * 1e-3) / 1e9, "hbm_frac": xb / (vx * 1e-3) / 1e9 / hbm,
                                   "rel_err_vs_fp32_path": err,

@@ -31,6 +31,16 @@ namespace {
 
 using namespace ppf;
 
+// A separate FFT pass-1 output buffer saves one barrier per round where it
+// still leaves room for the same number of CTAs per SM (two below 512 threads).
+template <int C, typename TIn>
+constexpr bool ppf_split_u()
+{
+    using Cfg = PpfCfg<C>;
+    constexpr size_t b = ppf_smem_bytes<C, TIn>() + (size_t)Cfg::NTR * Cfg::ROW * sizeof(float2);
+    return Cfg::NT >= 512 ? b <= 227 * 1024 : 2 * (b + 1024) <= 228 * 1024;
+}
+
 template <int C, int T, typename TIn>
 __global__ void __launch_bounds__(PpfCfg<C>::NT)
 ppf_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *__restrict__ taps,
@@ -42,11 +52,13 @@ ppf_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *
     constexpr int BUF_BYTES = kRound * NPC * ROW_BYTES;
     constexpr int IC = NPC * kPols;                                // inputs of this CTA
     static_assert(ROW_BYTES % 16 == 0, "rows must be whole 16-byte chunks");
+    constexpr bool kSplitU = ppf_split_u<C, TIn>();
 
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *tw = reinterpret_cast<float2 *>(smem);
     unsigned char *inbuf = smem + C * sizeof(float2);
     float2 *u = reinterpret_cast<float2 *>(inbuf + 2 * BUF_BYTES);
+    float2 *u2 = kSplitU ? u + Cfg::NTR * ROW : u;                    // FFT pass-1 output
 
     const int tid = threadIdx.x;
     const int sb = blockIdx.z;
@@ -120,8 +132,9 @@ ppf_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *
         cp_async_commit();
 
         // ---- FFT pass 1: R-point FFTs over n1 (stride R), times W_C^(n2 k1) ----
-        // inputs of every task are read before any output is written, because
-        // the outputs go to other positions (row k1 of length R + 1)
+        // With a second buffer (u2) the outputs go there; in place, every
+        // task's inputs are read before any output is written, because the
+        // outputs go to other positions (row k1 of length R + 1)
         float2 v1[Cfg::FFT_ITERS][R];
 #pragma unroll
         for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
@@ -130,12 +143,12 @@ ppf_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *
 #pragma unroll
             for (int n1 = 0; n1 < R; ++n1) v1[it][n1] = row[R * n1 + task % R];
         }
-        __syncthreads();
+        if constexpr (!kSplitU) __syncthreads();
 #pragma unroll
         for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
             const int task = it * NT + tid;
             const int tr = task / R, n2 = task % R;
-            float2 *row = u + tr * ROW;
+            float2 *row = u2 + tr * ROW;
             fft_reg<R>(v1[it]);
 #pragma unroll
             for (int k1 = 1; k1 < R; ++k1) v1[it][k1] = cmul(v1[it][k1], tw[n2 * k1]);
@@ -148,7 +161,7 @@ ppf_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *
         for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
             const int task = it * NT + tid;
             const int tr = task / R, k1 = task % R;
-            const float2 *row = u + tr * ROW;
+            const float2 *row = u2 + tr * ROW;
             float2 v[R];
 #pragma unroll
             for (int n2 = 0; n2 < R; ++n2) v[n2] = row[(R + 1) * k1 + n2];
@@ -178,7 +191,8 @@ cudaError_t launch_t(const Handle &h, const void *raw, float2 *chan, cudaStream_
     while (rpc > 1 && (long long)((rounds_total + rpc - 1) / rpc) * sgroups * SB < 152LL * 4) rpc /= 2;
     dim3 grid((rounds_total + rpc - 1) / rpc, sgroups, SB);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-    constexpr size_t smem = ppf_smem_bytes<C, TIn>();
+    constexpr size_t smem =
+        ppf_smem_bytes<C, TIn>() + (ppf_split_u<C, TIn>() ? (size_t)Cfg::NTR * Cfg::ROW * sizeof(float2) : 0);
     auto kern = ppf_kernel<C, T, TIn>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
