@@ -356,8 +356,10 @@ cudaError_t launch_t(const Handle &h, const void *raw, void *corr, const float *
     const int N = h.p.n_stations, S = h.p.n_spectra, SB = h.p.n_subbands;
     const int rounds_total = (S + kRound - 1) / kRound;
     const int sgroups = (N + Cfg::NPC - 1) / Cfg::NPC;
-    int rpc = 8;
-    while (rpc > 1 && (long long)((rounds_total + rpc - 1) / rpc) * sgroups * SB < 152LL * 4) rpc /= 2;
+    // long runs of rounds per CTA amortise the T-1 history rows each CTA reads
+    // and filters first; shorten them only while the grid would be under ~8 waves
+    int rpc = 32;
+    while (rpc > 1 && (long long)((rounds_total + rpc - 1) / rpc) * sgroups * SB < 152LL * 16) rpc /= 2;
     dim3 grid(sgroups, (rounds_total + rpc - 1) / rpc, SB);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
     constexpr size_t smem = fused_smem_bytes<C, TIn>();
