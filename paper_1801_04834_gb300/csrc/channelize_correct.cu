@@ -73,12 +73,14 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
     constexpr int ROW_BYTES = C * kPols * (int)sizeof(TIn);
     constexpr int BUF_BYTES = kRound * NPC * ROW_BYTES;
     constexpr int IC = NPC * kPols;                 // inputs of this CTA
-    // planar staging [C][IC][17] (odd rows, so the read-out of 16 spectra per
-    // input is conflict free)
-    constexpr int SROW = IC * (kRound + 1);         // planar staging row per channel
+    // planar staging [IC][C][17] + a pad per input: rows of 17 (odd) keep the
+    // pass-2 stores (lanes = consecutive channels) and the read-out (lanes =
+    // consecutive channels, 16 spectra each) conflict free; the pad moves the
+    // inputs of one half-warp onto different banks
+    constexpr int SIL = C * (kRound + 1) + (C == 16 ? 4 : 8);   // staging block per input
     constexpr int PHC = fused_phc<C>();
     constexpr int PHROW = IC * PHC;                 // factor-table row per spectrum
-    static_assert(OUT == 1 || C * SROW <= Cfg::NTR * ROW, "staging fits in the FFT buffer");
+    static_assert(OUT == 1 || IC * SIL <= Cfg::NTR * ROW, "staging fits in the FFT buffer");
     static_assert(NT >= 512 ? fused_smem_bytes<C, TIn>() <= 227 * 1024
                             : 2 * (fused_smem_bytes<C, TIn>() + 1024) <= 228 * 1024,
                   "two CTAs per SM (one at 512 threads)");
@@ -259,7 +261,7 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
 #pragma unroll
             for (int k2 = 0; k2 < R; ++k2) {
                 const int kout = k1 + R * ((k2 + R / 2) % R);
-                u[kout * SROW + il * (kRound + 1) + j] = y[it][k2];   // [C][IC][17]
+                u[il * SIL + kout * (kRound + 1) + j] = y[it][k2];    // [IC][C][17]
             }
         }
         __syncthreads();
@@ -269,10 +271,10 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
             float *out = reinterpret_cast<float *>(corr);
             const long long pstride = (long long)I_pad * S_pad;
             for (int e = tid; e < C * IC; e += NT) {
-                const int il = e % IC, kout = e / IC;
+                const int kout = e % C, il = e / C;
                 const int i = 2 * n0 + il;
                 if (i >= I) continue;
-                const float2 *src = u + kout * SROW + il * (kRound + 1);
+                const float2 *src = u + il * SIL + kout * (kRound + 1);
                 float4 *re = reinterpret_cast<float4 *>(out + (((long long)sb * C + kout) * 2) * pstride +
                                                         (long long)i * S_pad + sr);
                 float4 *im = re + pstride / 4;
@@ -291,10 +293,10 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
             unsigned short *out = reinterpret_cast<unsigned short *>(corr);
             const long long pstride = (long long)I_pad * S_pad;
             for (int e = tid; e < C * IC; e += NT) {
-                const int il = e % IC, kout = e / IC;
+                const int kout = e % C, il = e / C;
                 const int i = 2 * n0 + il;
                 if (i >= I) continue;
-                const float2 *src = u + kout * SROW + il * (kRound + 1);
+                const float2 *src = u + il * SIL + kout * (kRound + 1);
                 unsigned short re[kRound], im[kRound], rl[kRound], iml[kRound];
 #pragma unroll
                 for (int j = 0; j < kRound; ++j) {

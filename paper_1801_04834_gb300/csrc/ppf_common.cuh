@@ -18,8 +18,10 @@ struct PpfCfg {
     static constexpr int NPC = (C * kPols >= 256) ? 1 : 256 / (C * kPols);  // stations per CTA
     static constexpr int NT = NPC * C * kPols;                    // threads per CTA
     // smem row of one transform: C + R float2, which holds the pass-1 output
-    // as R rows of R + 1 (the odd row length keeps pass-2 reads conflict free)
-    static constexpr int ROW = R * (R + 1);
+    // as R rows of R + 1 (the odd row length keeps pass-2 reads conflict free),
+    // padded for R >= 8 to 8 mod 16 entries so that the FIR stores of the two
+    // pols of a channel (rows one apart) fall on different banks
+    static constexpr int ROW = R * (R + 1) + (R >= 8 ? ((8 - (R * (R + 1)) % 16) + 16) % 16 : 0);
     static constexpr int NTR = NPC * kPols * kRound;              // transforms per round
     static constexpr int FFT_ITERS = NTR * R / NT;
     static_assert(R * R == C, "C must be a square of R");
