@@ -60,8 +60,9 @@ class Oracle:
         L.fxo_fx.argtypes = [I, P, I, I, I, I, I, I, P, D, P, P, P, P, P, P]
         L.fxo_vjp.argtypes = [P, I, I, I, I, I, D, P, P, P, P, P, P, P]
         L.fxo_beamform.argtypes = [P, I, I, I, I, I, D, P, I, P, P, I, I, P]
+        L.fxo_beamform_incoherent.argtypes = [P, I, I, I, I, I, P, I, I, P]
         for f in (L.fxo_channelize, L.fxo_correct, L.fxo_correlate, L.fxo_fx, L.fxo_vjp,
-                  L.fxo_beamform, L.fxo_threads):
+                  L.fxo_beamform, L.fxo_beamform_incoherent, L.fxo_threads):
             f.restype = I
         self._L = L
 
@@ -148,6 +149,16 @@ class Oracle:
                     "beamform")
         return out
 
+    def beamform_incoherent(self, corr, weights=None, mode=1, tint=1):
+        """Incoherent beam from corr [SB][C][S][N][P][2]: mode 1 Stokes I
+        [SB][C][S/tint]; mode 2 Stokes IQUV [SB][C][S/tint][4]."""
+        corr = _f64(corr)
+        SB, C, S, N, P, _ = corr.shape
+        out = np.empty((SB, C, S // tint) if mode == 1 else (SB, C, S // tint, 4))
+        self._check(self._L.fxo_beamform_incoherent(_ptr(corr), SB, N, P, C, S, _ptr(_f64(weights)), mode, tint,
+                                                    _ptr(out)), "beamform_incoherent")
+        return out
+
 
 _default = None
 
@@ -189,3 +200,7 @@ def vjp(*a, **k):
 
 def beamform(*a, **k):
     return default().beamform(*a, **k)
+
+
+def beamform_incoherent(*a, **k):
+    return default().beamform_incoherent(*a, **k)

@@ -17,6 +17,7 @@
  *                   by the chain rule entry by entry (constant delays)
  *   fxo_beamform    coherent beams: per-sample phase-shifted station sum,
  *                   then complex voltages or Stokes I / IQUV
+ *   fxo_beamform_incoherent  Stokes per station, then the weighted station sum
  * OpenMP splits independent outer loops (subbands, stations, channels) across
  * host threads, as the paper's host code does over subbands (Sec. "Parallelization
  * libraries"); it does not change any arithmetic.
@@ -388,6 +389,49 @@ int fxo_beamform(const double *corr, int SB, int N, int P, int C, int S, double 
                         double *o = out + ((((size_t)sb * NB + b) * C + k) * SO + so) * 4;
                         for (int q = 0; q < 4; ++q) o[q] = acc[q];
                     }
+                }
+            }
+    return 0;
+}
+
+/* Incoherent beam (Sec. "Signal processing with GPU kernels": incoherent
+ * beamforming first computes Stokes parameters and then sums over antenna
+ * fields). Per subband, channel and spectrum, each station's Stokes
+ * parameters from its own X = Y_n0, Y = Y_n1 (definitions as in
+ * fxo_beamform) are multiplied by the station weight a_n (NULL = 1) and
+ * summed over stations and over tint consecutive spectra:
+ *   mode 1  out [SB][C][S/tint]      Stokes I
+ *   mode 2  out [SB][C][S/tint][4]   Stokes I, Q, U, V
+ * corr is the corrected block [SB][C][S][N][P]. */
+int fxo_beamform_incoherent(const double *corr, int SB, int N, int P, int C, int S, const double *weights, int mode,
+                            int tint, double *out)
+{
+    if (P != 2 || mode < 1 || mode > 2 || tint < 1 || S % tint != 0) return -1;
+    const int SO = S / tint;
+#pragma omp parallel for collapse(2) schedule(dynamic)
+    for (int sb = 0; sb < SB; ++sb)
+        for (int k = 0; k < C; ++k)
+            for (int so = 0; so < SO; ++so) {
+                double acc[4] = {0.0, 0.0, 0.0, 0.0};
+                for (int t = 0; t < tint; ++t) {
+                    const int s = tint * so + t;
+                    for (int n = 0; n < N; ++n) {
+                        const double wn = weights ? weights[n] : 1.0;
+                        const double *y = corr + ((((size_t)sb * C + k) * S + s) * N + n) * P * 2;
+                        const double xre = y[0], xim = y[1], yre = y[2], yim = y[3];
+                        const double xx = xre * xre + xim * xim;
+                        const double yy = yre * yre + yim * yim;
+                        acc[0] += wn * (xx + yy);
+                        acc[1] += wn * (xx - yy);
+                        acc[2] += wn * 2.0 * (xre * yre + xim * yim);    /* 2 Re(X conj Y) */
+                        acc[3] += wn * 2.0 * (xim * yre - xre * yim);    /* 2 Im(X conj Y) */
+                    }
+                }
+                if (mode == 1) {
+                    out[((size_t)sb * C + k) * SO + so] = acc[0];
+                } else {
+                    double *o = out + (((size_t)sb * C + k) * SO + so) * 4;
+                    for (int q = 0; q < 4; ++q) o[q] = acc[q];
                 }
             }
     return 0;

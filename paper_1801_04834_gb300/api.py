@@ -32,7 +32,7 @@ class Correlator:
                  taps, centres, n_taps: int = 16, fmt: int = FX_CI16, precision: int = FX_F32,
                  sample_rate_hz: float = SAMPLE_RATE_HZ, operand_scale: float = 0.0, device=None,
                  host_chunk_subbands: int = 0, streaming: bool = False, max_coarse_shift: int = 0,
-                 max_beams: int = 0, xf32_small_tiles: bool = False):
+                 max_beams: int = 0, xf32_small_tiles: bool = False, extra_flags: int = 0):
         self.lib = _abi.load()
         if device is not None:
             torch.cuda.set_device(device)
@@ -56,7 +56,7 @@ class Correlator:
         p.h_taps = taps.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         p.operand_scale = operand_scale
         p.flags = (_abi.FX_FLAG_STREAMING if streaming else 0) | \
-            (_abi.FX_FLAG_XF32_SMALL_TILES if xf32_small_tiles else 0)
+            (_abi.FX_FLAG_XF32_SMALL_TILES if xf32_small_tiles else 0) | extra_flags
         p.host_chunk_subbands = host_chunk_subbands
         p.max_coarse_shift = max_coarse_shift
         p.max_beams = max_beams
@@ -241,6 +241,12 @@ class Correlator:
             self._dev(out, "out", torch.float32, 4 * int(np.prod(self.beam_shape(nb, output, tint)))),
             _stream_ptr(stream)), "fx_beamform")
         return out
+
+    def poll_status(self):
+        """fx_poll_status: (status, code) of the device-side error word (synchronises)."""
+        code = ctypes.c_int(0)
+        rc = self.lib.fx_poll_status(self.handle, ctypes.byref(code))
+        return rc, code.value
 
     def stream_reset(self, stream=None):
         check(self.lib.fx_stream_reset(self.handle, _stream_ptr(stream)), "fx_stream_reset")

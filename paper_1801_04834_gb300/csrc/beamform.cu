@@ -82,6 +82,7 @@ struct BfParams {
     unsigned bf16;
     float inv_scale, inv_scale2;
     long long timeout_cycles;
+    int no_tma;              // failure-detection test hook: issue no loads
 };
 
 // Bounded wait: false on timeout (sets abort + status) or when another role aborted.
@@ -241,6 +242,10 @@ __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_co
                     ok = false;
                     break;
                 }
+                if (P.no_tma) {
+                    ++w_issued;
+                    continue;
+                }
                 mbar_arrive_expect_tx(wfull(sl), (unsigned)P.NBQ * kWBytes);
                 for (int q = 0; q < P.NBQ; ++q)
                     for (int pl = 0; pl < 3; ++pl)
@@ -263,7 +268,7 @@ __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_co
                     ++d_issued;
                 }
             }
-            if (!ok) {
+            if (!ok && !P.no_tma) {
                 // the last loads issued into each ring may still be in flight
                 for (long long u = d_issued > kDS ? d_issued - kDS : 0; u < d_issued; ++u)
                     drain_wait(dfull((int)(u % kDS)), (unsigned)((u / kDS) & 1), P.timeout_cycles);
@@ -532,6 +537,7 @@ cudaError_t launch_beamform(const Handle &h, const void *corr, int NB, const dou
     P.inv_scale = 1.0f / h.operand_scale;
     P.inv_scale2 = 1.0f / (h.operand_scale * h.operand_scale);
     P.timeout_cycles = h.tc_timeout_cycles;
+    P.no_tma = h.tc_test_no_tma;
     const long long grid = std::min<long long>(P.n_ch, h.num_sms);
     if (grid <= 0) return cudaSuccess;
     switch (mode * 64 + tint) {

@@ -67,6 +67,7 @@ struct T3Params {
     int N, I_pad, nk;         // stations, padded inputs, stages per item (a multiple of kChunk)
     long long B;              // baselines
     long long timeout_cycles;
+    int no_tma;               // failure-detection test hook: issue no loads
 };
 
 __device__ __forceinline__ bool t3wait(unsigned bar, unsigned parity, volatile int *abort_flag, const T3Params &P,
@@ -159,6 +160,7 @@ __global__ void __launch_bounds__(kT3Threads, 1) xcorr_tf32_kernel(const __grid_
                         ok = false;
                         break;
                     }
+                    if (P.no_tma) continue;
                     mbar_arrive_expect_tx(full_bar(s), kT3Hi);
                     const unsigned dst = tiles_u32 + (unsigned)s * kT3Stage;
                     for (int pl = 0; pl < 2; ++pl)
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(kT3Threads, 1) xcorr_tf32_kernel(const __grid_
                                     (int)(w * 2 + pl));
                 }
             }
-            if (!ok) {
+            if (!ok && !P.no_tma) {
                 const long long first = it > kT3Stages ? it - kT3Stages : 0;
                 for (long long u = first; u < it; ++u)
                     drain_wait(full_bar((int)(u % kT3Stages)), (unsigned)((u / kT3Stages) & 1), P.timeout_cycles);
@@ -393,6 +395,7 @@ cudaError_t launch_xcorr_tf32(const Handle &h, const float *corr, float2 *vis, c
     P.nk = h.S_pad / kT3K;
     P.B = h.B;
     P.timeout_cycles = h.tc_timeout_cycles;
+    P.no_tma = h.tc_test_no_tma;
     const size_t smem = 1024 + (size_t)kT3Stages * kT3Stage + 8 * kT3Bars + 16;
     cudaError_t e = cudaFuncSetAttribute(xcorr_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -28,6 +28,9 @@ What pins what:
                      station rotated by exp(+2 pi i f_k delay)
   stokes             Stokes closed forms for Y = X, X = iY, Y = 0; integration
                      = sum of per-spectrum values; I^2 >= Q^2 + U^2 + V^2
+  incoherent         incoherent beam: powers add (closed form against the
+                     coherent beam), per-station Stokes closed forms, linear
+                     in the weights, one station = its zero-delay coherent beam
 """
 from __future__ import annotations
 
@@ -461,7 +464,44 @@ def pin_stokes(o):
     assert np.allclose(i4, s4[..., 0], rtol=1e-12)
 
 
+def pin_incoherent(o):
+    """Incoherent beam: a plane wave of amplitude (3, 2) per station gives
+    I = (9 + 4) sum_n a_n per spectrum (powers add, phases do not matter),
+    against (9 + 4) (sum_n a_n)^2 for the coherent beam steered at it; the
+    Stokes closed forms hold per station (Y = X: U = I, Q = V = 0); the sum is
+    linear in the station weights; and with one station it equals that
+    station's coherent beam at zero delay."""
+    SB, N, C, S = 2, 5, 4, 6
+    rng = np.random.default_rng(31)
+    centres = synth.subband_centres(SB)
+    d0 = rng.uniform(-3e-6, 3e-6, N)
+    a = rng.uniform(0.5, 1.5, N)
+    corr, _ = _plane_wave(32, SB, N, C, S, centres, d0)
+    inc = o.beamform_incoherent(corr, a, mode=2, tint=1)
+    assert np.allclose(inc[..., 0], 13.0 * a.sum(), rtol=1e-12)
+    coh = o.beamform(corr, FS, centres, d0[None, :], a, mode=2, tint=1)
+    assert np.allclose(coh[:, 0, ..., 0], 13.0 * a.sum() ** 2, rtol=1e-10)
+    y = cplx(synth.noise(33, (SB, C, S, N, 2)))
+    same = np.stack([y, y], axis=-1)
+    st = o.beamform_incoherent(np.stack([same.real, same.imag], axis=-1), None, mode=2, tint=2)
+    assert np.allclose(st[..., 2], st[..., 0], rtol=1e-12)
+    assert np.allclose(st[..., 1], 0, atol=1e-9 * st[..., 0].max())
+    assert np.allclose(st[..., 3], 0, atol=1e-9 * st[..., 0].max())
+    noise = synth.noise(34, (SB, C, S, N, 2, 2))
+    whole = o.beamform_incoherent(noise, a, mode=2, tint=3)
+    parts = sum(a[n] * o.beamform_incoherent(noise, np.eye(N)[n], mode=2, tint=3) for n in range(N))
+    assert np.allclose(whole, parts, rtol=1e-12)
+    one = np.ascontiguousarray(noise[:, :, :, 1:2])
+    assert np.allclose(o.beamform_incoherent(one, None, mode=2, tint=3)[:, None],
+                       o.beamform(one, FS, centres, np.zeros((1, 1)), None, mode=2, tint=3), rtol=1e-12)
+    # a one-hot weight picks that station: its zero-delay coherent beam with the same weight
+    for m in range(N):
+        e = np.eye(N)[m]
+        assert np.allclose(o.beamform_incoherent(noise, e, mode=2, tint=3)[:, None],
+                           o.beamform(noise, FS, centres, np.zeros((1, N)), e, mode=2, tint=3), rtol=1e-12)
+
+
 ALL_PINS = [pin_fir_delta, pin_tone, pin_dft_vs_numpy, pin_point_source, pin_bandpass,
             pin_delay_ramp, pin_correlate_einsum, pin_hermitian, pin_linearity,
             pin_gradient_fd, pin_gradient_truth, pin_fx_chain, pin_ci4_decode, pin_flags,
-            pin_beam_point_source, pin_beam_station_sum, pin_stokes]
+            pin_beam_point_source, pin_beam_station_sum, pin_stokes, pin_incoherent]

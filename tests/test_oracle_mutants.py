@@ -53,6 +53,11 @@ MUTANTS = [
     ("stokes_u_from_imag", "acc[2] += 2.0 * cre;", "acc[2] += 2.0 * cim;"),
     ("stokes_q_sign", "acc[1] += xx - yy;", "acc[1] += yy - xx;"),
     ("stokes_tint_index", "const int s = so * tint + t;", "const int s = so + t * SO;"),
+    ("incoherent_weight_squared", "acc[0] += wn * (xx + yy);", "acc[0] += wn * wn * (xx + yy);"),
+    ("incoherent_u_sign", "acc[2] += wn * 2.0 * (xre * yre + xim * yim);    /* 2 Re(X conj Y) */",
+     "acc[2] += wn * 2.0 * (xre * yre - xim * yim);    /* 2 Re(X conj Y) */"),
+    ("incoherent_one_station", "const double *y = corr + ((((size_t)sb * C + k) * S + s) * N + n) * P * 2;",
+     "const double *y = corr + ((((size_t)sb * C + k) * S + s) * N + 0) * P * 2;"),
 ]
 
 
