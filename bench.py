@@ -727,6 +727,11 @@ def measure_beamformer(args, dev):
     step_ms = _time(lambda: (fstage(), beams()), args.steps, stream)
     f_ms = _time(fstage, args.steps, stream)
     b_ms = _time(beams, args.steps, stream)
+    # incoherent beam (Stokes I per station, summed) on the same corrected block
+    inc = torch.empty((SB, C, S // tint), dtype=torch.float32, device=dev)
+    c.beamform_incoherent(corr, output=1, tint=tint, out=inc)
+    i_ms = _time(lambda: c.beamform_incoherent(corr, output=1, tint=tint, out=inc), args.steps, stream)
+    i_bytes = c.sizes.corr_bytes + inc.numel() * 4
     peaks, _ = measured_peaks()
     nb_pad = (NB + 63) // 64 * 64
     wbytes = SB * C * 3 * nb_pad * 64 * 2                             # planes (im, re, -im) per beam quarter
@@ -740,9 +745,10 @@ def measure_beamformer(args, dev):
            "beamform_useful_TFLOPs": useful / (b_ms * 1e-3) / 1e12,
            "beamform_hbm_GBps": bf_bytes / (b_ms * 1e-3) / 1e9,
            "beamform_hbm_frac": bf_bytes / (b_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-           "beamform_algorithmic_bytes": bf_bytes}
+           "beamform_algorithmic_bytes": bf_bytes,
+           "incoherent_ms": i_ms, "incoherent_hbm_frac": i_bytes / (i_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
     c.close()
-    del raw, corr, out
+    del raw, corr, out, inc
     return res
 
 

@@ -277,6 +277,19 @@ typedef enum { FX_BEAM_VOLTAGES = 0, FX_BEAM_STOKES_I = 1, FX_BEAM_STOKES_IQUV =
 fx_status fx_beamform(fx_handle *h, const void *d_corr, int n_beams, const double *d_beam_delays,
                       const float *d_station_weights, int output, int tint, float *d_out, fx_stream stream);
 
+/* Incoherent beam (same section: incoherent beamforming first computes the
+ * Stokes parameters of each antenna field, then sums over fields). For every
+ * subband, channel and spectrum: sum_n a_n Stokes(Y_n0, Y_n1) (definitions as
+ * in fx_beamform), summed over tint consecutive spectra (a power of two <= 32
+ * dividing S). d_corr: the corrected block of the handle's precision (FP32
+ * interleaved, FP16/BF16 planar divided by operand_scale^2 on output, or the
+ * FX_TF32_SPLIT planar FP32 block; split FP16: FX_ERR_UNSUPPORTED).
+ * d_station_weights [N] float or NULL (= 1). output FX_BEAM_STOKES_I:
+ * d_out [SB][C][S/tint] float; FX_BEAM_STOKES_IQUV: d_out [SB][C][S/tint][4].
+ * Asynchronous, allocation free, graph-capturable; needs no max_beams. */
+fx_status fx_beamform_incoherent(fx_handle *h, const void *d_corr, const float *d_station_weights, int output,
+                                 int tint, float *d_out, fx_stream stream);
+
 /* ---- differentiation form ------------------------------------------------
  * With the delay held constant over the block (tau_begin = tau_end = tau) the
  * corrected sample is Y_a = c_a X_a, c_a(k) = g_a exp(2 pi i f_k tau_n(a))

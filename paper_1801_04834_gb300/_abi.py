@@ -60,6 +60,7 @@ SIGNATURES = {
     "fx_stream_reset": (I, [P, P]),
     "fx_beamform": (I, [P, P, I, P, P, I, I, P, P]),
     "fx_ffma_probe": (I, [I, I, P, P]),
+    "fx_beamform_incoherent": (I, [P, P, P, I, I, P, P]),
     "fx_poll_status": (I, [P, ctypes.POINTER(ctypes.c_int)]),
     "fx_apply_gains": (I, [P, P, P, P, P, P]),
     "fx_batch_create": (I, [P, I, I, ctypes.c_float, ctypes.POINTER(P)]),

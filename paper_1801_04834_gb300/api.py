@@ -242,6 +242,19 @@ class Correlator:
             _stream_ptr(stream)), "fx_beamform")
         return out
 
+    def beamform_incoherent(self, corr, station_weights=None, output=1, tint=1, out=None, stream=None):
+        """fx_beamform_incoherent: Stokes I (output 1) or IQUV (2) per station,
+        weighted sum over stations, summed over tint spectra."""
+        shape = (self.SB, self.C, self.S // tint) if output == 1 else (self.SB, self.C, self.S // tint, 4)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=self.device)
+        check(self.lib.fx_beamform_incoherent(
+            self.handle, self._dev(corr, "corr", self.corr_dtype(), self.sizes.corr_bytes),
+            self._opt(station_weights, "station_weights", torch.float32, 4 * self.N), output, tint,
+            self._dev(out, "out", torch.float32, 4 * int(np.prod(shape))), _stream_ptr(stream)),
+            "fx_beamform_incoherent")
+        return out
+
     def poll_status(self):
         """fx_poll_status: (status, code) of the device-side error word (synchronises)."""
         code = ctypes.c_int(0)

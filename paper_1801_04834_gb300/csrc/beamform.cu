@@ -440,6 +440,74 @@ __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_co
     }
 }
 
+// ---- incoherent beam ---------------------------------------------------------
+// Sec. "Signal processing with GPU kernels": incoherent beamforming first forms
+// Stokes parameters per antenna field and then sums over fields. Per
+// (subband, channel) and spectrum s: sum_n a_n Stokes(X_n(s), Y_n(s)), summed
+// over tint consecutive spectra. No contraction, so CUDA cores: one thread per
+// spectrum (lanes = consecutive spectra, so each station's planes are read in
+// coalesced runs), stations accumulated in registers, tint lanes summed with
+// shuffles. SRC: 0 FP32 [SB][C][S][I], 1 FP16 planar, 2 BF16 planar,
+// 3 FP32 planar ([SB][C][2][I_pad][S_pad]).
+template <int MODE, int SRC>
+__global__ void __launch_bounds__(128) incoherent_kernel(const void *__restrict__ corr, const float *__restrict__ weights,
+                                                         float *__restrict__ out, int N, int S, int I_pad, int S_pad,
+                                                         int tint, float inv_scale2, int sblocks)
+{
+    const long long gch = blockIdx.x / sblocks;
+    const int s = (int)(blockIdx.x % sblocks) * 128 + threadIdx.x;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const bool in = SRC == 0 ? s < S : s < S_pad;
+    if (in) {
+        for (int n = 0; n < N; ++n) {
+            const float a = weights ? __ldg(weights + n) : 1.f;
+            float xr, xj, yr, yj;
+            if constexpr (SRC == 0) {
+                const float4 v = *reinterpret_cast<const float4 *>(
+                    reinterpret_cast<const float2 *>(corr) + (gch * S + s) * (long long)(2 * N) + 2 * n);
+                xr = v.x; xj = v.y; yr = v.z; yj = v.w;
+            } else if constexpr (SRC == 3) {
+                const float *re = reinterpret_cast<const float *>(corr) + gch * 2 * (long long)I_pad * S_pad;
+                const float *im = re + (long long)I_pad * S_pad;
+                xr = re[(long long)(2 * n) * S_pad + s];
+                xj = im[(long long)(2 * n) * S_pad + s];
+                yr = re[(long long)(2 * n + 1) * S_pad + s];
+                yj = im[(long long)(2 * n + 1) * S_pad + s];
+            } else {
+                const unsigned short *re =
+                    reinterpret_cast<const unsigned short *>(corr) + gch * 2 * (long long)I_pad * S_pad;
+                const unsigned short *im = re + (long long)I_pad * S_pad;
+                auto f = [](unsigned short b) {
+                    return SRC == 2 ? __bfloat162float(__ushort_as_bfloat16(b)) : __half2float(__ushort_as_half(b));
+                };
+                xr = f(re[(long long)(2 * n) * S_pad + s]);
+                xj = f(im[(long long)(2 * n) * S_pad + s]);
+                yr = f(re[(long long)(2 * n + 1) * S_pad + s]);
+                yj = f(im[(long long)(2 * n + 1) * S_pad + s]);
+            }
+            const float xx = fmaf(xr, xr, xj * xj), yy = fmaf(yr, yr, yj * yj);
+            acc[0] = fmaf(a, xx + yy, acc[0]);
+            if constexpr (MODE == 2) {
+                acc[1] = fmaf(a, xx - yy, acc[1]);
+                acc[2] = fmaf(a, 2.f * fmaf(xr, yr, xj * yj), acc[2]);     // 2 Re(X conj Y)
+                acc[3] = fmaf(a, 2.f * fmaf(xj, yr, -xr * yj), acc[3]);    // 2 Im(X conj Y)
+            }
+        }
+    }
+    constexpr int NQ = MODE == 1 ? 1 : 4;
+    for (int off = 1; off < tint; off <<= 1)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+    if (s < S && (threadIdx.x % tint) == 0) {
+        const long long o = gch * (S / tint) + s / tint;
+        if constexpr (MODE == 1)
+            out[o] = acc[0] * inv_scale2;
+        else
+            *reinterpret_cast<float4 *>(out + o * 4) =
+                make_float4(acc[0] * inv_scale2, acc[1] * inv_scale2, acc[2] * inv_scale2, acc[3] * inv_scale2);
+    }
+}
+
 // ---- host side ----------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
@@ -475,6 +543,32 @@ cudaError_t bf_launch(const BfParams &P, unsigned grid, cudaStream_t st)
 }
 
 }  // namespace
+
+cudaError_t launch_beamform_incoherent(const Handle &h, const void *corr, const float *weights, int mode, int tint,
+                                       float *out, cudaStream_t st)
+{
+    const int SB = h.p.n_subbands, C = h.p.n_channels, N = h.p.n_stations, S = h.p.n_spectra;
+    const long long n_ch = (long long)SB * C;
+    const int sblocks = ((h.p.precision == FX_F32 ? S : h.S_pad) + 127) / 128;
+    const long long blocks = n_ch * sblocks;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const float is2 = 1.0f / (h.operand_scale * h.operand_scale);
+    auto go = [&](auto kern) {
+        kern<<<(unsigned)blocks, 128, 0, st>>>(corr, weights, out, N, S, h.I_pad, h.S_pad, tint, is2, sblocks);
+        return cudaGetLastError();
+    };
+    switch (h.p.precision * 4 + mode) {
+    case FX_F32 * 4 + 1: return go(incoherent_kernel<1, 0>);
+    case FX_F32 * 4 + 2: return go(incoherent_kernel<2, 0>);
+    case FX_F16 * 4 + 1: return go(incoherent_kernel<1, 1>);
+    case FX_F16 * 4 + 2: return go(incoherent_kernel<2, 1>);
+    case FX_BF16 * 4 + 1: return go(incoherent_kernel<1, 2>);
+    case FX_BF16 * 4 + 2: return go(incoherent_kernel<2, 2>);
+    case FX_TF32_SPLIT * 4 + 1: return go(incoherent_kernel<1, 3>);
+    case FX_TF32_SPLIT * 4 + 2: return go(incoherent_kernel<2, 3>);
+    default: return cudaErrorNotSupported;
+    }
+}
 
 size_t bf_weight_bytes(const Handle &h, int n_beams)
 {

@@ -335,6 +335,25 @@ extern "C" fx_status fx_beamform(fx_handle *h, const void *d_corr, int n_beams, 
                         who);
 }
 
+extern "C" fx_status fx_beamform_incoherent(fx_handle *h, const void *d_corr, const float *d_station_weights,
+                                            int output, int tint, float *d_out, fx_stream stream)
+{
+    const char *who = "fx_beamform_incoherent";
+    fx_status st = check_handle(h, who);
+    if (st) return st;
+    if (h->p.precision == FX_F16_SPLIT) return fail(FX_ERR_UNSUPPORTED, "%s: split FP16 operands", who);
+    if (!d_corr || !d_out) return fail(FX_ERR_INVALID, "%s: NULL buffer", who);
+    if (output != FX_BEAM_STOKES_I && output != FX_BEAM_STOKES_IQUV)
+        return fail(FX_ERR_INVALID, "%s: output must be FX_BEAM_STOKES_I or FX_BEAM_STOKES_IQUV", who);
+    if (tint < 1 || tint > 32 || !is_pow2(tint) || h->p.n_spectra % tint != 0)
+        return fail(FX_ERR_INVALID, "%s: tint must be a power of two <= 32 dividing S", who);
+    if (((uintptr_t)d_corr & 15) || ((uintptr_t)d_out & 15) || ((uintptr_t)d_station_weights & 3))
+        return fail(FX_ERR_INVALID, "%s: misaligned buffer", who);
+    return after_launch(fxi::launch_beamform_incoherent(*h, d_corr, d_station_weights, output, tint, d_out,
+                                                        (cudaStream_t)stream),
+                        who);
+}
+
 extern "C" fx_status fx_stream_reset(fx_handle *h, fx_stream stream)
 {
     fx_status st = check_handle(h, "fx_stream_reset");

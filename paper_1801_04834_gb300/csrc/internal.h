@@ -85,6 +85,8 @@ cudaError_t launch_adjoint(const Handle &h, const float2 *R, const float2 *G, co
 
 // beamform.cu
 size_t bf_weight_bytes(const Handle &h, int n_beams);
+cudaError_t launch_beamform_incoherent(const Handle &h, const void *corr, const float *weights, int mode, int tint,
+                                       float *out, cudaStream_t st);
 cudaError_t launch_beamform(const Handle &h, const void *corr, int n_beams, const double *delays,
                             const float *weights, int mode, int tint, float *out, cudaStream_t st);
 

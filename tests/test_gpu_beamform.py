@@ -104,3 +104,35 @@ def test_beamform_rejects_bad_arguments():
     c.close()
     with pytest.raises(RuntimeError):
         make_corr(blk, precision=0, max_beams=4)                                      # FP32 handle
+
+
+@pytest.mark.parametrize("precision,bound", [(0, 2e-6), (1, 4e-3), (2, 2e-2), (4, 2e-6)])
+@pytest.mark.parametrize("output,tint", [(1, 1), (1, 16), (2, 4)])
+@pytest.mark.parametrize("fmt,SB,N,C,S", [(synth.CI16, 2, 7, 64, 96), (synth.CI8, 1, 24, 256, 64),
+                                          (synth.CI16, 1, 1, 16, 160)])
+def test_incoherent_vs_oracle(precision, bound, output, tint, fmt, SB, N, C, S):
+    """Incoherent beam against the oracle on the GPU's own corrected block
+    decoded to FP64 (the kernel alone; FP32 accumulation over stations and
+    spectra, so FP32 operands are held to 2e-6), and end to end from the raw
+    samples at the operand precision's bound."""
+    rng = np.random.default_rng(N + C + S)
+    tau = rng.uniform(-5e-6, 5e-6, N)
+    blk = synth.make_block(800 + N, fmt, SB, N, C, S, sigma=100.0 if fmt == synth.CI16 else 20.0,
+                           tones=[synth.Tone(amp=20.0, channel=3, delays=tau)])
+    c = make_corr(blk, precision=precision, operand_scale=2.0 ** -6 if precision in (1, 2) else 0.0)
+    wts = rng.uniform(0.5, 1.5, N).astype(np.float32)
+    t = torch.from_numpy(tau).cuda()
+    corr = c.channelize_correct(torch.from_numpy(blk.raw).cuda(), t, t)
+    got = c.beamform_incoherent(corr, torch.from_numpy(wts).cuda(), output=output, tint=tint)
+    torch.cuda.synchronize()
+    got = got.cpu().numpy().astype(np.float64)
+    # the same operands as the kernel read, in FP64 and unscaled
+    y = corr.cpu().numpy().astype(np.float64) if precision == 0 else decode_planar(c, corr)
+    ref_k = oracle.beamform_incoherent(y, wts, mode=output, tint=tint)
+    ek = per_subband_rel(got, ref_k)
+    assert np.all(ek < 2e-6), ("kernel", ek)
+    chan = oracle.channelize(fmt, blk.raw, 16, C, S, blk.taps)
+    ref = oracle.beamform_incoherent(oracle.correct(chan, FS, blk.centres, tau, tau), wts, mode=output, tint=tint)
+    e = per_subband_rel(got, ref)
+    assert np.all(e < bound), e
+    c.close()
