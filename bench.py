@@ -358,16 +358,19 @@ def run_fx(args, w):
     ms_f = statistics.mean(e[0].elapsed_time(e[1]) for e in ev3[1:])
     ms_c = statistics.mean(e[1].elapsed_time(e[2]) for e in ev3[1:])
     ms_3 = statistics.mean(e[0].elapsed_time(e[3]) for e in ev3[1:])
-    # FP32 X-stage with the other register tile (2 x 4 stations), same operands
-    ms_x_small = None
+    # FP32 X-stage in its other forms, same operands
+    ms_x_forms = {}
     if w["precision"] == 0:
-        c2 = fxg.Correlator(w["N"], w["SB"], w["C"], w["S"], taps=taps, centres=centres, n_taps=w["T"],
-                            fmt=w["fmt"], precision=0, xf32_small_tiles=True)
-        vis2 = torch.empty_like(vis)
-        c2.correlate(corr, vis2)
-        ms_x_small = _time(lambda: c2.correlate(corr, vis2), args.steps, stream)
-        c2.close()
-        del vis2
+        for form in ("2x4", "3mult"):
+            c2 = fxg.Correlator(w["N"], w["SB"], w["C"], w["S"], taps=taps, centres=centres, n_taps=w["T"],
+                                fmt=w["fmt"], precision=0, xf32_form=form)
+            vis2 = torch.empty_like(vis)
+            c2.correlate(corr, vis2)
+            ms_x_forms[form] = _time(lambda: c2.correlate(corr, vis2), args.steps, stream)
+            ms_x_forms[form + "_rel_diff"] = float(torch.linalg.vector_norm((vis2 - vis).double()) /
+                                                   torch.linalg.vector_norm(vis.double()))
+            c2.close()
+            del vis2
     max_ms = max_over_ranks(total_ms, ws, dev)
     ms_step = max_ms / args.steps
     value = aggregate_value(sky_seconds(w) * args.steps, ws, max_ms / 1e3)
@@ -406,9 +409,9 @@ def run_fx(args, w):
             "correct_ms": ms_c, "correct_GBps": c_bytes / (ms_c * 1e-3) / 1e9,
             "correct_hbm_frac": c_bytes / (ms_c * 1e-3) / 1e9 / hbm},
     }
-    if ms_x_small is not None:
-        kernels["correlate_tiles"] = "4x4 stations" if w["N"] >= 16 else "2x4 stations"
-        kernels["correlate_2x4_tiles_ms"] = ms_x_small
+    if ms_x_forms:
+        kernels["correlate_form"] = "4x4-station tiles" if w["N"] >= 16 else "2x4-station tiles"
+        kernels["correlate_other_forms_ms"] = ms_x_forms
     # measured FP32 FMA throughput (registers only) beside the derived ALU peak
     sink = torch.zeros(1, dtype=torch.float32, device=dev)
     nblk, iters = 8 * torch.cuda.get_device_properties(dev).multi_processor_count, 4096

@@ -107,10 +107,13 @@ typedef struct {
  * samples, and allocates one assembled raw block as workspace. */
 #define FX_FLAG_STREAMING 0x1u
 
-/* Tuning hint for the FP32 X-stage: register tiles of 2 x 4 stations (more
- * threads per SM) instead of the default 4 x 4 from 16 stations up. Results
- * are identical up to FP32 rounding order. */
+/* Tuning hints for the FP32 X-stage (results agree up to FP32 rounding
+ * order). Default: 4 x 4-station register tiles from 16 stations up (2 x 4
+ * below). SMALL: 2 x 4 tiles. THREE_MULT: 2 x 4 tiles with the
+ * three-multiplication complex product (sum xr yr, sum xi yi,
+ * sum (xr + xi)(yr - yi)): 3 FMAs per complex MAC instead of 4. */
 #define FX_FLAG_XF32_SMALL_TILES 0x2u
+#define FX_FLAG_XF32_THREE_MULT 0x4u
 
 /* Failure-detection test hook: the tensor-core X-stage issues no operand
  * loads, so its consumer waits run out after about a millisecond; the call

@@ -76,6 +76,7 @@ FX_NOALLOC_MAX_PHASES = 1 << 20
 FX_FLAG_TEST_NO_LOADS = 0x80000000
 FX_FLAG_STREAMING = 0x1
 FX_FLAG_XF32_SMALL_TILES = 0x2
+FX_FLAG_XF32_THREE_MULT = 0x4
 FX_BEAM_VOLTAGES, FX_BEAM_STOKES_I, FX_BEAM_STOKES_IQUV = 0, 1, 2
 
 _lib = None

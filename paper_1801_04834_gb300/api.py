@@ -32,7 +32,7 @@ class Correlator:
                  taps, centres, n_taps: int = 16, fmt: int = FX_CI16, precision: int = FX_F32,
                  sample_rate_hz: float = SAMPLE_RATE_HZ, operand_scale: float = 0.0, device=None,
                  host_chunk_subbands: int = 0, streaming: bool = False, max_coarse_shift: int = 0,
-                 max_beams: int = 0, xf32_small_tiles: bool = False, extra_flags: int = 0):
+                 max_beams: int = 0, xf32_form: str = "auto", extra_flags: int = 0):
         self.lib = _abi.load()
         if device is not None:
             torch.cuda.set_device(device)
@@ -55,8 +55,10 @@ class Correlator:
         p.h_subband_centre_hz = centres.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         p.h_taps = taps.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         p.operand_scale = operand_scale
-        p.flags = (_abi.FX_FLAG_STREAMING if streaming else 0) | \
-            (_abi.FX_FLAG_XF32_SMALL_TILES if xf32_small_tiles else 0) | extra_flags
+        # FP32 X-stage form: "auto" (4x4 tiles from 16 stations up), "2x4" tiles, or
+        # "3mult" (2x4 tiles with the three-multiplication complex product)
+        form = {"auto": 0, "2x4": _abi.FX_FLAG_XF32_SMALL_TILES, "3mult": _abi.FX_FLAG_XF32_THREE_MULT}[xf32_form]
+        p.flags = (_abi.FX_FLAG_STREAMING if streaming else 0) | form | extra_flags
         p.host_chunk_subbands = host_chunk_subbands
         p.max_coarse_shift = max_coarse_shift
         p.max_beams = max_beams

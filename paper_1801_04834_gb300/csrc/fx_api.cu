@@ -88,7 +88,7 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
     if (!(p.sample_rate_hz > 0)) return fail(FX_ERR_INVALID, "sample_rate_hz must be > 0");
     if (!p.h_subband_centre_hz) return fail(FX_ERR_INVALID, "h_subband_centre_hz is NULL");
     if (!p.h_taps) return fail(FX_ERR_INVALID, "h_taps is NULL");
-    if ((p.flags & ~(FX_FLAG_TEST_NO_LOADS | FX_FLAG_STREAMING | FX_FLAG_XF32_SMALL_TILES)) != 0)
+    if ((p.flags & ~(FX_FLAG_TEST_NO_LOADS | FX_FLAG_STREAMING | FX_FLAG_XF32_SMALL_TILES | FX_FLAG_XF32_THREE_MULT)) != 0)
         return fail(FX_ERR_INVALID, "unknown flags 0x%x", p.flags);
     if (p.max_coarse_shift < 0 || p.max_coarse_shift > (1 << 24))
         return fail(FX_ERR_INVALID, "max_coarse_shift out of range");
@@ -131,11 +131,14 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
         const double a = 2.0 * 3.14159265358979323846 * (double)m / (double)C;
         tw[m] = make_float2((float)std::cos(a), (float)-std::sin(a));
     }
-    // FP32 X-stage tiles: 4 x 4 stations from 16 stations up unless the caller asks for 2 x 4
-    h->xf32_rs = (N >= 16 && !(p.flags & FX_FLAG_XF32_SMALL_TILES)) ? 4 : 2;
-    int ntiles = fxi::xf32_build_tiles(N, h->xf32_rs, nullptr);
+    // FP32 X-stage form: 4 x 4 tiles from 16 stations up unless the caller asks otherwise
+    h->xf32_mode = (p.flags & FX_FLAG_XF32_SMALL_TILES) ? 0 : (p.flags & FX_FLAG_XF32_THREE_MULT) ? 2
+                   : N >= 16                              ? 1
+                                                          : 0;
+    const int rs = h->xf32_mode == 1 ? 4 : 2;
+    int ntiles = fxi::xf32_build_tiles(N, rs, nullptr);
     std::vector<int2> tiles(ntiles);
-    fxi::xf32_build_tiles(N, h->xf32_rs, tiles.data());
+    fxi::xf32_build_tiles(N, rs, tiles.data());
     h->xf32_ntiles = ntiles;
 
     cudaError_t e = cudaSuccess;

@@ -26,7 +26,7 @@ struct Handle {
     int *d_status = nullptr;           // device-side error word
     int2 *d_xf32_tiles = nullptr;      // tile list of the FP32 correlator
     int xf32_ntiles = 0;
-    int xf32_rs = 2;                   // its row-tile height in stations (2 or 4)
+    int xf32_mode = 1;                 // its form: 0 2x4 tiles, 1 4x4 tiles, 2 2x4 tiles with 3 multiplications
     double *d_adj_partial = nullptr;   // [adjoint CTAs][I][3] per-CTA gradient sums
     // streaming (FX_FLAG_STREAMING): FIR history ping-pong + assembled block
     int hist_len = 0;                  // samples of history per (subband, station)

@@ -54,8 +54,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Thread g = blockIdx.x * blockDim.x + threadIdx.x works on tile g % ntiles of
 // channel g / ntiles; the CTA stages the rows of channels [ch_first, ch_first + max_ch).
 // kKC time samples per shared-memory chunk (32, or less for very many stations).
-template <int kKC, int RS>
-__global__ void __launch_bounds__(RS == 4 ? 256 : kMaxThreads, 1)
+template <int kKC, int RS, bool G3>
+__global__ void __launch_bounds__(G3 ? 384 : (RS == 4 ? 256 : kMaxThreads), 1)
 xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
                  const int2 *__restrict__ tiles, int ntiles, int N, int S, int IP, int max_ch,
                  long long total_ch)
@@ -113,11 +113,21 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
     //   acc += (xr, xi) * (yr, yr);  acc += (xi, -xr) * (yi, yi)
     // (per component the same two FMAs in the same order as the scalar form)
     constexpr int RA = 2 * RS;                     // row inputs of a tile
+    // G3 (three-multiplication form): t12[a][b] = (sum xr yr, sum xi yi) by one
+    // packed FMA on the natural (xr, xi), (yr, yi) pairs, t3[a][b] = sum
+    // (xr + xi)(yr - yi) by one scalar FMA; then re = t1 + t2 and
+    // im = t3 - t1 + t2 (3 FMAs per complex MAC instead of 4, no operand copies)
+    constexpr int RG = G3 ? RA : 1;
     float2 acc[RA][8];
+    float t3[RG][8];
 #pragma unroll
     for (int a = 0; a < RA; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b) acc[a][b] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < RG; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) t3[a][b] = 0.f;
 
     const int nchunks = (S + kKC - 1) / kKC;
     load_chunk(0, 0);
@@ -166,6 +176,25 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
                     y2 = rowp[2 * quarter + q];
                     y3 = rowp[3 * quarter + q];
                 }
+                if constexpr (G3) {
+                    const float2 yv[8] = {make_float2(y0.x, y0.y), make_float2(y0.z, y0.w),
+                                          make_float2(y1.x, y1.y), make_float2(y1.z, y1.w),
+                                          make_float2(y2.x, y2.y), make_float2(y2.z, y2.w),
+                                          make_float2(y3.x, y3.y), make_float2(y3.z, y3.w)};
+                    float dy[8];
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) dy[b] = yv[b].x - yv[b].y;
+#pragma unroll
+                    for (int a = 0; a < RA; ++a) {
+                        const float sx = xv[a].x + xv[a].y;
+#pragma unroll
+                        for (int b = 0; b < 8; ++b) {
+                            acc[a][b] = __ffma2_rn(xv[a], yv[b], acc[a][b]);   // (xr yr, xi yi)
+                            t3[a % RG][b] = fmaf(sx, dy[b], t3[a % RG][b]);   // (xr + xi)(yr - yi)
+                        }
+                    }
+                    continue;
+                }
                 const float yr[8] = {y0.x, y0.z, y1.x, y1.z, y2.x, y2.z, y3.x, y3.z};
                 const float yi[8] = {y0.y, y0.w, y1.y, y1.w, y2.y, y2.w, y3.y, y3.w};
 #pragma unroll
@@ -192,7 +221,14 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
             const int j = 4 * q + jj;
             if (i <= j && j < N) {
                 const long long b = (long long)j * (j + 1) / 2 + i;
-                float4 v = make_float4(acc[a][2 * jj].x, acc[a][2 * jj].y, acc[a][2 * jj + 1].x, acc[a][2 * jj + 1].y);
+                float4 v;
+                if constexpr (G3) {
+                    const float2 u0 = acc[a][2 * jj], u1 = acc[a][2 * jj + 1];
+                    v = make_float4(u0.x + u0.y, (t3[a % RG][2 * jj] - u0.x) + u0.y, u1.x + u1.y,
+                                    (t3[a % RG][2 * jj + 1] - u1.x) + u1.y);
+                } else {
+                    v = make_float4(acc[a][2 * jj].x, acc[a][2 * jj].y, acc[a][2 * jj + 1].x, acc[a][2 * jj + 1].y);
+                }
                 *reinterpret_cast<float4 *>(vis + (gch * B + b) * 4 + 2 * p) = v;
             }
         }
@@ -219,12 +255,13 @@ int xf32_build_tiles(int N, int RS, int2 *out)
 
 // CTA size (largest of 512, 384, 256, 128, 96, 64, 32 threads) whose touched
 // channels fit in shared memory, shrunk while the grid would not fill the GPU.
-bool xf32_geometry(int N, long long total_ch, int ntiles, int kc, int RS, int *threads, int *max_ch)
+bool xf32_geometry(int N, long long total_ch, int ntiles, int kc, int mode, int *threads, int *max_ch)
 {
     const int IP = 8 * ((N + 3) / 4);
     const size_t row_bytes = (size_t)kc * IP * sizeof(float2);
     static const int cand[] = {512, 384, 256, 128, 96, 64, 32};
-    int t = 0, mc = 0, k = RS == 4 ? 2 : 0;          // 64 accumulators: at most 256 threads
+    // 4x4 tiles (64 accumulators): at most 256 threads; three-multiplication form: 384
+    int t = 0, mc = 0, k = mode == 1 ? 2 : mode == 2 ? 1 : 0;
     for (; k < 7; ++k) {
         mc = (cand[k] + ntiles - 1) / ntiles + 1;
         if (2 * mc * row_bytes <= kSmemBudget) {
@@ -247,23 +284,26 @@ cudaError_t launch_xcorr_f32(const Handle &h, const float2 *corr, float2 *vis, c
 {
     const int N = h.p.n_stations, S = h.p.n_spectra;
     const int IP = 8 * ((N + 3) / 4);
-    const int RS = h.xf32_rs;
+    const int mode = h.xf32_mode;                   // 0: 2x4, 1: 4x4, 2: 2x4 three-multiplication
     const int nt = h.xf32_ntiles;
     const long long total = (long long)h.p.n_subbands * h.p.n_channels;
     int threads = 0, max_ch = 0, kc = 32;
     for (; kc >= 4; kc /= 2)
-        if (xf32_geometry(N, total, nt, kc, RS, &threads, &max_ch)) break;
+        if (xf32_geometry(N, total, nt, kc, mode, &threads, &max_ch)) break;
     if (kc < 4) return cudaErrorNotSupported;   // > ~800 stations
     const size_t smem = 2ull * max_ch * kc * IP * sizeof(float2);
     const long long blocks = (total * nt + threads - 1) / threads;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    auto pick = [&](auto rs) {
+    auto pick = [&](auto rs, auto g3) {
         constexpr int R = decltype(rs)::value;
-        return kc == 32 ? xcorr_f32_kernel<32, R> : kc == 16 ? xcorr_f32_kernel<16, R>
-                                               : kc == 8     ? xcorr_f32_kernel<8, R>
-                                                             : xcorr_f32_kernel<4, R>;
+        constexpr bool G = decltype(g3)::value;
+        return kc == 32 ? xcorr_f32_kernel<32, R, G> : kc == 16 ? xcorr_f32_kernel<16, R, G>
+                                                  : kc == 8     ? xcorr_f32_kernel<8, R, G>
+                                                                : xcorr_f32_kernel<4, R, G>;
     };
-    auto kern = RS == 4 ? pick(std::integral_constant<int, 4>{}) : pick(std::integral_constant<int, 2>{});
+    auto kern = mode == 1   ? pick(std::integral_constant<int, 4>{}, std::false_type{})
+                : mode == 2 ? pick(std::integral_constant<int, 2>{}, std::true_type{})
+                            : pick(std::integral_constant<int, 2>{}, std::false_type{});
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)blocks, threads, smem, st>>>(corr, vis, h.d_xf32_tiles, nt, N, S, IP, max_ch, total);

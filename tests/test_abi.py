@@ -62,7 +62,7 @@ def _params(**over):
 @pytest.mark.parametrize("field,value,status", [
     ("n_pols", 1, -5), ("n_channels", 32, -5), ("n_taps", 5, -5), ("n_stations", 0, -1),
     ("n_subbands", 0, -1), ("n_spectra", 0, -1), ("format", 7, -1), ("precision", 9, -1),
-    ("sample_rate_hz", 0.0, -1), ("flags", 4, -1), ("max_coarse_shift", -1, -1), ("operand_scale", 3.0, -1),
+    ("sample_rate_hz", 0.0, -1), ("flags", 8, -1), ("max_coarse_shift", -1, -1), ("operand_scale", 3.0, -1),
 ])
 def test_create_rejects_bad_params(lib, field, value, status):
     p, keep = _params(**{field: value})

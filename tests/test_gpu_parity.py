@@ -101,20 +101,21 @@ def test_correct_f32_parity(N, C, S, ramp):
     assert rel_err(got0.astype(np.float64), ref0) < 2e-6
 
 
-@pytest.mark.parametrize("small_tiles", [False, True])
+@pytest.mark.parametrize("form", ["auto", "2x4", "3mult"])
 @pytest.mark.parametrize("N,C,S,SB", [(8, 64, 100, 2), (64, 4 * 4, 33, 1), (1, 16, 20, 3),
                                       (13, 16, 65, 1), (76, 16, 40, 1), (96, 16, 17, 1),
                                       (150, 16, 45, 1), (64, 64, 70, 3), (17, 16, 9, 2), (18, 64, 31, 1)])
-def test_correlate_f32_parity(N, C, S, SB, small_tiles):
-    """FFMA X-stage with both register tiles (4 x 4 stations by default from
-    16 stations up, 2 x 4 with the small-tile hint), ragged station counts."""
+def test_correlate_f32_parity(N, C, S, SB, form):
+    """FFMA X-stage in each form (4 x 4 tiles by default from 16 stations,
+    2 x 4 tiles, 2 x 4 tiles with the three-multiplication product), ragged
+    station counts."""
     if C not in (16, 64, 256):
         pytest.skip("channel count not built")
     corr = synth.noise(21 + N, (SB, C, S, N, 2, 2))
     ref = oracle.correlate(corr)
     blk = synth.Block(0, SB, N, 2, C, 16, S, None, synth.kaiser_sinc_taps(16, C),
                       synth.subband_centres(SB))
-    c = make_corr(blk, xf32_small_tiles=small_tiles)
+    c = make_corr(blk, xf32_form=form)
     got = c.correlate(torch.from_numpy(corr).to("cuda", torch.float32)).cpu().numpy().astype(np.float64)
     assert got.shape == ref.shape
     assert np.all(per_subband_rel(got, ref) < 2e-6)
