@@ -510,6 +510,27 @@ def run_fx(args, w):
                 cv.close()
             except Exception as ex:  # report, do not hide
                 variants[name] = {"error": str(ex)[:200]}
+        # F-stage and X-stage piece by piece through two L2-sized operand buffers
+        # (fx_channelize_correlate); pieces of 48 MB or less
+        for name, prec, G, TC in (("chunked_fp16", 1, 4, 384), ("chunked_fp32", 0, 4, 192)):
+            try:
+                if w["S"] % TC or w["SB"] < G:
+                    continue
+                cv = fxg.Correlator(w["N"], w["SB"], w["C"], w["S"], taps=taps, centres=centres,
+                                    n_taps=w["T"], fmt=w["fmt"], precision=prec, chunk_subbands=G,
+                                    chunk_spectra=TC)
+                vis_v = torch.empty_like(vis)
+                cv.channelize_correlate(raw, delays, delays, bandpass=bandpass, out=vis_v)
+                torch.cuda.synchronize()
+                vs = _time(lambda: cv.channelize_correlate(raw, delays, delays, bandpass=bandpass, out=vis_v),
+                           args.steps, stream)
+                err = float(torch.linalg.vector_norm(vis_v.double() - ref_vis) / torch.linalg.vector_norm(ref_vis))
+                variants[name] = {"piece": f"{G} subbands x {TC} spectra", "step_ms": vs,
+                                  "step_rtf": sky_seconds(w) / (vs * 1e-3), "rel_err_vs_fp32_path": err}
+                del vis_v
+                cv.close()
+            except Exception as ex:  # report, do not hide
+                variants[name] = {"error": str(ex)[:200]}
 
     del raw, chan
     extras = {}

@@ -96,6 +96,12 @@ typedef struct {
                                     subbands; 0: no host pipeline */
     int max_coarse_shift;        /* with FX_FLAG_STREAMING: largest integer-sample
                                     coarse delay per station (>= 0) */
+    int chunk_subbands;          /* with chunk_spectra > 0: subbands per piece of
+                                    fx_channelize_correlate (>= 1) */
+    int chunk_spectra;           /* > 0: allocate two operand buffers of
+                                    chunk_subbands x chunk_spectra (a multiple of 64
+                                    dividing n_spectra) for fx_channelize_correlate;
+                                    precision FX_F32, FX_F16 or FX_BF16 */
     int max_beams;               /* in [0, 256]; > 0: allocate the beamformer's weight
                                     table for up to this many beams (fx_beamform);
                                     needs precision FX_F16 or FX_BF16 and
@@ -212,6 +218,20 @@ fx_status fx_correlate(fx_handle *h, const void *d_corr, float *d_vis, fx_stream
 fx_status fx_process_host(fx_handle *h, const void *h_raw, const double *h_delay_begin,
                           const double *h_delay_end, const float *h_bandpass, const float *h_gains,
                           float *h_vis, fx_stream stream);
+
+/* ---- F-stage and X-stage over L2-sized pieces ----------------------------
+ * The same result as fx_channelize_correct + fx_correlate (integrated over the
+ * whole block), computed piece by piece: for each group of chunk_subbands
+ * subbands and each run of chunk_spectra spectra, the fused F-stage writes the
+ * corrected operands of that piece into one of two handle-owned buffers (sized
+ * to stay in L2) and the X-stage adds the piece's products into d_vis, so the
+ * corrected block never goes through HBM as a whole. Buffers as in
+ * fx_channelize_correct (d_raw, delays, bandpass, gains) and fx_correlate
+ * (d_vis, overwritten). Handle needs chunk_spectra > 0 (else FX_ERR_INVALID).
+ * Stream-ordered, allocation free, graph-capturable. */
+fx_status fx_channelize_correlate(fx_handle *h, const void *d_raw, const double *d_delay_begin,
+                                  const double *d_delay_end, const float *d_bandpass, const float *d_gains,
+                                  float *d_vis, fx_stream stream);
 
 /* ---- streaming form --------------------------------------------------------
  * Consecutive blocks of a continuous stream (Sec. "Signal processing with GPU

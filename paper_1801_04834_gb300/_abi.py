@@ -33,6 +33,7 @@ class fx_params(ctypes.Structure):
                 ("h_taps", ctypes.POINTER(ctypes.c_float)),
                 ("operand_scale", ctypes.c_float), ("flags", ctypes.c_uint),
                 ("host_chunk_subbands", ctypes.c_int), ("max_coarse_shift", ctypes.c_int),
+                ("chunk_subbands", ctypes.c_int), ("chunk_spectra", ctypes.c_int),
                 ("max_beams", ctypes.c_int)]
 
 
@@ -60,6 +61,7 @@ SIGNATURES = {
     "fx_stream_reset": (I, [P, P]),
     "fx_beamform": (I, [P, P, I, P, P, I, I, P, P]),
     "fx_ffma_probe": (I, [I, I, P, P]),
+    "fx_channelize_correlate": (I, [P, P, P, P, P, P, P, P]),
     "fx_beamform_incoherent": (I, [P, P, P, I, I, P, P]),
     "fx_poll_status": (I, [P, ctypes.POINTER(ctypes.c_int)]),
     "fx_apply_gains": (I, [P, P, P, P, P, P]),

@@ -32,7 +32,8 @@ class Correlator:
                  taps, centres, n_taps: int = 16, fmt: int = FX_CI16, precision: int = FX_F32,
                  sample_rate_hz: float = SAMPLE_RATE_HZ, operand_scale: float = 0.0, device=None,
                  host_chunk_subbands: int = 0, streaming: bool = False, max_coarse_shift: int = 0,
-                 max_beams: int = 0, xf32_form: str = "auto", extra_flags: int = 0):
+                 max_beams: int = 0, xf32_form: str = "auto", extra_flags: int = 0,
+                 chunk_subbands: int = 0, chunk_spectra: int = 0):
         self.lib = _abi.load()
         if device is not None:
             torch.cuda.set_device(device)
@@ -62,6 +63,7 @@ class Correlator:
         p.host_chunk_subbands = host_chunk_subbands
         p.max_coarse_shift = max_coarse_shift
         p.max_beams = max_beams
+        p.chunk_subbands, p.chunk_spectra = chunk_subbands, chunk_spectra
         h = ctypes.c_void_p()
         check(self.lib.fx_create(ctypes.byref(p), ctypes.byref(h)), "fx_create")
         self.handle = h
@@ -186,6 +188,22 @@ class Correlator:
             self._opt(gains, "gains", torch.float32, 16 * N),
             self._dev(out, "corr", self.corr_dtype(), self.sizes.corr_bytes),
             _stream_ptr(stream)), "fx_channelize_correct")
+        return out
+
+    def channelize_correlate(self, raw, delay_begin, delay_end, bandpass=None, gains=None, out=None, stream=None):
+        """fx_channelize_correlate: raw samples to visibilities piece by piece
+        (chunk_subbands x chunk_spectra), the corrected block never whole in HBM."""
+        if out is None:
+            out = torch.empty(self.vis_shape(), dtype=torch.float32, device=self.device)
+        N, C = self.N, self.C
+        check(self.lib.fx_channelize_correlate(
+            self.handle, self._dev(raw, "raw", self.raw_dtype(), self.sizes.raw_bytes),
+            self._dev(delay_begin, "delay_begin", torch.float64, 8 * N),
+            self._dev(delay_end, "delay_end", torch.float64, 8 * N),
+            self._opt(bandpass, "bandpass", torch.float32, 4 * N * C),
+            self._opt(gains, "gains", torch.float32, 16 * N),
+            self._dev(out, "vis", torch.float32, self.sizes.vis_bytes), _stream_ptr(stream)),
+            "fx_channelize_correlate")
         return out
 
     def correlate(self, corr, out=None, stream=None):

@@ -66,7 +66,8 @@ __global__ void __launch_bounds__(PpfCfg<C>::NT, PpfCfg<C>::NT >= 512 ? 1 : 2)
 ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const float *__restrict__ taps,
                    const float2 *__restrict__ twiddle, const float2 *__restrict__ phase,
                    const float *__restrict__ bandpass, const float2 *__restrict__ gains, int N, int S, int I_pad,
-                   int S_pad, float scale, int rounds_per_cta, const float *__restrict__ flags)
+                   int S_pad, float scale, int rounds_per_cta, const float *__restrict__ flags, int s_base,
+                   int s_end)
 {
     using Cfg = PpfCfg<C>;
     constexpr int R = Cfg::R, NPC = Cfg::NPC, NT = Cfg::NT, ROW = Cfg::ROW;
@@ -95,10 +96,13 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
     const int tid = threadIdx.x;
     const int sb = blockIdx.z;
     const int n0 = blockIdx.x * NPC;                // station groups fastest
-    const int s0 = blockIdx.y * rounds_per_cta * kRound;
+    // spectra [s_base, s_end) of the block (s_base a multiple of 16); outputs are
+    // written at s - s_base with S_pad (planar) or S_pad (FP32: spectra per
+    // channel) as the output's spectrum stride
+    const int s0 = s_base + blockIdx.y * rounds_per_cta * kRound;
     const int rows_total = S + T - 1;
     const long long L = (long long)rows_total * C;
-    const int nrounds = min(rounds_per_cta, (S - s0 + kRound - 1) / kRound);
+    const int nrounds = min(rounds_per_cta, (s_end - s0 + kRound - 1) / kRound);
     const int I = N * kPols;
 
     auto stage = [&](int buf, int r0, int nrows) {
@@ -241,11 +245,11 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
                 const int task = it * NT + tid;
                 const int tr = task / R, k1 = task % R;
                 const int s = sr + tr / IC, i = 2 * n0 + tr % IC;
-                if (s < S && i < I) {
+                if (s < s_end && i < I) {
 #pragma unroll
                     for (int k2 = 0; k2 < R; ++k2) {
                         const int kout = k1 + R * ((k2 + R / 2) % R);
-                        out[(((long long)sb * C + kout) * S + s) * I + i] = y[it][k2];
+                        out[(((long long)sb * C + kout) * S_pad + (s - s_base)) * I + i] = y[it][k2];
                     }
                 }
             }
@@ -276,14 +280,14 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
                 if (i >= I) continue;
                 const float2 *src = u + il * SIL + kout * (kRound + 1);
                 float4 *re = reinterpret_cast<float4 *>(out + (((long long)sb * C + kout) * 2) * pstride +
-                                                        (long long)i * S_pad + sr);
+                                                        (long long)i * S_pad + (sr - s_base));
                 float4 *im = re + pstride / 4;
 #pragma unroll
                 for (int q = 0; q < kRound / 4; ++q) {
                     float2 v[4];
 #pragma unroll
                     for (int t = 0; t < 4; ++t)
-                        v[t] = (sr + 4 * q + t < S) ? src[4 * q + t] : make_float2(0.f, 0.f);
+                        v[t] = (sr + 4 * q + t < s_end) ? src[4 * q + t] : make_float2(0.f, 0.f);
                     re[q] = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
                     im[q] = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
                 }
@@ -300,7 +304,7 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
                 unsigned short re[kRound], im[kRound], rl[kRound], iml[kRound];
 #pragma unroll
                 for (int j = 0; j < kRound; ++j) {
-                    const float2 v = (sr + j < S) ? src[j] : make_float2(0.f, 0.f);
+                    const float2 v = (sr + j < s_end) ? src[j] : make_float2(0.f, 0.f);
                     re[j] = to_bits(v.x, OUT);
                     im[j] = to_bits(v.y, OUT);
                     if constexpr (OUT == 4) {
@@ -308,7 +312,8 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
                         iml[j] = __half_as_ushort(__float2half_rn(v.y - __half2float(__ushort_as_half(im[j]))));
                     }
                 }
-                const long long base = (((long long)sb * C + kout) * planes) * pstride + (long long)i * S_pad + sr;
+                const long long base =
+                    (((long long)sb * C + kout) * planes) * pstride + (long long)i * S_pad + (sr - s_base);
                 auto put = [&](long long off, const unsigned short (&v)[kRound]) {
                     uint4 w0, w1;
                     w0.x = v[0] | ((unsigned)v[1] << 16);
@@ -351,12 +356,17 @@ __global__ void planar_pad_kernel(unsigned short *__restrict__ corr, long long n
 
 template <int C, int T, typename TIn, int OUT>
 cudaError_t launch_t(const Handle &h, const void *raw, void *corr, const float *bandpass, const float2 *gains,
-                     const float *flags,
-                     cudaStream_t st)
+                     const float *flags, const FWindow *win, cudaStream_t st)
 {
     using Cfg = PpfCfg<C>;
     const int N = h.p.n_stations, S = h.p.n_spectra, SB = h.p.n_subbands;
-    const int rounds_total = (S + kRound - 1) / kRound;
+    // spectra [s_base, s_end) into an output whose spectrum stride is s_out
+    const int s_base = win ? win->s_base : 0;
+    const int s_end = win ? win->s_end : S;
+    const int s_out = win ? win->s_out : (OUT == 1 ? S : h.S_pad);
+    if (s_base % kRound != 0 || s_end > S || s_base >= s_end || s_end - s_base > s_out)
+        return cudaErrorInvalidValue;
+    const int rounds_total = (s_end - s_base + kRound - 1) / kRound;
     const int sgroups = (N + Cfg::NPC - 1) / Cfg::NPC;
     // long runs of rounds per CTA amortise the T-1 history rows each CTA reads
     // and filters first; shorten them only while the grid would be under ~8 waves
@@ -370,53 +380,55 @@ cudaError_t launch_t(const Handle &h, const void *raw, void *corr, const float *
     if (e != cudaSuccess) return e;
     const float scale = (OUT == 1 || OUT == 5) ? 1.f : h.operand_scale;
     kern<<<grid, Cfg::NT, smem, st>>>(reinterpret_cast<const TIn *>(raw), corr, h.d_taps, h.d_twiddle, h.d_phase,
-                                      bandpass, gains, N, S, h.I_pad, h.S_pad, scale, rpc, flags);
+                                      bandpass, gains, N, S, h.I_pad, s_out, scale, rpc, flags, s_base, s_end);
     e = cudaGetLastError();
     if (e != cudaSuccess || OUT == 1) return e;
     const int S16 = rounds_total * kRound;
-    if (h.I_pad > h.I || h.S_pad > S16) {
+    if (h.I_pad > h.I || s_out > S16) {
         const long long rows = (long long)SB * C * (OUT == 4 ? 4 : 2) * h.I_pad;
         if (rows > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
         // zero bits are zero in either element size: FP32 rows are twice as many 16-bit words
         const int w = OUT == 5 ? 2 : 1;
         planar_pad_kernel<<<(unsigned)rows, 64, 0, st>>>(reinterpret_cast<unsigned short *>(corr), rows, h.I, h.I_pad,
-                                                          w * S16, w * h.S_pad);
+                                                          w * S16, w * s_out);
         e = cudaGetLastError();
     }
     return e;
 }
 
 template <int C, int T, typename TIn>
-cudaError_t launch_out(const Handle &h, const void *raw, void *corr, const float *bp, const float2 *g, const float *fl, cudaStream_t st)
+cudaError_t launch_out(const Handle &h, const void *raw, void *corr, const float *bp, const float2 *g, const float *fl,
+                       const FWindow *w, cudaStream_t st)
 {
     switch (h.p.precision) {
-    case FX_F32: return launch_t<C, T, TIn, 1>(h, raw, corr, bp, g, fl, st);
-    case FX_F16: return launch_t<C, T, TIn, 2>(h, raw, corr, bp, g, fl, st);
-    case FX_BF16: return launch_t<C, T, TIn, 3>(h, raw, corr, bp, g, fl, st);
-    case FX_TF32_SPLIT: return launch_t<C, T, TIn, 5>(h, raw, corr, bp, g, fl, st);
-    default: return launch_t<C, T, TIn, 4>(h, raw, corr, bp, g, fl, st);
+    case FX_F32: return launch_t<C, T, TIn, 1>(h, raw, corr, bp, g, fl, w, st);
+    case FX_F16: return launch_t<C, T, TIn, 2>(h, raw, corr, bp, g, fl, w, st);
+    case FX_BF16: return launch_t<C, T, TIn, 3>(h, raw, corr, bp, g, fl, w, st);
+    case FX_TF32_SPLIT: return launch_t<C, T, TIn, 5>(h, raw, corr, bp, g, fl, w, st);
+    default: return launch_t<C, T, TIn, 4>(h, raw, corr, bp, g, fl, w, st);
     }
 }
 
 template <int C, typename TIn>
 cudaError_t launch_taps(const Handle &h, const void *raw, void *corr, const float *bp, const float2 *g,
-                        const float *fl, cudaStream_t st)
+                        const float *fl, const FWindow *w, cudaStream_t st)
 {
     switch (h.p.n_taps) {
-    case 4: return launch_out<C, 4, TIn>(h, raw, corr, bp, g, fl, st);
-    case 8: return launch_out<C, 8, TIn>(h, raw, corr, bp, g, fl, st);
-    case 16: return launch_out<C, 16, TIn>(h, raw, corr, bp, g, fl, st);
+    case 4: return launch_out<C, 4, TIn>(h, raw, corr, bp, g, fl, w, st);
+    case 8: return launch_out<C, 8, TIn>(h, raw, corr, bp, g, fl, w, st);
+    case 16: return launch_out<C, 16, TIn>(h, raw, corr, bp, g, fl, w, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <typename TIn>
-cudaError_t launch_fmt(const Handle &h, const void *raw, void *corr, const float *bp, const float2 *g, const float *fl, cudaStream_t st)
+cudaError_t launch_fmt(const Handle &h, const void *raw, void *corr, const float *bp, const float2 *g, const float *fl,
+                       const FWindow *w, cudaStream_t st)
 {
     switch (h.p.n_channels) {
-    case 16: return launch_taps<16, TIn>(h, raw, corr, bp, g, fl, st);
-    case 64: return launch_taps<64, TIn>(h, raw, corr, bp, g, fl, st);
-    case 256: return launch_taps<256, TIn>(h, raw, corr, bp, g, fl, st);
+    case 16: return launch_taps<16, TIn>(h, raw, corr, bp, g, fl, w, st);
+    case 64: return launch_taps<64, TIn>(h, raw, corr, bp, g, fl, w, st);
+    case 256: return launch_taps<256, TIn>(h, raw, corr, bp, g, fl, w, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -424,11 +436,11 @@ cudaError_t launch_fmt(const Handle &h, const void *raw, void *corr, const float
 }  // namespace
 
 cudaError_t launch_channelize_correct(const Handle &h, const void *raw, const float *bandpass, const float2 *gains,
-                                      void *corr, cudaStream_t st, const float *flags)
+                                      void *corr, cudaStream_t st, const float *flags, const FWindow *window)
 {
-    if (h.p.format == FX_CI16) return launch_fmt<short2>(h, raw, corr, bandpass, gains, flags, st);
-    if (h.p.format == FX_CI8) return launch_fmt<char2>(h, raw, corr, bandpass, gains, flags, st);
-    return launch_fmt<ppf::ci4_t>(h, raw, corr, bandpass, gains, flags, st);
+    if (h.p.format == FX_CI16) return launch_fmt<short2>(h, raw, corr, bandpass, gains, flags, window, st);
+    if (h.p.format == FX_CI8) return launch_fmt<char2>(h, raw, corr, bandpass, gains, flags, window, st);
+    return launch_fmt<ppf::ci4_t>(h, raw, corr, bandpass, gains, flags, window, st);
 }
 
 }  // namespace fxi

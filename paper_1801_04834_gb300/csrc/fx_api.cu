@@ -53,13 +53,22 @@ bool xstage_supported(const Handle &h)
     return xtc_plan(h, &rl, &stg, &sb);
 }
 
-cudaError_t launch_xstage(const Handle &h, const void *corr, float2 *vis, cudaStream_t st)
+cudaError_t launch_xstage(const Handle &h, const void *corr, float2 *vis, cudaStream_t st, bool accumulate)
 {
     switch (h.p.precision) {
-    case FX_F32: return launch_xcorr_f32(h, static_cast<const float2 *>(corr), vis, st);
-    case FX_TF32_SPLIT: return launch_xcorr_tf32(h, static_cast<const float *>(corr), vis, st);
-    default: return launch_xcorr_tc(h, corr, vis, st);
+    case FX_F32: return launch_xcorr_f32(h, static_cast<const float2 *>(corr), vis, st, accumulate);
+    case FX_TF32_SPLIT:
+        if (accumulate) return cudaErrorNotSupported;
+        return launch_xcorr_tf32(h, static_cast<const float *>(corr), vis, st);
+    default: return launch_xcorr_tc(h, corr, vis, st, accumulate);
     }
+}
+
+// Operand bytes of one piece of fx_channelize_correlate.
+static size_t chunk_bytes(const Handle &h)
+{
+    const size_t G = (size_t)h.p.chunk_subbands, C = h.p.n_channels, T = h.p.chunk_spectra;
+    return h.p.precision == FX_F32 ? G * C * T * h.I * sizeof(float2) : G * C * 2 * (size_t)h.I_pad * T * 2;
 }
 
 }  // namespace fxi
@@ -94,6 +103,11 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
         return fail(FX_ERR_INVALID, "max_coarse_shift out of range");
     if (p.host_chunk_subbands < 0) return fail(FX_ERR_INVALID, "host_chunk_subbands must be >= 0");
     if (p.max_beams < 0 || p.max_beams > 256) return fail(FX_ERR_INVALID, "max_beams must be in [0, 256]");
+    if (p.chunk_spectra < 0 || (p.chunk_spectra > 0 && (p.chunk_spectra % 64 != 0 || p.n_spectra % p.chunk_spectra != 0 ||
+                                                        p.chunk_subbands < 1 || p.chunk_subbands > p.n_subbands)))
+        return fail(FX_ERR_INVALID, "chunk_spectra must be a multiple of 64 dividing n_spectra, chunk_subbands in [1, SB]");
+    if (p.chunk_spectra > 0 && p.precision != FX_F32 && p.precision != FX_F16 && p.precision != FX_BF16)
+        return fail(FX_ERR_UNSUPPORTED, "fx_channelize_correlate supports FX_F32, FX_F16 and FX_BF16");
     if (p.max_beams > 0 && ((p.precision != FX_F16 && p.precision != FX_BF16) || p.n_stations > 64))
         return fail(FX_ERR_UNSUPPORTED, "the beamformer needs FX_F16 or FX_BF16 operands and at most 64 stations");
     float scale = p.operand_scale == 0.f ? 1.f : p.operand_scale;
@@ -167,6 +181,10 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
     FX_TRY(cudaMemset(h->d_status, 0, sizeof(int) * 4));
     if (p.host_chunk_subbands > 0) FX_TRY(fxi::pipe_create(*h, p.host_chunk_subbands));
     if (p.max_beams > 0) FX_TRY(cudaMalloc(&h->d_bfw, fxi::bf_weight_bytes(*h, p.max_beams)));
+    if (p.chunk_spectra > 0) {
+        FX_TRY(cudaMalloc(&h->d_chunk[0], fxi::chunk_bytes(*h)));
+        FX_TRY(cudaMalloc(&h->d_chunk[1], fxi::chunk_bytes(*h)));
+    }
     if (p.flags & FX_FLAG_STREAMING) {
         h->hist_len = (T - 1) * C + p.max_coarse_shift;
         const size_t hist_bytes = (size_t)SB * N * h->hist_len * fxi::raw_sample_bytes(*h);
@@ -198,6 +216,8 @@ extern "C" void fx_destroy(fx_handle *h)
     cudaFree(h->d_hist[1]);
     cudaFree(h->d_block);
     cudaFree(h->d_bfw);
+    cudaFree(h->d_chunk[0]);
+    cudaFree(h->d_chunk[1]);
     fxi::pipe_destroy(*h);
     delete h;
 }
@@ -355,6 +375,48 @@ extern "C" fx_status fx_beamform_incoherent(fx_handle *h, const void *d_corr, co
     return after_launch(fxi::launch_beamform_incoherent(*h, d_corr, d_station_weights, output, tint, d_out,
                                                         (cudaStream_t)stream),
                         who);
+}
+
+extern "C" fx_status fx_channelize_correlate(fx_handle *h, const void *d_raw, const double *d_delay_begin,
+                                             const double *d_delay_end, const float *d_bandpass, const float *d_gains,
+                                             float *d_vis, fx_stream stream)
+{
+    const char *who = "fx_channelize_correlate";
+    fx_status st = check_handle(h, who);
+    if (st) return st;
+    if (!h->d_chunk[0]) return fail(FX_ERR_INVALID, "%s: handle was created with chunk_spectra = 0", who);
+    if (!d_raw || !d_vis || !d_delay_begin || !d_delay_end) return fail(FX_ERR_INVALID, "%s: NULL buffer", who);
+    if (((uintptr_t)d_raw & 15) || ((uintptr_t)d_vis & 15) || ((uintptr_t)d_gains & 7) ||
+        ((uintptr_t)d_bandpass & 3) || ((uintptr_t)d_delay_begin & 7) || ((uintptr_t)d_delay_end & 7))
+        return fail(FX_ERR_INVALID, "%s: misaligned buffer", who);
+    if (!fxi::xstage_supported(*h)) return fail(FX_ERR_UNSUPPORTED, "%s: no tensor-core plan", who);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int SB = h->p.n_subbands, N = h->p.n_stations, C = h->p.n_channels, S = h->p.n_spectra;
+    const int G = h->p.chunk_subbands, TC = h->p.chunk_spectra;
+    const size_t raw_sb = (size_t)N * (S + h->p.n_taps - 1) * C * fxi::raw_sample_bytes(*h);   // bytes per subband
+    const size_t vis_sb = (size_t)C * h->B * 4;                                                 // float2 per subband
+    const float2 *gains = reinterpret_cast<const float2 *>(d_gains);
+    cudaError_t e = fxi::launch_phase_table(*h, d_delay_begin, d_delay_end, s);
+    long long k = 0;
+    for (int g0 = 0; g0 < SB && e == cudaSuccess; g0 += G) {
+        fxi::Handle v = *h;                                   // view of subbands [g0, g0 + gs)
+        const int gs = SB - g0 < G ? SB - g0 : G;
+        v.p.n_subbands = gs;
+        v.d_centres = h->d_centres + g0;
+        v.d_phase = h->d_phase + (size_t)g0 * N * C;
+        const void *raw_g = static_cast<const unsigned char *>(d_raw) + (size_t)g0 * raw_sb;
+        float2 *vis_g = reinterpret_cast<float2 *>(d_vis) + (size_t)g0 * vis_sb;
+        fxi::Handle x = v;                                    // the X-stage's view of one piece
+        x.p.n_spectra = TC;
+        x.S_pad = TC;
+        for (int t0 = 0; t0 < S && e == cudaSuccess; t0 += TC, ++k) {
+            void *buf = h->d_chunk[k & 1];
+            const fxi::FWindow w{t0, t0 + TC, TC};
+            e = fxi::launch_channelize_correct(v, raw_g, d_bandpass, gains, buf, s, nullptr, &w);
+            if (e == cudaSuccess) e = fxi::launch_xstage(x, buf, vis_g, s, t0 > 0);
+        }
+    }
+    return after_launch(e, who);
 }
 
 extern "C" fx_status fx_stream_reset(fx_handle *h, fx_stream stream)

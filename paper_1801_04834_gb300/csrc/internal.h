@@ -33,6 +33,8 @@ struct Handle {
     void *d_hist[2] = {nullptr, nullptr};
     int hist_cur = 0;
     void *d_block = nullptr;
+    // fx_channelize_correlate (chunk_spectra > 0): two operand buffers of one piece
+    void *d_chunk[2] = {nullptr, nullptr};
     // beamformer (max_beams > 0): weight table [SB][C][re/im][ceil64(max_beams)][64]
     unsigned short *d_bfw = nullptr;
     // host pipeline (fx_process_host), when host_chunk_subbands > 0
@@ -46,9 +48,15 @@ struct Handle {
 cudaError_t launch_ppf(const Handle &h, const void *raw, float2 *chan, cudaStream_t st);
 bool ppf_supported(int C, int T);
 
-// channelize_correct.cu (flags: [N][S] lost-data weights or null)
+// channelize_correct.cu (flags: [N][S] lost-data weights or null). A window
+// produces spectra [s_base, s_end) (s_base a multiple of 16) into an output
+// whose spectrum stride is s_out (spectrum s at s - s_base); null = the block.
+struct FWindow {
+    int s_base, s_end, s_out;
+};
 cudaError_t launch_channelize_correct(const Handle &h, const void *raw, const float *bandpass, const float2 *gains,
-                                      void *corr, cudaStream_t st, const float *flags = nullptr);
+                                      void *corr, cudaStream_t st, const float *flags = nullptr,
+                                      const FWindow *window = nullptr);
 
 // stream.cu
 int raw_sample_bytes(const Handle &h);   // bytes of one time sample of one station (both pols)
@@ -68,7 +76,8 @@ cudaError_t launch_correct_f32_noalloc(int N, int SB, int C, int S, double fs, c
 
 // xcorr_f32.cu
 int xf32_build_tiles(int N, int RS, int2 *host_tiles /* may be null: count only */);
-cudaError_t launch_xcorr_f32(const Handle &h, const float2 *corr, float2 *vis, cudaStream_t st);
+cudaError_t launch_xcorr_f32(const Handle &h, const float2 *corr, float2 *vis, cudaStream_t st,
+                             bool accumulate = false);   // accumulate: add to vis
 
 // host_pipeline.cu
 cudaError_t pipe_create(Handle &h, int chunk);
@@ -98,11 +107,12 @@ cudaError_t launch_ffma_probe(int iterations, int blocks, float *sink, cudaStrea
 
 // fx_api.cu: the X-stage of the handle's precision
 bool xstage_supported(const Handle &h);
-cudaError_t launch_xstage(const Handle &h, const void *corr, float2 *vis, cudaStream_t st);
+cudaError_t launch_xstage(const Handle &h, const void *corr, float2 *vis, cudaStream_t st, bool accumulate = false);
 
 // xcorr_tc.cu
 bool xtc_plan(const Handle &h, int *rload, int *stages, unsigned *stage_bytes);
-cudaError_t launch_xcorr_tc(const Handle &h, const void *corr, float2 *vis, cudaStream_t st);
+cudaError_t launch_xcorr_tc(const Handle &h, const void *corr, float2 *vis, cudaStream_t st,
+                            bool accumulate = false);    // accumulate: add to vis
 
 }  // namespace fxi
 

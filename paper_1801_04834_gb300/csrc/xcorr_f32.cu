@@ -58,7 +58,7 @@ template <int kKC, int RS, bool G3>
 __global__ void __launch_bounds__(G3 ? 384 : (RS == 4 ? 256 : kMaxThreads), 1)
 xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
                  const int2 *__restrict__ tiles, int ntiles, int N, int S, int IP, int max_ch,
-                 long long total_ch)
+                 long long total_ch, int accumulate)
 {
     extern __shared__ float4 sm[];   // [2][max_ch][KC][IP/2] float4
     const int I = 2 * N;
@@ -229,7 +229,15 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
                 } else {
                     v = make_float4(acc[a][2 * jj].x, acc[a][2 * jj].y, acc[a][2 * jj + 1].x, acc[a][2 * jj + 1].y);
                 }
-                *reinterpret_cast<float4 *>(vis + (gch * B + b) * 4 + 2 * p) = v;
+                float4 *dst = reinterpret_cast<float4 *>(vis + (gch * B + b) * 4 + 2 * p);
+                if (accumulate) {                      // add to the sums of earlier time chunks
+                    const float4 o = *dst;
+                    v.x += o.x;
+                    v.y += o.y;
+                    v.z += o.z;
+                    v.w += o.w;
+                }
+                *dst = v;
             }
         }
     }
@@ -280,7 +288,7 @@ bool xf32_geometry(int N, long long total_ch, int ntiles, int kc, int mode, int 
     return true;
 }
 
-cudaError_t launch_xcorr_f32(const Handle &h, const float2 *corr, float2 *vis, cudaStream_t st)
+cudaError_t launch_xcorr_f32(const Handle &h, const float2 *corr, float2 *vis, cudaStream_t st, bool accumulate)
 {
     const int N = h.p.n_stations, S = h.p.n_spectra;
     const int IP = 8 * ((N + 3) / 4);
@@ -306,7 +314,8 @@ cudaError_t launch_xcorr_f32(const Handle &h, const float2 *corr, float2 *vis, c
                             : pick(std::integral_constant<int, 2>{}, std::false_type{});
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)blocks, threads, smem, st>>>(corr, vis, h.d_xf32_tiles, nt, N, S, IP, max_ch, total);
+    kern<<<(unsigned)blocks, threads, smem, st>>>(corr, vis, h.d_xf32_tiles, nt, N, S, IP, max_ch, total,
+                                                   accumulate ? 1 : 0);
     return cudaGetLastError();
 }
 

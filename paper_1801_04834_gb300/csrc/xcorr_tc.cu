@@ -89,6 +89,7 @@ struct TcCommon {
     float inv_scale2;
     long long timeout_cycles;
     int no_tma;                       // failure-detection test: issue no loads
+    int accumulate;                   // add to the visibilities instead of writing them
 };
 
 template <int MAXJ>
@@ -357,6 +358,17 @@ __global__ void __launch_bounds__(kThreads, 1) xcorr_tc_kernel(const __grid_cons
                 float re[16], im[16];
                 tmem_ld16(t_re + 16 * cc, re);
                 tmem_ld16(t_im + 16 * cc, im);
+                // accumulating: the sums of earlier time chunks, loaded while TMEM is read
+                float4 old[8];
+                if (a.accumulate) {
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const int j = j0 + jj;
+                        old[jj] = (i <= j && j < J.N)
+                                      ? *reinterpret_cast<const float4 *>(vrow + ((long long)j * (j + 1) / 2 + i) * 4 + 2 * p)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
                 tmem_ld_wait();
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
@@ -364,8 +376,14 @@ __global__ void __launch_bounds__(kThreads, 1) xcorr_tc_kernel(const __grid_cons
                     if (i <= j && j < J.N) {
                         const long long b = (long long)j * (j + 1) / 2 + i;
                         const float s = a.inv_scale2;
-                        *reinterpret_cast<float4 *>(vrow + b * 4 + 2 * p) =
-                            make_float4(re[2 * jj] * s, im[2 * jj] * s, re[2 * jj + 1] * s, im[2 * jj + 1] * s);
+                        float4 v = make_float4(re[2 * jj] * s, im[2 * jj] * s, re[2 * jj + 1] * s, im[2 * jj + 1] * s);
+                        if (a.accumulate) {
+                            v.x += old[jj].x;
+                            v.y += old[jj].y;
+                            v.z += old[jj].z;
+                            v.w += old[jj].w;
+                        }
+                        *reinterpret_cast<float4 *>(vrow + b * 4 + 2 * p) = v;
                     }
                 }
             }
@@ -526,6 +544,7 @@ void fill_common(TcCommon &c, int *status, float scale, long long timeout, int n
     c.inv_scale2 = 1.0f / (scale * scale);
     c.timeout_cycles = timeout;
     c.no_tma = no_tma;
+    c.accumulate = 0;
 }
 
 }  // namespace
@@ -544,7 +563,7 @@ bool xtc_plan(const Handle &h, int *rload, int *stages, unsigned *stage_bytes)
     return true;
 }
 
-cudaError_t launch_xcorr_tc(const Handle &h, const void *corr, float2 *vis, cudaStream_t st)
+cudaError_t launch_xcorr_tc(const Handle &h, const void *corr, float2 *vis, cudaStream_t st, bool accumulate)
 {
     TcConfig cfg = default_config(h.p.precision, h.I_pad);
     std::vector<JobShape> js(1);
@@ -555,6 +574,7 @@ cudaError_t launch_xcorr_tc(const Handle &h, const void *corr, float2 *vis, cuda
     if (!geometry(cfg, h.p.precision, js, P.c)) return cudaErrorNotSupported;
     if (!encode_job(cfg, h.p.precision, js[0], h.S_pad / kBK, P.jobs[0])) return cudaErrorInvalidValue;
     fill_common(P.c, h.d_status, h.operand_scale, h.tc_timeout_cycles, h.tc_test_no_tma);
+    P.c.accumulate = accumulate ? 1 : 0;
     P.c.items = nullptr;
     P.c.n_items = js[0].n_ch * P.jobs[0].items_per_ch;
     return launch_params(P, h.num_sms, st);
