@@ -6,8 +6,9 @@
 // Sec. "Processing steps" (fixed-point input converted to floating point).
 // The paper's FFT was a cuFFT call; here the FFT is fused behind the FIR.
 //
-// Work decomposition (one CTA = NPC stations x 2 pols x all C channels x a run
-// of spectra):
+// Work decomposition of ppf_kernel (C = 256; C = 16 and 64 use the
+// warp-specialised ppf_ws_kernel below, same FIR and FFT, overlapped): one CTA
+// = NPC stations x 2 pols x all C channels x a run of spectra:
 //   * Raw samples stream through shared memory 16 time rows (one row = C
 //     samples) at a time with cp.async, double buffered.
 //   * FIR: thread (station, channel c, pol p) keeps the last T samples of its
@@ -180,27 +181,232 @@ ppf_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *
     cp_async_wait<0>();
 }
 
-template <int C, int T, typename TIn>
-cudaError_t launch_t(const Handle &h, const void *raw, float2 *chan, cudaStream_t st)
+// ---------------------------------------------------------------------------
+// Warp-specialised form (C = 16, 64): the FIR (CUDA-core FMA bound) and the
+// FFT (shared-memory bound) of consecutive rounds overlap instead of
+// alternating between CTA-wide barriers. A CTA holds NF FIR threads (NPC
+// stations x 2 pols x C channels, the sliding-window FIR above) and NF FFT
+// threads:
+//   FIR round b -> transform rows u[b & 1]; bar.arrive FULL[b & 1]
+//   FFT round b: bar.sync FULL[b & 1], both FFT passes in place in u[b & 1],
+//                output; bar.arrive EMPTY[b & 1], which FIR round b + 2 waits for
+// Each transform row is handled by R consecutive lanes of one FFT warp, so the
+// in-place pass 1 (every lane reads its column of the row before any lane
+// writes the row back transposed) and pass 2 need only __syncwarp. Raw rows
+// are staged by the FIR threads alone (barrier RAW). Named barriers are
+// hardware barriers with fixed arrival counts; every FIR thread and every FFT
+// thread runs the same number of rounds, so each barrier instance completes.
+// 128 FIR + 128 FFT threads at <= 85 registers and <= 56 KB of shared memory
+// leave room for three CTAs per SM.
+template <int C>
+struct PpfWsCfg {
+    static constexpr int R = PpfCfg<C>::R;
+    static constexpr int NPC = 64 / C;                       // C = 64: 1 station, C = 16: 4
+    static constexpr int NF = NPC * C * kPols;               // 128 FIR threads (and 128 FFT threads)
+    static constexpr int NTR = NPC * kPols * kRound;         // transforms per round
+    static constexpr int ROW = PpfCfg<C>::ROW;
+    static constexpr int ITERS = NTR * R / NF;               // FFT tasks per FFT thread per round
+    static_assert(C == 16 || C == 64, "warp-specialised PPF: C = 16 or 64");
+    static_assert(NTR * R % NF == 0 && 32 % R == 0, "a transform row stays inside one warp");
+};
+
+template <int C, typename TIn>
+constexpr size_t ppf_ws_smem_bytes()
 {
-    using Cfg = PpfCfg<C>;
+    using W = PpfWsCfg<C>;
+    return (size_t)C * sizeof(float2) + 2ull * kRound * W::NPC * C * kPols * sizeof(TIn) +
+           2ull * W::NTR * W::ROW * sizeof(float2);
+}
+
+enum { kBarRaw = 1, kBarFull = 2, kBarEmpty = 4 };   // FULL/EMPTY use ids +0, +1
+
+__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void bar_arrive(int id, int n)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+template <int C, int T, typename TIn>
+__global__ void __launch_bounds__(2 * PpfWsCfg<C>::NF, 3)
+ppf_ws_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *__restrict__ taps,
+              const float2 *__restrict__ twiddle, int N, int S, int rounds_per_cta)
+{
+    using W = PpfWsCfg<C>;
+    constexpr int R = W::R, NPC = W::NPC, NF = W::NF, ROW = W::ROW, NTR = W::NTR;
+    constexpr int ROW_BYTES = C * kPols * (int)sizeof(TIn);
+    constexpr int BUF_BYTES = kRound * NPC * ROW_BYTES;
+    constexpr int IC = NPC * kPols;
+    constexpr int ALL = 2 * NF;
+    static_assert(ROW_BYTES % 16 == 0, "rows must be whole 16-byte chunks");
+    static_assert(3 * (ppf_ws_smem_bytes<C, TIn>() + 1024) <= 228 * 1024, "three CTAs per SM");
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2 *tw = reinterpret_cast<float2 *>(smem);
+    unsigned char *inbuf = smem + C * sizeof(float2);
+    float2 *u = reinterpret_cast<float2 *>(inbuf + 2 * BUF_BYTES);   // [2][NTR][ROW]
+
+    const int tid = threadIdx.x;
+    const int sb = blockIdx.z;
+    const int n0 = blockIdx.y * NPC;
+    const int s0 = blockIdx.x * rounds_per_cta * kRound;
+    const int rows_total = S + T - 1;
+    const long long L = (long long)rows_total * C;
+    const int nrounds = min(rounds_per_cta, (S - s0 + kRound - 1) / kRound);
+
+    for (int i = tid; i < C; i += ALL) tw[i] = twiddle[i];
+    __syncthreads();
+
+    if (tid < NF) {
+        // ---- FIR threads: thread = (station nl, channel c, pol p) ----
+        auto stage = [&](int buf, int r0, int nrows) {
+            const int chunks = nrows * ROW_BYTES / 16;
+            for (int q = tid; q < NPC * chunks; q += NF) {
+                const int st = q / chunks, ch = q - st * chunks;
+                const int n = n0 + st;
+                const int row_in = (ch * 16) / ROW_BYTES;
+                const int byte_in_row = (ch * 16) - row_in * ROW_BYTES;
+                unsigned char *dst = inbuf + buf * BUF_BYTES + (row_in * NPC + st) * ROW_BYTES + byte_in_row;
+                const bool ok = (n < N) && (r0 + row_in < rows_total);
+                const unsigned char *src = reinterpret_cast<const unsigned char *>(raw);
+                if (ok) src += ((((long long)sb * N + n) * L + (long long)r0 * C) * kPols) * sizeof(TIn) + ch * 16;
+                cp_async16(dst, src, ok ? 16 : 0);
+            }
+        };
+        const int p = tid % kPols;
+        const int c = (tid / kPols) % C;
+        const int nl = tid / (kPols * C);
+        float2 h[T];
+#pragma unroll
+        for (int k = 0; k < T; ++k) h[k] = make_float2(taps[k * C + c], taps[k * C + c]);
+
+        stage(1, s0, T - 1);                        // FIR history
+        cp_async_commit();
+        stage(0, s0 + T - 1, kRound);               // round 0
+        cp_async_commit();
+        cp_async_wait<1>();
+        bar_sync(kBarRaw, NF);
+        float2 win[T];
+        const TIn *in1 = reinterpret_cast<const TIn *>(inbuf + BUF_BYTES);
+#pragma unroll
+        for (int k = 0; k < T - 1; ++k) win[k] = to_f2(in1[k * NF + tid]);
+        win[T - 1] = make_float2(0.f, 0.f);
+        bar_sync(kBarRaw, NF);
+        if (nrounds > 1) stage(1, s0 + T - 1 + kRound, kRound);
+        cp_async_commit();
+
+        for (int b = 0; b < nrounds; ++b) {
+            const int q = b & 1;
+            cp_async_wait<1>();
+            bar_sync(kBarRaw, NF);                  // raw rows of round b are in
+            if (b >= 2) bar_sync(kBarEmpty + q, ALL);   // the FFT threads are done with u[q]
+            const TIn *in = reinterpret_cast<const TIn *>(inbuf + q * BUF_BYTES);
+            float2 *uq = u + q * NTR * ROW;
+#pragma unroll
+            for (int j = 0; j < kRound; ++j) {
+                win[(T - 1 + j) % T] = to_f2(in[j * NF + tid]);
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < T; ++k) acc = __ffma2_rn(h[k], win[(j + k) % T], acc);
+                uq[(j * IC + nl * kPols + p) * ROW + c] = acc;     // transform row j * IC + input
+            }
+            bar_arrive(kBarFull + q, ALL);
+            bar_sync(kBarRaw, NF);                  // every FIR thread has read raw buffer q
+            if (b + 2 < nrounds) stage(q, s0 + T - 1 + (b + 2) * kRound, kRound);
+            cp_async_commit();
+        }
+        cp_async_wait<0>();
+    } else {
+        // ---- FFT threads: task = (transform row, column); R lanes of one warp per row ----
+        const int t = tid - NF;
+        float2 twr[R];                              // W_C^(n2 k1) of this thread's column n2 = t mod R
+#pragma unroll
+        for (int k1 = 1; k1 < R; ++k1) twr[k1] = tw[(t % R) * k1];
+        float2 *obase = chan + ((long long)sb * N + n0) * kPols * S * C;
+        for (int b = 0; b < nrounds; ++b) {
+            const int q = b & 1;
+            float2 *uq = u + q * NTR * ROW;
+            bar_sync(kBarFull + q, ALL);            // FIR round b is in u[q]
+#pragma unroll
+            for (int it = 0; it < W::ITERS; ++it) {
+                const int task = it * NF + t;
+                const int tr = task / R, n2 = task % R;
+                float2 *row = uq + tr * ROW;
+                float2 v[R];
+                // pass 1: R-point FFT over n1 (stride R), times W_C^(n2 k1)
+#pragma unroll
+                for (int n1 = 0; n1 < R; ++n1) v[n1] = row[R * n1 + n2];
+                fft_reg<R>(v);
+#pragma unroll
+                for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], twr[k1]);
+                __syncwarp();                       // the row's R lanes have read it
+#pragma unroll
+                for (int k1 = 0; k1 < R; ++k1) row[(R + 1) * k1 + n2] = v[k1];
+                __syncwarp();
+                // pass 2: R-point FFT over n2 of row k1 = this lane's column, X[k1 + R k2]
+                const int k1 = n2;
+#pragma unroll
+                for (int m = 0; m < R; ++m) v[m] = row[(R + 1) * k1 + m];
+                if (it == W::ITERS - 1 && b + 2 < nrounds) bar_arrive(kBarEmpty + q, ALL);
+                fft_reg<R>(v);
+                const int j = tr / IC, il = tr % IC;
+                const int s = s0 + b * kRound + j;
+                if (s < S && n0 + il / kPols < N) {
+                    float2 *out = obase + ((long long)il * S + s) * C;
+#pragma unroll
+                    for (int k2 = 0; k2 < R; ++k2) out[k1 + R * ((k2 + R / 2) % R)] = v[k2];
+                }
+            }
+        }
+    }
+}
+
+template <int C, int T, typename TIn>
+cudaError_t launch_ws(const Handle &h, const void *raw, float2 *chan, cudaStream_t st)
+{
+    using W = PpfWsCfg<C>;
     const int N = h.p.n_stations, S = h.p.n_spectra, SB = h.p.n_subbands;
     const int rounds_total = (S + kRound - 1) / kRound;
-    const int sgroups = (N + Cfg::NPC - 1) / Cfg::NPC;
-    // long runs of rounds per CTA amortise the T-1 history rows each CTA reads
-    // and filters first; shorten them only while the grid would be under ~8 waves
-    int rpc = 32;
+    const int sgroups = (N + W::NPC - 1) / W::NPC;
+    // long runs amortise the T-1 history rows each CTA filters first; shorten
+    // them only while the grid would be under ~5 waves of three CTAs per SM
+    int rpc = 64;
     while (rpc > 1 && (long long)((rounds_total + rpc - 1) / rpc) * sgroups * SB < 152LL * 16) rpc /= 2;
     dim3 grid((rounds_total + rpc - 1) / rpc, sgroups, SB);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-    constexpr size_t smem =
-        ppf_smem_bytes<C, TIn>() + (ppf_split_u<C, TIn>() ? (size_t)Cfg::NTR * Cfg::ROW * sizeof(float2) : 0);
-    auto kern = ppf_kernel<C, T, TIn>;
+    constexpr size_t smem = ppf_ws_smem_bytes<C, TIn>();
+    auto kern = ppf_ws_kernel<C, T, TIn>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, Cfg::NT, smem, st>>>(reinterpret_cast<const TIn *>(raw), chan, h.d_taps, h.d_twiddle,
-                                      N, S, rpc);
+    kern<<<grid, 2 * W::NF, smem, st>>>(reinterpret_cast<const TIn *>(raw), chan, h.d_taps, h.d_twiddle, N, S, rpc);
     return cudaGetLastError();
+}
+
+template <int C, int T, typename TIn>
+cudaError_t launch_t(const Handle &h, const void *raw, float2 *chan, cudaStream_t st)
+{
+    if constexpr (C == 16 || C == 64) {
+        return launch_ws<C, T, TIn>(h, raw, chan, st);
+    } else {
+        // C = 256: one CTA of 512 FIR lanes alternating FIR and FFT
+        using Cfg = PpfCfg<C>;
+        const int N = h.p.n_stations, S = h.p.n_spectra, SB = h.p.n_subbands;
+        const int rounds_total = (S + kRound - 1) / kRound;
+        const int sgroups = (N + Cfg::NPC - 1) / Cfg::NPC;
+        // long runs of rounds per CTA amortise the T-1 history rows each CTA reads
+        // and filters first; shorten them only while the grid would be under ~8 waves
+        int rpc = 32;
+        while (rpc > 1 && (long long)((rounds_total + rpc - 1) / rpc) * sgroups * SB < 152LL * 16) rpc /= 2;
+        dim3 grid((rounds_total + rpc - 1) / rpc, sgroups, SB);
+        if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+        constexpr size_t smem =
+            ppf_smem_bytes<C, TIn>() + (ppf_split_u<C, TIn>() ? (size_t)Cfg::NTR * Cfg::ROW * sizeof(float2) : 0);
+        auto kern = ppf_kernel<C, T, TIn>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, Cfg::NT, smem, st>>>(reinterpret_cast<const TIn *>(raw), chan, h.d_taps, h.d_twiddle,
+                                          N, S, rpc);
+        return cudaGetLastError();
+    }
 }
 
 template <int C, typename TIn>

@@ -77,6 +77,34 @@ def test_channelize_parity(fmt, SB, N, C, T, S):
     assert np.max(np.abs(got - ref)) < 2e-5 * scale * np.sqrt(C)
 
 
+@pytest.mark.parametrize("fmt,SB,N,C,T,S,stations", [
+    # sizes whose grid keeps 4 rounds per CTA (ragged last round): the FIR/FFT
+    # buffer ping-pong of the warp-specialised PPF runs past its first reuse
+    (synth.CI16, 2, 64, 64, 16, 1210, [0, 31, 63]),
+    (synth.CI8, 4, 64, 16, 8, 2430, [2, 3, 60]),
+    # the LOFAR 16-bit shape on 13 subbands: 64 rounds per CTA as in the benchmark
+    (synth.CI16, 13, 64, 64, 16, 3072, [5, 62]),
+])
+def test_channelize_multiround(fmt, SB, N, C, T, S, stations):
+    """Long CTA runs of the PPF against the oracle on a few stations (the
+    channeliser treats stations independently, so the oracle runs on those
+    stations' samples alone)."""
+    rng = np.random.default_rng(S + C)
+    amp = 60 if fmt == synth.CI8 else 300
+    dt = np.int8 if fmt == synth.CI8 else np.int16
+    raw = rng.integers(-amp, amp + 1, size=(SB, N, (S + T - 1) * C, 2, 2), dtype=dt)
+    taps = synth.kaiser_sinc_taps(T, C)
+    fxg = fx()
+    c = fxg.Correlator(N, SB, C, S, taps=taps, centres=synth.subband_centres(SB), n_taps=T, fmt=fmt, precision=0)
+    sbs, st = torch.tensor([0, SB - 1]), torch.tensor(stations)
+    got = c.channelize(torch.from_numpy(raw).cuda())[sbs.cuda()][:, st.cuda()].cpu().numpy().astype(np.float64)
+    ref = oracle.channelize(fmt, raw[[0, SB - 1]][:, stations], T, C, S, taps)
+    assert got.shape == ref.shape
+    assert rel_err(got, ref) < 2e-6
+    assert np.max(np.abs(got - ref)) < 2e-5 * np.sqrt(np.mean(ref ** 2)) * np.sqrt(C)
+    c.close()
+
+
 @pytest.mark.parametrize("N,C,S,ramp", [(8, 64, 48, False), (5, 16, 70, True), (3, 256, 9, True)])
 def test_correct_f32_parity(N, C, S, ramp):
     rng = np.random.default_rng(7 + N)
