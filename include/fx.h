@@ -28,7 +28,14 @@
  * input index i = n*P + p, SB subbands, C channels, T taps, S spectra):
  *   raw   [SB][N][L][P]      complex int16, int8 or int4, L = (S + T - 1) * C samples
  *   chan  [SB][N][P][S][C]   complex float
- *   corr  FX_F32:            [SB][C][S][I] complex float
+ *   corr  FX_F32:            [SB][C][S16/16][N][16][P] complex float,
+ *                            S16 = S rounded up to 16 ("spectrum-blocked":
+ *                            sample (n, p) of spectrum s in channel k is at
+ *                            (((sb*C + k)*S16/16 + s/16)*N + n)*16*P
+ *                            + (s%16)*P + p; one channel's block is
+ *                            contiguous, and within it each station's 16
+ *                            spectra x 2 pols are one 256-byte run); spectra
+ *                            S .. S16-1 are written as zeros
  *         FX_F16, FX_BF16:   [SB][C][2][I_pad][S_pad] half / bfloat16,
  *                            plane 0 real parts, plane 1 imaginary parts
  *         FX_F16_SPLIT:      [SB][C][4][I_pad][S_pad] half, planes hi.re,
@@ -417,7 +424,7 @@ fx_status fx_poll_status(fx_handle *h, int *code);
  * Arguments as for fx_correct with an FX_F32 handle: d_subband_centre_hz [SB]
  * double (device), d_delay_begin/d_delay_end [N] double seconds (device),
  * d_bandpass [N][C] float or NULL, d_gains [N][P] complex float or NULL,
- * d_chan the chan layout, d_corr the FP32 corr layout [SB][C][S][I]. Pols = 2,
+ * d_chan the chan layout, d_corr the FP32 (spectrum-blocked) corr layout. Pols = 2,
  * channels in {16, 64, 256}. */
 #define FX_NOALLOC_MAX_PHASES (1u << 20)
 fx_status fx_correct_f32_noalloc(int n_stations, int n_subbands, int n_channels, int n_spectra,

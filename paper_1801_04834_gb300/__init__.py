@@ -7,4 +7,4 @@ offers a torch-tensor convenience layer (`Correlator`). PyTorch supplies
 device memory and streams."""
 from ._abi import (FX_BF16, FX_CI8, FX_CI16, FX_F16, FX_F16_SPLIT, FX_F32, FX_TF32_SPLIT, FxError,  # noqa: F401
                    load, last_error)
-from .api import Correlator  # noqa: F401
+from .api import Correlator, f32_block, f32_unblock  # noqa: F401

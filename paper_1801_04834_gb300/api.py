@@ -19,6 +19,34 @@ from ._abi import FX_CI4, FX_CI8, FX_CI16, FX_F16, FX_F16_SPLIT, FX_F32, FX_TF32
 SAMPLE_RATE_HZ = 195312.5
 
 
+def f32_unblock(corr, n_spectra: int):
+    """View of the FP32 corrected layout [SB][C][S16/16][N][16][2][2] (the
+    spectrum-blocked order the X-stage reads; torch tensor or numpy array) in
+    natural order [SB][C][S][N][2][2] (spectra S .. S16-1 dropped). A reshape,
+    no arithmetic."""
+    SB, C, NB, N = corr.shape[:4]
+    if isinstance(corr, torch.Tensor):
+        y = corr.permute(0, 1, 2, 4, 3, 5, 6).reshape(SB, C, NB * 16, N, 2, 2)
+    else:
+        y = np.ascontiguousarray(corr.transpose(0, 1, 2, 4, 3, 5, 6)).reshape(SB, C, NB * 16, N, 2, 2)
+    return y[:, :, :n_spectra]
+
+
+def f32_block(y):
+    """[SB][C][S][N][2][2] (natural order; torch tensor or numpy array) ->
+    the FP32 corrected layout [SB][C][S16/16][N][16][2][2], zero-padded to a
+    multiple of 16 spectra. A reshape, no arithmetic."""
+    SB, C, S, N = y.shape[:4]
+    S16 = (S + 15) // 16 * 16
+    if isinstance(y, torch.Tensor):
+        z = torch.zeros((SB, C, S16, N, 2, 2), dtype=y.dtype, device=y.device)
+        z[:, :, :S] = y
+        return z.reshape(SB, C, S16 // 16, 16, N, 2, 2).permute(0, 1, 2, 4, 3, 5, 6).contiguous()
+    z = np.zeros((SB, C, S16, N, 2, 2), dtype=y.dtype)
+    z[:, :, :S] = y
+    return np.ascontiguousarray(z.reshape(SB, C, S16 // 16, 16, N, 2, 2).transpose(0, 1, 2, 4, 3, 5, 6))
+
+
 def _stream_ptr(stream):
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
@@ -89,8 +117,8 @@ class Correlator:
         return (self.SB, self.N, 2, self.S, self.C, 2)
 
     def corr_shape(self):
-        if self.precision == FX_F32:
-            return (self.SB, self.C, self.S, self.N, 2, 2)
+        if self.precision == FX_F32:   # spectrum-blocked; f32_unblock gives [SB][C][S][N][2][2]
+            return (self.SB, self.C, (self.S + 15) // 16, self.N, 16, 2, 2)
         return (self.SB, self.C, self.planes, self.I_pad, self.S_pad)
 
     def corr_dtype(self):

@@ -447,7 +447,8 @@ __global__ void __launch_bounds__(kBfThreads, 1) beamform_kernel(const __grid_co
 // over tint consecutive spectra. No contraction, so CUDA cores: one thread per
 // spectrum (lanes = consecutive spectra, so each station's planes are read in
 // coalesced runs), stations accumulated in registers, tint lanes summed with
-// shuffles. SRC: 0 FP32 [SB][C][S][I], 1 FP16 planar, 2 BF16 planar,
+// shuffles. SRC: 0 FP32 spectrum-blocked [SB][C][ceil16(S)/16][N][16][2]
+// (16 lanes read one station's 256-byte run), 1 FP16 planar, 2 BF16 planar,
 // 3 FP32 planar ([SB][C][2][I_pad][S_pad]).
 template <int MODE, int SRC>
 __global__ void __launch_bounds__(128) incoherent_kernel(const void *__restrict__ corr, const float *__restrict__ weights,
@@ -463,8 +464,9 @@ __global__ void __launch_bounds__(128) incoherent_kernel(const void *__restrict_
             const float a = weights ? __ldg(weights + n) : 1.f;
             float xr, xj, yr, yj;
             if constexpr (SRC == 0) {
+                const long long NB = (S + 15) / 16;
                 const float4 v = *reinterpret_cast<const float4 *>(
-                    reinterpret_cast<const float2 *>(corr) + (gch * S + s) * (long long)(2 * N) + 2 * n);
+                    reinterpret_cast<const float2 *>(corr) + (((gch * NB + s / 16) * N + n) * 16 + s % 16) * 2);
                 xr = v.x; xj = v.y; yr = v.z; yj = v.w;
             } else if constexpr (SRC == 3) {
                 const float *re = reinterpret_cast<const float *>(corr) + gch * 2 * (long long)I_pad * S_pad;

@@ -23,10 +23,10 @@
 //
 // Transforms are stored spectrum-major (row j * IC + input), which keeps the
 // FIR stores and both FFT passes free of bank conflicts. Output:
-//   FP32   [SB][C][S][I]: written from the pass-2 registers; a warp store
-//          covers whole 32-byte runs of inputs of one (channel, spectrum);
-//          the grid walks station groups fastest so neighbouring CTAs fill
-//          the same lines while they are in L2;
+//   FP32   spectrum-blocked [SB][C][ceil16(S)/16][N][16][2]: for C = 16, 64
+//          by the warp-specialised ppf_correct_ws_kernel below (each warp
+//          store is one station's 16 spectra x 2 pols of a channel, 256
+//          contiguous bytes); for C = 256 from the pass-2 registers;
 //   planar [SB][C][planes][I_pad][S_pad]: turned in shared memory (reusing
 //          the FFT buffer) into per (channel, plane, input) runs of 16
 //          spectra (32 bytes), FP16/BF16 (x operand_scale) or hi/lo FP16.
@@ -238,18 +238,22 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
             }
         }
         if constexpr (OUT == 1) {
-            // ---- write out from registers: 2*NPC consecutive inputs per (channel, spectrum) ----
+            // ---- write out from registers into the spectrum-blocked FP32 layout
+            // [SB][C][S_pad/16][N][16][2] (zeros past s_end) ----
             float2 *out = reinterpret_cast<float2 *>(corr);
+            const int NB = S_pad / kRound;
 #pragma unroll
             for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
                 const int task = it * NT + tid;
                 const int tr = task / R, k1 = task % R;
                 const int s = sr + tr / IC, i = 2 * n0 + tr % IC;
-                if (s < s_end && i < I) {
+                if (i < I) {
+                    const int so = s - s_base;
 #pragma unroll
                     for (int k2 = 0; k2 < R; ++k2) {
                         const int kout = k1 + R * ((k2 + R / 2) % R);
-                        out[(((long long)sb * C + kout) * S_pad + (s - s_base)) * I + i] = y[it][k2];
+                        out[((((long long)sb * C + kout) * NB + so / kRound) * N + (i >> 1)) * (2 * kRound) +
+                            (so % kRound) * 2 + (i & 1)] = s < s_end ? y[it][k2] : make_float2(0.f, 0.f);
                     }
                 }
             }
@@ -341,6 +345,297 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
     cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised fused kernel, FP32 output (C = 16, 64). As ppf_ws_kernel:
+// 128 FIR threads (NPC = 64 / C stations) and 128 FFT threads per CTA, FIR
+// round b -> rows u[b & 1] -> FULL[b & 1]; FFT round b -> EMPTY[b & 1] for FIR
+// round b + 2. Three further choices keep the shared-memory/L1 pipe (which
+// also carries the global stores) below saturation:
+//  * rows are input-major (row = input * 16 + spectrum, each input's 16 rows
+//    offset by 8 entries so the FIR stores of the two pols use different banks);
+//    pass 1 (R lanes per row, as in ppf_ws_kernel) writes its results
+//    transposed, P1[k1][n2][row] with row stride NTR + 16/R (conflict free),
+//    over u[b & 1] once every FFT thread has read its rows (barrier FFT);
+//  * pass 2 runs with lane = row: a warp takes (group of 32 rows, k1) items,
+//    so each output store of a warp is one station's 16 spectra x 2 pols of
+//    one channel, 256 contiguous bytes of the spectrum-blocked layout;
+//  * the FIR threads, which have the lighter share of the work, tabulate
+//    exp(i phi) x flag per (station, channel, spectrum) of their round into a
+//    double-buffered table; the FFT threads multiply in bandpass x gain (a
+//    per-CTA table) and the phase factor.
+template <int C>
+struct FusedWsCfg {
+    static constexpr int R = PpfCfg<C>::R;
+    static constexpr int NPC = 64 / C;
+    static constexpr int NF = NPC * C * kPols;           // 128 FIR threads, 128 FFT threads
+    static constexpr int IC = NPC * kPols;               // inputs of a CTA
+    static constexpr int NTR = IC * kRound;              // rows per round
+    static constexpr int ROW = PpfCfg<C>::ROW;
+    static constexpr int PADG = 8;                       // float2 offset per input (16 rows)
+    static constexpr int USZ = NTR * ROW + IC * PADG;    // one row buffer
+    static constexpr int RS = NTR + 16 / R;              // P1 row stride
+    static constexpr int EJ = kRound + 1;                // phase table: 16 spectra + pad
+    static constexpr int ESZ = NPC * C * EJ;             // one phase-table buffer
+    static constexpr int ITEMS = (NTR / 32) * R;         // pass-2 items (row group, k1)
+    static_assert(C == 16 || C == 64, "warp-specialised fused kernel: C = 16 or 64");
+    static_assert(R * R * RS <= USZ, "P1 fits over the row buffer");
+    static_assert(ITEMS % 4 == 0 && NTR % 32 == 0, "four FFT warps share the pass-2 items");
+};
+
+template <int C, typename TIn>
+constexpr size_t fused_ws_smem_bytes()
+{
+    using W = FusedWsCfg<C>;
+    return (size_t)C * sizeof(float2) + 2ull * kRound * W::NPC * C * kPols * sizeof(TIn) +
+           (2ull * W::USZ + 2ull * W::ESZ + (size_t)W::IC * C) * sizeof(float2);
+}
+
+// CTAs per SM the shared memory allows: 3 at C = 64, 2 at C = 16 (four stations' rows)
+template <int C, typename TIn>
+constexpr int fused_ws_ctas()
+{
+    return 3 * (fused_ws_smem_bytes<C, TIn>() + 1024) <= 228 * 1024 ? 3 : 2;
+}
+
+enum { kFBarRaw = 1, kFBarFft = 2, kFBarFull = 3, kFBarEmpty = 5 };   // FULL/EMPTY use ids +0, +1
+
+__device__ __forceinline__ void fbar_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void fbar_arrive(int id, int n)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// OUT as ppf_correct_kernel: 1 FP32 spectrum-blocked, 2 FP16 / 3 BF16 / 4 split
+// FP16 / 5 FP32 planar ([SB][C][planes][I_pad][s_out], x scale for 2-4).
+template <int C, int T, typename TIn, int OUT>
+__global__ void __launch_bounds__(2 * FusedWsCfg<C>::NF, fused_ws_ctas<C, TIn>())
+ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const float *__restrict__ taps,
+                      const float2 *__restrict__ twiddle, const float2 *__restrict__ phase,
+                      const float *__restrict__ bandpass, const float2 *__restrict__ gains, int N, int S, int I_pad,
+                      int s_out, float scale, int rounds_per_cta, const float *__restrict__ flags, int s_base,
+                      int s_end)
+{
+    using W = FusedWsCfg<C>;
+    constexpr int R = W::R, NPC = W::NPC, NF = W::NF, IC = W::IC, ROW = W::ROW, PADG = W::PADG, USZ = W::USZ;
+    constexpr int RS = W::RS, EJ = W::EJ, ESZ = W::ESZ;
+    constexpr int ROW_BYTES = C * kPols * (int)sizeof(TIn);
+    constexpr int BUF_BYTES = kRound * NPC * ROW_BYTES;
+    constexpr int ALL = 2 * NF;
+    static_assert(ROW_BYTES % 16 == 0, "rows must be whole 16-byte chunks");
+    static_assert(2 * (fused_ws_smem_bytes<C, TIn>() + 1024) <= 228 * 1024, "at least two CTAs per SM");
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2 *tw = reinterpret_cast<float2 *>(smem);
+    unsigned char *inbuf = smem + C * sizeof(float2);
+    float2 *u = reinterpret_cast<float2 *>(inbuf + 2 * BUF_BYTES);   // [2][USZ]
+    float2 *et = u + 2 * USZ;                                         // [2][NPC][C][EJ]
+    float2 *bgt = et + 2 * ESZ;                                       // [IC][C] bandpass x gain
+
+    const int tid = threadIdx.x;
+    const int sb = blockIdx.z;
+    const int n0 = blockIdx.x * NPC;                // station groups fastest
+    const int s0 = s_base + blockIdx.y * rounds_per_cta * kRound;
+    const int rows_total = S + T - 1;
+    const long long L = (long long)rows_total * C;
+    const int nrounds = min(rounds_per_cta, (s_end - s0 + kRound - 1) / kRound);
+    auto rowp = [&](float2 *uq, int r) { return uq + r * ROW + (r / kRound) * PADG; };
+
+    for (int i = tid; i < C; i += ALL) tw[i] = twiddle[i];
+    for (int e = tid; e < IC * C; e += ALL) {
+        const int il = e / C, k = e % C;
+        const int n = min(n0 + il / kPols, N - 1);
+        const float b = bandpass ? bandpass[(long long)n * C + k] : 1.f;
+        const float2 g = gains ? gains[n * kPols + il % kPols] : make_float2(1.f, 0.f);
+        bgt[e] = make_float2(b * g.x * scale, b * g.y * scale);
+    }
+    __syncthreads();
+
+    if (tid < NF) {
+        // ---------------- FIR threads: (station nl, channel c, pol p) ----------------
+        auto stage = [&](int buf, int r0, int nrows) {
+            const int chunks = nrows * ROW_BYTES / 16;
+            for (int q = tid; q < NPC * chunks; q += NF) {
+                const int st = q / chunks, ch = q - st * chunks;
+                const int n = n0 + st;
+                const int row_in = (ch * 16) / ROW_BYTES;
+                const int byte_in_row = (ch * 16) - row_in * ROW_BYTES;
+                unsigned char *dst = inbuf + buf * BUF_BYTES + (row_in * NPC + st) * ROW_BYTES + byte_in_row;
+                const bool ok = (n < N) && (r0 + row_in < rows_total);
+                const unsigned char *src = reinterpret_cast<const unsigned char *>(raw);
+                if (ok) src += ((((long long)sb * N + n) * L + (long long)r0 * C) * kPols) * sizeof(TIn) + ch * 16;
+                cp_async16(dst, src, ok ? 16 : 0);
+            }
+        };
+        const int p = tid % kPols;
+        const int c = (tid / kPols) % C;
+        const int nl = tid / (kPols * C);
+        // phase-table role: (station, channel) = tid mod NPC*C, spectra j0, j0 + 2, ...
+        constexpr int OWN = NPC * C;                // = NF / 2
+        const int own_nc = tid % OWN, own_j0 = tid / OWN;
+        const int own_n = min(n0 + own_nc / C, N - 1);
+        const float2 pst = phase[((long long)sb * N + own_n) * C + own_nc % C];   // (phi0, step)
+        float2 h[T];
+#pragma unroll
+        for (int k = 0; k < T; ++k) h[k] = make_float2(taps[k * C + c], taps[k * C + c]);
+
+        stage(1, s0, T - 1);
+        cp_async_commit();
+        stage(0, s0 + T - 1, kRound);
+        cp_async_commit();
+        cp_async_wait<1>();
+        fbar_sync(kFBarRaw, NF);
+        float2 win[T];
+        const TIn *in1 = reinterpret_cast<const TIn *>(inbuf + BUF_BYTES);
+#pragma unroll
+        for (int k = 0; k < T - 1; ++k) win[k] = to_f2(in1[k * NF + tid]);
+        win[T - 1] = make_float2(0.f, 0.f);
+        fbar_sync(kFBarRaw, NF);
+        if (nrounds > 1) stage(1, s0 + T - 1 + kRound, kRound);
+        cp_async_commit();
+
+        for (int b = 0; b < nrounds; ++b) {
+            const int q = b & 1;
+            const int sr = s0 + b * kRound;
+            cp_async_wait<1>();
+            fbar_sync(kFBarRaw, NF);                // raw rows of round b are in
+            if (b >= 2) fbar_sync(kFBarEmpty + q, ALL);   // FFT threads are done with u[q], et[q]
+            const TIn *in = reinterpret_cast<const TIn *>(inbuf + q * BUF_BYTES);
+            float2 *uq = u + q * USZ;
+            float2 *fo = rowp(uq, (nl * kPols + p) * kRound) + c;
+#pragma unroll
+            for (int j = 0; j < kRound; ++j) {
+                win[(T - 1 + j) % T] = to_f2(in[j * NF + tid]);
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < T; ++k) acc = __ffma2_rn(h[k], win[(j + k) % T], acc);
+                fo[j * ROW] = acc;                  // row (input, spectrum j)
+            }
+            // exp(i phi) x flag of this round: phi = phi0 + s step reduced to
+            // [-pi, pi] (two-constant Cody-Waite split of 2 pi), then __sincosf
+            float2 *eq = et + q * ESZ + own_nc * EJ;
+#pragma unroll
+            for (int qq = 0; qq < kRound / 2; ++qq) {
+                const int j = own_j0 + 2 * qq;
+                const float phi = fmaf((float)(sr + j), pst.y, pst.x);
+                const float kq = rintf(phi * 0.15915494309189535f);
+                float r = fmaf(-kq, 6.28125f, phi);
+                r = fmaf(-kq, 1.9353071795864769e-3f, r);
+                float sn, cs;
+                __sincosf(r, &sn, &cs);
+                const float fw = flags ? flags[(long long)own_n * S + min(sr + j, S - 1)] : 1.f;
+                eq[j] = make_float2(cs * fw, sn * fw);
+            }
+            fbar_arrive(kFBarFull + q, ALL);
+            fbar_sync(kFBarRaw, NF);                // every FIR thread has read raw buffer q
+            if (b + 2 < nrounds) stage(q, s0 + T - 1 + (b + 2) * kRound, kRound);
+            cp_async_commit();
+        }
+        cp_async_wait<0>();
+    } else {
+        // ---------------- FFT threads ----------------
+        const int t = tid - NF;
+        const int warp = t / 32, lane = t % 32;
+        float2 twr[R];                              // W_C^(n2 k1), n2 = t mod R
+#pragma unroll
+        for (int k1 = 1; k1 < R; ++k1) twr[k1] = tw[(t % R) * k1];
+        const int NB = s_out / kRound;
+        const int I = N * kPols;
+        constexpr int P1ITERS = W::NTR * R / NF;
+        for (int b = 0; b < nrounds; ++b) {
+            const int q = b & 1;
+            const int sr = s0 + b * kRound;
+            float2 *uq = u + q * USZ;
+            const float2 *eq = et + q * ESZ;
+            fbar_sync(kFBarFull + q, ALL);          // FIR round b is in u[q], et[q]
+            // pass 1: R-point FFTs over n1 (stride R), times W_C^(n2 k1)
+            float2 v1[P1ITERS][R];
+#pragma unroll
+            for (int it = 0; it < P1ITERS; ++it) {
+                const int task = it * NF + t;
+                const float2 *row = rowp(uq, task / R);
+#pragma unroll
+                for (int n1 = 0; n1 < R; ++n1) v1[it][n1] = row[R * n1 + task % R];
+                fft_reg<R>(v1[it]);
+#pragma unroll
+                for (int k1 = 1; k1 < R; ++k1) v1[it][k1] = cmul(v1[it][k1], twr[k1]);
+            }
+            fbar_sync(kFBarFft, NF);                // every FFT thread has read its rows of u[q]
+#pragma unroll
+            for (int it = 0; it < P1ITERS; ++it) {
+                const int task = it * NF + t;
+#pragma unroll
+                for (int k1 = 0; k1 < R; ++k1) uq[(k1 * R + task % R) * RS + task / R] = v1[it][k1];
+            }
+            fbar_sync(kFBarFft, NF);                // P1 complete
+            // pass 2: lane = row (input il, spectrum j), item = (row group, k1)
+#pragma unroll
+            for (int it = 0; it < W::ITEMS / 4; ++it) {
+                const int item = warp + 4 * it;
+                const int g = item / R, k1 = item % R;
+                const int r = 32 * g + lane;
+                const int il = r / kRound, j = r % kRound;
+                float2 v[R];
+#pragma unroll
+                for (int m = 0; m < R; ++m) v[m] = uq[(k1 * R + m) * RS + r];
+                fft_reg<R>(v);
+                const float2 *bg = bgt + il * C;
+                const float2 *e = eq + ((il / kPols) * C) * EJ + j;
+#pragma unroll
+                for (int k2 = 0; k2 < R; ++k2) {
+                    const int kout = k1 + R * ((k2 + R / 2) % R);
+                    v[k2] = cmul(v[k2], cmul(bg[kout], e[kout * EJ]));
+                }
+                if (it == W::ITEMS / 4 - 1 && b + 2 < nrounds) fbar_arrive(kFBarEmpty + q, ALL);
+                const int s = sr + j, i = 2 * n0 + il;
+                if (i < I) {
+                    if constexpr (OUT == 1) {
+                        // one warp store = one station's 16 spectra x 2 pols of a channel (256 B)
+                        float2 *out = reinterpret_cast<float2 *>(corr) +
+                                      ((((long long)sb * C) * NB + (sr - s_base) / kRound) * N + (i >> 1)) *
+                                          (2 * kRound) + j * 2 + (i & 1);
+                        const long long kstride = (long long)NB * N * (2 * kRound);
+#pragma unroll
+                        for (int k2 = 0; k2 < R; ++k2) {
+                            const int kout = k1 + R * ((k2 + R / 2) % R);
+                            out[kout * kstride] = s < s_end ? v[k2] : make_float2(0.f, 0.f);
+                        }
+                    } else {
+                        // planar: one warp store = 2 inputs x 16 spectra of one (channel, plane)
+                        constexpr int planes = OUT == 4 ? 4 : 2;
+                        const long long pstride = (long long)I_pad * s_out;
+                        const long long base = (long long)sb * C * planes * pstride + (long long)i * s_out + (s - s_base);
+#pragma unroll
+                        for (int k2 = 0; k2 < R; ++k2) {
+                            const int kout = k1 + R * ((k2 + R / 2) % R);
+                            const float2 y = s < s_end ? v[k2] : make_float2(0.f, 0.f);
+                            const long long o = base + (long long)kout * planes * pstride;
+                            if constexpr (OUT == 5) {
+                                float *out = reinterpret_cast<float *>(corr);
+                                out[o] = y.x;
+                                out[o + pstride] = y.y;
+                            } else {
+                                unsigned short *out = reinterpret_cast<unsigned short *>(corr);
+                                const unsigned short hr = to_bits(y.x, OUT), hi = to_bits(y.y, OUT);
+                                out[o] = hr;
+                                out[o + pstride] = hi;
+                                if constexpr (OUT == 4) {
+                                    out[o + 2 * pstride] =
+                                        __half_as_ushort(__float2half_rn(y.x - __half2float(__ushort_as_half(hr))));
+                                    out[o + 3 * pstride] =
+                                        __half_as_ushort(__float2half_rn(y.y - __half2float(__ushort_as_half(hi))));
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
 // Zero the padding of the planar layout that the fused kernel does not cover:
 // inputs [I, I_pad) and spectra [ceil16(S), S_pad) of every (subband, channel, plane).
 __global__ void planar_pad_kernel(unsigned short *__restrict__ corr, long long n_rows, int I, int I_pad, int S16,
@@ -354,6 +649,20 @@ __global__ void planar_pad_kernel(unsigned short *__restrict__ corr, long long n
     for (int s = from + threadIdx.x; s < S_pad; s += blockDim.x) r[s] = 0;
 }
 
+// Zeros of the planar layout outside what the F-stage wrote: inputs [I, I_pad)
+// and spectra [S16, s_out) of every (subband, channel, plane).
+cudaError_t planar_pad(const Handle &h, void *corr, int out, int S16, int s_out, cudaStream_t st)
+{
+    if (h.I_pad <= h.I && s_out <= S16) return cudaSuccess;
+    const long long rows = (long long)h.p.n_subbands * h.p.n_channels * (out == 4 ? 4 : 2) * h.I_pad;
+    if (rows > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    // zero bits are zero in either element size: FP32 rows are twice as many 16-bit words
+    const int w = out == 5 ? 2 : 1;
+    planar_pad_kernel<<<(unsigned)rows, 64, 0, st>>>(reinterpret_cast<unsigned short *>(corr), rows, h.I, h.I_pad,
+                                                      w * S16, w * s_out);
+    return cudaGetLastError();
+}
+
 template <int C, int T, typename TIn, int OUT>
 cudaError_t launch_t(const Handle &h, const void *raw, void *corr, const float *bandpass, const float2 *gains,
                      const float *flags, const FWindow *win, cudaStream_t st)
@@ -363,37 +672,50 @@ cudaError_t launch_t(const Handle &h, const void *raw, void *corr, const float *
     // spectra [s_base, s_end) into an output whose spectrum stride is s_out
     const int s_base = win ? win->s_base : 0;
     const int s_end = win ? win->s_end : S;
-    const int s_out = win ? win->s_out : (OUT == 1 ? S : h.S_pad);
-    if (s_base % kRound != 0 || s_end > S || s_base >= s_end || s_end - s_base > s_out)
+    // FP32: the spectrum-blocked layout, s_out a multiple of 16 (ceil16(S) by default)
+    const int s_out = win ? win->s_out : (OUT == 1 ? (S + kRound - 1) / kRound * kRound : h.S_pad);
+    if (s_base % kRound != 0 || s_end > S || s_base >= s_end || s_end - s_base > s_out ||
+        (OUT == 1 && s_out % kRound != 0))
         return cudaErrorInvalidValue;
     const int rounds_total = (s_end - s_base + kRound - 1) / kRound;
-    const int sgroups = (N + Cfg::NPC - 1) / Cfg::NPC;
-    // long runs of rounds per CTA amortise the T-1 history rows each CTA reads
-    // and filters first; shorten them only while the grid would be under ~8 waves
-    int rpc = 32;
-    while (rpc > 1 && (long long)((rounds_total + rpc - 1) / rpc) * sgroups * SB < 152LL * 16) rpc /= 2;
-    dim3 grid(sgroups, (rounds_total + rpc - 1) / rpc, SB);
-    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-    constexpr size_t smem = fused_smem_bytes<C, TIn>();
-    auto kern = ppf_correct_kernel<C, T, TIn, OUT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const float scale = (OUT == 1 || OUT == 5) ? 1.f : h.operand_scale;
-    kern<<<grid, Cfg::NT, smem, st>>>(reinterpret_cast<const TIn *>(raw), corr, h.d_taps, h.d_twiddle, h.d_phase,
-                                      bandpass, gains, N, S, h.I_pad, s_out, scale, rpc, flags, s_base, s_end);
-    e = cudaGetLastError();
-    if (e != cudaSuccess || OUT == 1) return e;
-    const int S16 = rounds_total * kRound;
-    if (h.I_pad > h.I || s_out > S16) {
-        const long long rows = (long long)SB * C * (OUT == 4 ? 4 : 2) * h.I_pad;
-        if (rows > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-        // zero bits are zero in either element size: FP32 rows are twice as many 16-bit words
-        const int w = OUT == 5 ? 2 : 1;
-        planar_pad_kernel<<<(unsigned)rows, 64, 0, st>>>(reinterpret_cast<unsigned short *>(corr), rows, h.I, h.I_pad,
-                                                          w * S16, w * s_out);
+    if constexpr (C == 16 || C == 64) {
+        using W = FusedWsCfg<C>;
+        const int sg = (N + W::NPC - 1) / W::NPC;
+        // long runs amortise the T-1 history rows each CTA filters first; shorten
+        // them only while the grid would be under ~5 waves
+        int rpc = 64;
+        while (rpc > 1 && (long long)((rounds_total + rpc - 1) / rpc) * sg * SB < 152LL * 16) rpc /= 2;
+        dim3 grid(sg, (rounds_total + rpc - 1) / rpc, SB);
+        if (grid.x > 0x7fffffffu || grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+        constexpr size_t smem = fused_ws_smem_bytes<C, TIn>();
+        auto kern = ppf_correct_ws_kernel<C, T, TIn, OUT>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, 2 * W::NF, smem, st>>>(reinterpret_cast<const TIn *>(raw), corr, h.d_taps, h.d_twiddle,
+                                            h.d_phase, bandpass, gains, N, S, h.I_pad, s_out, scale, rpc, flags,
+                                            s_base, s_end);
         e = cudaGetLastError();
+        if (e != cudaSuccess || OUT == 1) return e;
+        return planar_pad(h, corr, OUT, rounds_total * kRound, s_out, st);
+    } else {
+        const int sgroups = (N + Cfg::NPC - 1) / Cfg::NPC;
+        // long runs of rounds per CTA amortise the T-1 history rows each CTA reads
+        // and filters first; shorten them only while the grid would be under ~8 waves
+        int rpc = 32;
+        while (rpc > 1 && (long long)((rounds_total + rpc - 1) / rpc) * sgroups * SB < 152LL * 16) rpc /= 2;
+        dim3 grid(sgroups, (rounds_total + rpc - 1) / rpc, SB);
+        if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+        constexpr size_t smem = fused_smem_bytes<C, TIn>();
+        auto kern = ppf_correct_kernel<C, T, TIn, OUT>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, Cfg::NT, smem, st>>>(reinterpret_cast<const TIn *>(raw), corr, h.d_taps, h.d_twiddle, h.d_phase,
+                                          bandpass, gains, N, S, h.I_pad, s_out, scale, rpc, flags, s_base, s_end);
+        e = cudaGetLastError();
+        if (e != cudaSuccess || OUT == 1) return e;
+        return planar_pad(h, corr, OUT, rounds_total * kRound, s_out, st);
     }
-    return e;
 }
 
 template <int C, int T, typename TIn>

@@ -53,39 +53,55 @@ __device__ __forceinline__ float2 correct_one(float2 x, float2 ph, int s, float 
     return make_float2(bp * fmaf(xg.x, cs, -xg.y * sn), bp * fmaf(xg.x, sn, xg.y * cs));
 }
 
-// ---- FP32 output [SB][C][S][I] -----------------------------------------
-// CTA = (subband, spectrum s, block of CB channels), all I inputs. Reads are
-// CB-channel runs of one (station, pol, spectrum); writes are I-input runs of
-// one (channel, spectrum); the tile turns the corner in shared memory.
-constexpr int kCB = 32;
+// ---- FP32 output, spectrum-blocked [SB][C][ceil16(S)/16][N][16][2] ---------
+// CTA = (subband, station, block of 16 spectra), all C channels. Reads are
+// C-channel runs of one (pol, spectrum); writes are 256-byte runs (16 spectra
+// x 2 pols) of one channel; the tile [C][32 + 1] turns the corner in shared
+// memory. Spectra S .. ceil16(S) - 1 are written as zeros.
 constexpr int kNT = 256;
+constexpr int kBS = 16;                  // spectra per block of the FP32 layout
 
 __global__ void __launch_bounds__(kNT)
 correct_f32_kernel(const float2 *__restrict__ chan, const float2 *__restrict__ table,
                    const float *__restrict__ bandpass, const float2 *__restrict__ gains,
                    float2 *__restrict__ corr, int N, int C, int S)
 {
-    extern __shared__ float2 tile[];   // [CB][I + 1]
-    const int I = N * kPols;
-    const int s = blockIdx.x;
-    const int c0 = blockIdx.y * kCB;
-    const int sb = blockIdx.z;
-    const int cb = min(kCB, C - c0);
-    for (int e = threadIdx.x; e < I * cb; e += kNT) {
-        const int c = e % cb, i = e / cb;
-        const int n = i / kPols, p = i % kPols;
-        const int k = c0 + c;
-        const float2 x = chan[((((long long)sb * N + n) * kPols + p) * S + s) * C + k];
-        const float2 ph = table[((long long)sb * N + n) * C + k];
-        const float bp = bandpass ? bandpass[(long long)n * C + k] : 1.f;
-        const float2 g = gains ? gains[i] : make_float2(1.f, 0.f);
-        tile[c * (I + 1) + i] = correct_one(x, ph, s, bp, g);
+    extern __shared__ float2 tile[];     // [C][2 * kBS + 1]
+    constexpr int TW = 2 * kBS + 1;
+    const int blk = blockIdx.x, n = blockIdx.y, sb = blockIdx.z;
+    const int NB = gridDim.x;
+    const float2 *tb = table + ((long long)sb * N + n) * C;
+    for (int e = threadIdx.x; e < kPols * kBS * C; e += kNT) {
+        const int k = e % C, j = (e / C) % kBS, p = e / (C * kBS);
+        const int s = blk * kBS + j;
+        float2 y = make_float2(0.f, 0.f);
+        if (s < S) {
+            const float2 x = chan[((((long long)sb * N + n) * kPols + p) * S + s) * C + k];
+            const float bp = bandpass ? bandpass[(long long)n * C + k] : 1.f;
+            const float2 g = gains ? gains[n * kPols + p] : make_float2(1.f, 0.f);
+            y = correct_one(x, tb[k], s, bp, g);
+        }
+        tile[k * TW + j * kPols + p] = y;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < I * cb; e += kNT) {
-        const int i = e % I, c = e / I;
-        corr[(((long long)sb * C + c0 + c) * S + s) * I + i] = tile[c * (I + 1) + i];
+    float2 *out = corr + (((long long)sb * C * NB + blk) * N + n) * (2 * kBS);
+    const long long kstride = (long long)NB * N * (2 * kBS);
+    for (int e = threadIdx.x; e < C * 2 * kBS; e += kNT) {
+        const int jp = e % (2 * kBS), k = e / (2 * kBS);
+        out[k * kstride + jp] = tile[k * TW + jp];
     }
+}
+
+static cudaError_t launch_correct_f32(const float2 *chan, const float2 *table, const float *bandpass,
+                                      const float2 *gains, float2 *corr, int SB, int N, int C, int S, cudaStream_t st)
+{
+    const size_t smem = (size_t)C * (2 * kBS + 1) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(correct_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((S + kBS - 1) / kBS, N, SB);
+    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+    correct_f32_kernel<<<grid, kNT, smem, st>>>(chan, table, bandpass, gains, corr, N, C, S);
+    return cudaGetLastError();
 }
 
 // ---- planar 16-bit output [SB][C][planes][I_pad][S_pad] -----------------
@@ -238,30 +254,16 @@ cudaError_t launch_correct_f32_noalloc(int N, int SB, int C, int S, double fs, c
                                                                     fs);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = sizeof(float2) * kCB * (2 * N + 1);
-    e = cudaFuncSetAttribute(correct_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid(S, (C + kCB - 1) / kCB, SB);
-    correct_f32_kernel<<<grid, kNT, smem, st>>>(chan, table, bandpass, gains, corr, N, C, S);
-    return cudaGetLastError();
+    return launch_correct_f32(chan, table, bandpass, gains, corr, SB, N, C, S, st);
 }
 
 cudaError_t launch_correct(const Handle &h, const float2 *chan, const float *bandpass,
                            const float2 *gains, void *corr, cudaStream_t st)
 {
     const int N = h.p.n_stations, C = h.p.n_channels, S = h.p.n_spectra, SB = h.p.n_subbands;
-    if (h.p.precision == FX_F32) {
-        const size_t smem = sizeof(float2) * kCB * (h.I + 1);
-        if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-        cudaError_t e = cudaFuncSetAttribute(correct_f32_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        dim3 grid(S, (C + kCB - 1) / kCB, SB);
-        if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-        correct_f32_kernel<<<grid, kNT, smem, st>>>(chan, h.d_phase, bandpass, gains,
-                                                    reinterpret_cast<float2 *>(corr), N, C, S);
-        return cudaGetLastError();
-    }
+    if (h.p.precision == FX_F32)
+        return launch_correct_f32(chan, h.d_phase, bandpass, gains, reinterpret_cast<float2 *>(corr), SB, N, C, S,
+                                  st);
     dim3 grid(h.S_pad / kPT_S, h.I_pad / kPT_I, SB * (C / kPT_C));
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
     switch (h.p.precision) {

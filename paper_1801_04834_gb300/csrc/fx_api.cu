@@ -232,7 +232,7 @@ extern "C" fx_status fx_query_sizes(const fx_handle *h, fx_sizes *o)
     o->raw_bytes = SB * N * L * 2 * bpc;
     o->chan_bytes = SB * N * 2 * S * C * sizeof(float2);
     switch (p.precision) {
-    case FX_F32: o->corr_bytes = SB * C * S * N * 2 * sizeof(float2); o->corr_planes = 0; break;
+    case FX_F32: o->corr_bytes = SB * C * ((S + 15) / 16 * 16) * N * 2 * sizeof(float2); o->corr_planes = 0; break;
     case FX_F16:
     case FX_BF16: o->corr_bytes = SB * C * 2 * (size_t)h->I_pad * h->S_pad * 2; o->corr_planes = 2; break;
     case FX_TF32_SPLIT: o->corr_bytes = SB * C * 2 * (size_t)h->I_pad * h->S_pad * 4; o->corr_planes = 2; break;

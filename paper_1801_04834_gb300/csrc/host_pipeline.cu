@@ -37,7 +37,7 @@ static size_t corr_bytes_per_subband(const Handle &h)
 {
     const size_t C = h.p.n_channels, S = h.p.n_spectra;
     switch (h.p.precision) {
-    case FX_F32: return C * S * h.I * sizeof(float2);
+    case FX_F32: return C * ((S + 15) / 16 * 16) * h.I * sizeof(float2);   // spectrum-blocked, ceil16(S)
     case FX_F16:
     case FX_BF16: return C * 2 * (size_t)h.I_pad * h.S_pad * 2;
     case FX_TF32_SPLIT: return C * 2 * (size_t)h.I_pad * h.S_pad * 4;

@@ -7,8 +7,9 @@
 //
 //   V[sb][k][b(i,j)][2p+q] = sum_s Y[s][i,p] * conj(Y[s][j,q]),  i <= j
 //
-// Input is the FP32 corrected layout [SB][C][S][I] (I = 2N interleaved complex),
-// so one channel's block is one contiguous [S][I] matrix.
+// Input is the FP32 corrected layout, spectrum-blocked:
+// [SB][C][ceil16(S)/16][N][16][2] complex (one channel's block is contiguous;
+// within it, 16 spectra x 2 pols of one station are one 256-byte run).
 //
 // Register tiling over the station triangle: a thread owns RS stations (rows,
 // 2 RS inputs) x 4 stations (columns, 8 inputs). RS = 2: 32 complex
@@ -23,7 +24,10 @@
 // CTA (16 warps, 4 per scheduler), so a CTA covers the tiles of one to a few
 // channels whatever the station count; it streams the time samples of every
 // channel it touches through shared memory in chunks of KC samples with
-// double-buffered cp.async. Within a time row the 16-byte station entries are
+// double-buffered cp.async (consecutive threads copy consecutive spectra of
+// one station, so each warp reads whole 256-byte runs; time rows are padded
+// by one 16-byte entry so those copies land on distinct banks). Within a time
+// row the 16-byte station entries are
 // grouped by station index: RS = 2 stores
 // [even stations][odd stations], RS = 4 stores [stations = 0 mod 4][1 mod 4]
 // [2 mod 4][3 mod 4], so the row loads of consecutive row tiles fall on
@@ -60,12 +64,13 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
                  const int2 *__restrict__ tiles, int ntiles, int N, int S, int IP, int max_ch,
                  long long total_ch, int accumulate)
 {
-    extern __shared__ float4 sm[];   // [2][max_ch][KC][IP/2] float4
-    const int I = 2 * N;
+    extern __shared__ float4 sm[];   // [2][max_ch][KC][IP/2 + 1] float4
     const int row4 = IP / 2;                       // float4 (= station entries) per time row
+    const int rowp = row4 + 1;                     // padded row stride
     const int half = IP / 4;                       // RS = 2: offset of the odd-station half
     const int quarter = IP / 8;                    // RS = 4: offset between the residue groups
-    const int stage_f4 = max_ch * kKC * row4;
+    const int stage_f4 = max_ch * kKC * rowp;
+    const int NB = (S + 15) / 16;                  // 16-spectrum blocks of the input layout
     const int tid = threadIdx.x;
     const long long g0 = (long long)blockIdx.x * blockDim.x;
     const long long ch_first = g0 / ntiles;
@@ -74,28 +79,33 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
     const int nch = (int)(ch_end - ch_first);
     const int nthr = blockDim.x;
 
-    // element v = (cl * KC + s) * row4 + x; the thread's first (x, cl*KC + s) is
-    // found once and advanced by nthr with a carry (no division per element)
-    const int x_first = tid % row4, r_first = tid / row4;
-    const int dx = nthr % row4, dr = nthr / row4;
+    // element v = (cl * row4 + x) * KC + s: the thread's sample s = tid mod KC is
+    // the same in every chunk (nthr is a multiple of KC); its first (x, cl) is
+    // found once and advanced by nthr / KC with a carry (no division per element)
+    const int s_l = tid % kKC;
+    const int e_first = tid / kKC, de = nthr / kKC;
+    const int x_first = e_first % row4, c_first = e_first / row4;
+    const int dx = de % row4, dc = de / row4;
     auto load_chunk = [&](int stage, int s0) {
         float4 *dst0 = sm + stage * stage_f4;
-        const int total = nch * kKC * row4;
-        int x = x_first, rr = r_first;
-        for (int v = tid; v < total; v += nthr) {
-            const int s = rr % kKC, cl = rr / kKC;      // kKC is a power of two
+        const int total = nch * row4;
+        const int sa = s0 + s_l;
+        const bool s_ok = sa < S;
+        const long long run = (long long)(sa >> 4) * N;  // block of this sample
+        int x = x_first, cl = c_first;
+        for (int e = e_first; e < total; e += de) {
             const long long gch = ch_first + cl;
-            const bool ok = (2 * x < I) && (s0 + s < S);
+            const bool ok = s_ok && (x < N);
             const float2 *src = corr;
-            if (ok) src = corr + (gch * S + s0 + s) * (long long)I + 2 * x;
+            if (ok) src = corr + ((gch * NB * N + run + x) * 16 + (sa & 15)) * 2;
             const int xs = RS == 4 ? (x & 3) * quarter + (x >> 2)    // [0 mod 4][1][2][3]
                                    : (x & 1) * half + (x >> 1);      // [even stations][odd stations]
-            cp_async16(dst0 + rr * row4 + xs, src, ok ? 16 : 0);
+            cp_async16(dst0 + (cl * kKC + s_l) * rowp + xs, src, ok ? 16 : 0);
             x += dx;
-            rr += dr;
+            cl += dc;
             if (x >= row4) {
                 x -= row4;
-                ++rr;
+                ++cl;
             }
         }
     };
@@ -138,22 +148,22 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
         cp_async_wait<1>();
         __syncthreads();
         if (active) {
-            const float4 *base = sm + (kc & 1) * stage_f4 + cl * kKC * row4;
+            const float4 *base = sm + (kc & 1) * stage_f4 + cl * kKC * rowp;
 #pragma unroll 2
             for (int s = 0; s < kKC; ++s) {
-                const float4 *rowp = base + s * row4;
+                const float4 *row = base + s * rowp;
                 float2 xv[RA];
                 if constexpr (RS == 2) {
                     // row stations 2r (even half) and 2r+1 (odd half)
-                    const float4 x0 = rowp[r], x1 = rowp[half + r];
+                    const float4 x0 = row[r], x1 = row[half + r];
                     xv[0] = make_float2(x0.x, x0.y);
                     xv[1] = make_float2(x0.z, x0.w);
                     xv[2] = make_float2(x1.x, x1.y);
                     xv[3] = make_float2(x1.z, x1.w);
                 } else {
                     // row stations 4r .. 4r+3
-                    const float4 x0 = rowp[r], x1 = rowp[quarter + r], x2 = rowp[2 * quarter + r],
-                                 x3 = rowp[3 * quarter + r];
+                    const float4 x0 = row[r], x1 = row[quarter + r], x2 = row[2 * quarter + r],
+                                 x3 = row[3 * quarter + r];
                     xv[0] = make_float2(x0.x, x0.y);
                     xv[1] = make_float2(x0.z, x0.w);
                     xv[2] = make_float2(x1.x, x1.y);
@@ -166,15 +176,15 @@ xcorr_f32_kernel(const float2 *__restrict__ corr, float2 *__restrict__ vis,
                 // column stations 4q, 4q+1, 4q+2, 4q+3
                 float4 y0, y1, y2, y3;
                 if constexpr (RS == 2) {
-                    y0 = rowp[2 * q];
-                    y1 = rowp[half + 2 * q];
-                    y2 = rowp[2 * q + 1];
-                    y3 = rowp[half + 2 * q + 1];
+                    y0 = row[2 * q];
+                    y1 = row[half + 2 * q];
+                    y2 = row[2 * q + 1];
+                    y3 = row[half + 2 * q + 1];
                 } else {
-                    y0 = rowp[q];
-                    y1 = rowp[quarter + q];
-                    y2 = rowp[2 * quarter + q];
-                    y3 = rowp[3 * quarter + q];
+                    y0 = row[q];
+                    y1 = row[quarter + q];
+                    y2 = row[2 * quarter + q];
+                    y3 = row[3 * quarter + q];
                 }
                 if constexpr (G3) {
                     const float2 yv[8] = {make_float2(y0.x, y0.y), make_float2(y0.z, y0.w),
@@ -266,7 +276,7 @@ int xf32_build_tiles(int N, int RS, int2 *out)
 bool xf32_geometry(int N, long long total_ch, int ntiles, int kc, int mode, int *threads, int *max_ch)
 {
     const int IP = 8 * ((N + 3) / 4);
-    const size_t row_bytes = (size_t)kc * IP * sizeof(float2);
+    const size_t row_bytes = (size_t)kc * (IP + 2) * sizeof(float2);   // rows padded by one entry
     static const int cand[] = {512, 384, 256, 128, 96, 64, 32};
     // 4x4 tiles (64 accumulators): at most 256 threads; three-multiplication form: 384
     int t = 0, mc = 0, k = mode == 1 ? 2 : mode == 2 ? 1 : 0;
@@ -299,7 +309,7 @@ cudaError_t launch_xcorr_f32(const Handle &h, const float2 *corr, float2 *vis, c
     for (; kc >= 4; kc /= 2)
         if (xf32_geometry(N, total, nt, kc, mode, &threads, &max_ch)) break;
     if (kc < 4) return cudaErrorNotSupported;   // > ~800 stations
-    const size_t smem = 2ull * max_ch * kc * IP * sizeof(float2);
+    const size_t smem = 2ull * max_ch * kc * (IP + 2) * sizeof(float2);
     const long long blocks = (total * nt + threads - 1) / threads;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     auto pick = [&](auto rs, auto g3) {

@@ -127,7 +127,11 @@ def test_incoherent_vs_oracle(precision, bound, output, tint, fmt, SB, N, C, S):
     torch.cuda.synchronize()
     got = got.cpu().numpy().astype(np.float64)
     # the same operands as the kernel read, in FP64 and unscaled
-    y = corr.cpu().numpy().astype(np.float64) if precision == 0 else decode_planar(c, corr)
+    if precision == 0:
+        import paper_1801_04834_gb300 as fxg
+        y = fxg.f32_unblock(corr, c.S).cpu().numpy().astype(np.float64)
+    else:
+        y = decode_planar(c, corr)
     ref_k = oracle.beamform_incoherent(y, wts, mode=output, tint=tint)
     ek = per_subband_rel(got, ref_k)
     assert np.all(ek < 2e-6), ("kernel", ek)

@@ -119,13 +119,14 @@ def test_correct_f32_parity(N, C, S, ramp):
     blk = synth.Block(0, SB, N, 2, C, 16, S, None, synth.kaiser_sinc_taps(16, C), centres)
     c = make_corr(blk)
     dev = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
-    got = c.correct(dev(chan), dev(tb, torch.float64), dev(te, torch.float64), bandpass=dev(bp),
-                    gains=dev(g)).cpu().numpy().astype(np.float64)
+    unblock = fx().f32_unblock
+    got = unblock(c.correct(dev(chan), dev(tb, torch.float64), dev(te, torch.float64), bandpass=dev(bp),
+                            gains=dev(g)), S).cpu().numpy().astype(np.float64)
     assert got.shape == ref.shape
     assert rel_err(got, ref) < 2e-6
     # without bandpass / gains (NULL pointers mean ones)
     ref0 = oracle.correct(chan, FS, centres, tb, te)
-    got0 = c.correct(dev(chan), dev(tb, torch.float64), dev(te, torch.float64)).cpu().numpy()
+    got0 = unblock(c.correct(dev(chan), dev(tb, torch.float64), dev(te, torch.float64)), S).cpu().numpy()
     assert rel_err(got0.astype(np.float64), ref0) < 2e-6
 
 
@@ -144,7 +145,8 @@ def test_correlate_f32_parity(N, C, S, SB, form):
     blk = synth.Block(0, SB, N, 2, C, 16, S, None, synth.kaiser_sinc_taps(16, C),
                       synth.subband_centres(SB))
     c = make_corr(blk, xf32_form=form)
-    got = c.correlate(torch.from_numpy(corr).to("cuda", torch.float32)).cpu().numpy().astype(np.float64)
+    blocked = fx().f32_block(torch.from_numpy(corr).to("cuda", torch.float32))
+    got = c.correlate(blocked).cpu().numpy().astype(np.float64)
     assert got.shape == ref.shape
     assert np.all(per_subband_rel(got, ref) < 2e-6)
 

@@ -73,7 +73,8 @@ def test_tf32_split_planar_operands_match_fp32_path():
     t = d(tau, torch.float64)
     p = torch.full(c.corr_shape(), float("nan"), dtype=torch.float32, device="cuda")
     c.channelize_correct(raw, t, t, out=p)
-    f = c32.channelize_correct(raw, t, t)                      # [SB][C][S][N][2][2]
+    import paper_1801_04834_gb300 as fxg
+    f = fxg.f32_unblock(c32.channelize_correct(raw, t, t), c.S)   # [SB][C][S][N][2][2]
     torch.cuda.synchronize()
     I, S = c.I, c.S
     re = p[:, :, 0, :I, :S].permute(0, 1, 3, 2)               # [SB][C][S][I]
