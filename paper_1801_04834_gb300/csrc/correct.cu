@@ -54,51 +54,79 @@ __device__ __forceinline__ float2 correct_one(float2 x, float2 ph, int s, float 
 }
 
 // ---- FP32 output, spectrum-blocked [SB][C][ceil16(S)/16][N][16][2] ---------
-// CTA = (subband, station, block of 16 spectra), all C channels. Reads are
-// C-channel runs of one (pol, spectrum); writes are 256-byte runs (16 spectra
-// x 2 pols) of one channel; the tile [C][32 + 1] turns the corner in shared
-// memory. Spectra S .. ceil16(S) - 1 are written as zeros.
+// CTA = (subband, station, run of kBPC blocks of 16 spectra), all C channels;
+// stations run fastest in the grid so that CTAs resident together fill
+// neighbouring 256-byte runs of each channel. Per block the CTA first
+// tabulates exp(i phi) per (channel, spectrum) in shared memory
+// (phi = phi0 + s * step in FP32, reduced to [-pi, pi] with a two-constant
+// Cody-Waite split of 2 pi, then __sincosf: absolute error about 4e-7; both
+// pols share an entry). Reads are C-channel runs of one (pol, spectrum);
+// writes are 256-byte runs (16 spectra x 2 pols) of one channel; the tile
+// [C][32 + 1] turns the corner in shared memory. Spectra S .. ceil16(S) - 1
+// are written as zeros.
 constexpr int kNT = 256;
 constexpr int kBS = 16;                  // spectra per block of the FP32 layout
+constexpr int kBPC = 4;                  // blocks per CTA
 
 __global__ void __launch_bounds__(kNT)
 correct_f32_kernel(const float2 *__restrict__ chan, const float2 *__restrict__ table,
                    const float *__restrict__ bandpass, const float2 *__restrict__ gains,
                    float2 *__restrict__ corr, int N, int C, int S)
 {
-    extern __shared__ float2 tile[];     // [C][2 * kBS + 1]
+    extern __shared__ float2 tile[];     // [C][2 * kBS + 1], then the phasors [kBS][C]
     constexpr int TW = 2 * kBS + 1;
-    const int blk = blockIdx.x, n = blockIdx.y, sb = blockIdx.z;
-    const int NB = gridDim.x;
+    float2 *ph = tile + C * TW;
+    const int n = blockIdx.x, sb = blockIdx.z;
+    const int NB = (S + kBS - 1) / kBS;
     const float2 *tb = table + ((long long)sb * N + n) * C;
-    for (int e = threadIdx.x; e < kPols * kBS * C; e += kNT) {
-        const int k = e % C, j = (e / C) % kBS, p = e / (C * kBS);
-        const int s = blk * kBS + j;
-        float2 y = make_float2(0.f, 0.f);
-        if (s < S) {
-            const float2 x = chan[((((long long)sb * N + n) * kPols + p) * S + s) * C + k];
-            const float bp = bandpass ? bandpass[(long long)n * C + k] : 1.f;
-            const float2 g = gains ? gains[n * kPols + p] : make_float2(1.f, 0.f);
-            y = correct_one(x, tb[k], s, bp, g);
+    float2 g[kPols];
+#pragma unroll
+    for (int p = 0; p < kPols; ++p) g[p] = gains ? gains[n * kPols + p] : make_float2(1.f, 0.f);
+    const int blk_end = min(NB, (int)(blockIdx.y + 1) * kBPC);
+    for (int blk = blockIdx.y * kBPC; blk < blk_end; ++blk) {
+        if (blk > (int)blockIdx.y * kBPC) __syncthreads();   // the previous block's tile is written out
+        for (int e = threadIdx.x; e < kBS * C; e += kNT) {
+            const int k = e % C, j = e / C;
+            const float2 pt = tb[k];
+            const float phi = fmaf((float)(blk * kBS + j), pt.y, pt.x);
+            const float kq = rintf(phi * 0.15915494309189535f);            // phi / (2 pi)
+            float r = fmaf(-kq, 6.28125f, phi);                             // 2 pi = 6.28125 + 1.9353...e-3
+            r = fmaf(-kq, 1.9353071795864769e-3f, r);
+            float sn, cs;
+            __sincosf(r, &sn, &cs);
+            ph[e] = make_float2(cs, sn);
         }
-        tile[k * TW + j * kPols + p] = y;
-    }
-    __syncthreads();
-    float2 *out = corr + (((long long)sb * C * NB + blk) * N + n) * (2 * kBS);
-    const long long kstride = (long long)NB * N * (2 * kBS);
-    for (int e = threadIdx.x; e < C * 2 * kBS; e += kNT) {
-        const int jp = e % (2 * kBS), k = e / (2 * kBS);
-        out[k * kstride + jp] = tile[k * TW + jp];
+        __syncthreads();
+        for (int e = threadIdx.x; e < kPols * kBS * C; e += kNT) {
+            const int k = e % C, j = (e / C) % kBS, p = e / (C * kBS);
+            const int s = blk * kBS + j;
+            float2 y = make_float2(0.f, 0.f);
+            if (s < S) {
+                const float2 x = chan[((((long long)sb * N + n) * kPols + p) * S + s) * C + k];
+                const float bp = bandpass ? bandpass[(long long)n * C + k] : 1.f;
+                const float2 xg = make_float2(fmaf(x.x, g[p].x, -x.y * g[p].y), fmaf(x.x, g[p].y, x.y * g[p].x));
+                const float2 w = ph[j * C + k];
+                y = make_float2(bp * fmaf(xg.x, w.x, -xg.y * w.y), bp * fmaf(xg.x, w.y, xg.y * w.x));
+            }
+            tile[k * TW + j * kPols + p] = y;
+        }
+        __syncthreads();
+        float2 *out = corr + (((long long)sb * C * NB + blk) * N + n) * (2 * kBS);
+        const long long kstride = (long long)NB * N * (2 * kBS);
+        for (int e = threadIdx.x; e < C * 2 * kBS; e += kNT) {
+            const int jp = e % (2 * kBS), k = e / (2 * kBS);
+            out[k * kstride + jp] = tile[k * TW + jp];
+        }
     }
 }
 
 static cudaError_t launch_correct_f32(const float2 *chan, const float2 *table, const float *bandpass,
                                       const float2 *gains, float2 *corr, int SB, int N, int C, int S, cudaStream_t st)
 {
-    const size_t smem = (size_t)C * (2 * kBS + 1) * sizeof(float2);
+    const size_t smem = (size_t)C * (2 * kBS + 1 + kBS) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(correct_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((S + kBS - 1) / kBS, N, SB);
+    dim3 grid(N, ((S + kBS - 1) / kBS + kBPC - 1) / kBPC, SB);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
     correct_f32_kernel<<<grid, kNT, smem, st>>>(chan, table, bandpass, gains, corr, N, C, S);
     return cudaGetLastError();
