@@ -649,6 +649,214 @@ __global__ void planar_pad_kernel(unsigned short *__restrict__ corr, long long n
     for (int s = from + threadIdx.x; s < S_pad; s += blockDim.x) r[s] = 0;
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised fused kernel for C = 256 with planar outputs (OUT = 2..5):
+// one CTA per (station, pol), 256 FIR threads (one channel each) and 256 FFT
+// threads, one CTA per SM. A round's rows (16 spectra of one input) fit twice
+// in shared memory at this channel count only per input; the CTAs of a
+// station's two pols are neighbours in the grid and read the same raw rows
+// (the second read mostly from L2). FIR round b -> u[b & 1] and the phasors
+// exp(i phi) x flag of its 16 spectra (one __sincosf per channel and round,
+// then rotations by exp(i step), computed in FP32 from the FP64-derived step)
+// -> FULL; FFT round b: pass 1 (row = 16 lanes), transposed into
+// P1[k1][n2][row] over u[b & 1] after barrier FFT, pass 2 with lane = spectrum
+// (a half-warp per k1), so a warp store is 2 x 32 bytes of planar rows.
+struct Ws256 {
+    static constexpr int C = 256, R = 16, NF = 256;
+    static constexpr int ROW = C + 16;                  // FIR row stride (float2)
+    static constexpr int USZ = kRound * ROW;            // one row buffer: 16 spectra
+    static constexpr int RS = kRound + 1;               // P1 row stride
+    static constexpr int EJ = kRound + 1;               // phasor table: [C][EJ]
+    static constexpr int ESZ = C * EJ;
+    static_assert(R * R * RS <= USZ, "P1 fits over the row buffer");
+};
+
+template <typename TIn>
+constexpr size_t ws256_smem_bytes()
+{
+    using W = Ws256;
+    return (size_t)W::C * sizeof(float2) + 2ull * kRound * W::C * kPols * sizeof(TIn) +
+           (2ull * W::USZ + 2ull * W::ESZ + 2ull * W::C) * sizeof(float2);
+}
+
+template <int T, typename TIn, int OUT>
+__global__ void __launch_bounds__(2 * Ws256::NF, 1)
+ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const float *__restrict__ taps,
+                         const float2 *__restrict__ twiddle, const float2 *__restrict__ phase,
+                         const float *__restrict__ bandpass, const float2 *__restrict__ gains, int N, int S,
+                         int I_pad, int s_out, float scale, int rounds_per_cta, const float *__restrict__ flags,
+                         int s_base, int s_end)
+{
+    using W = Ws256;
+    constexpr int C = W::C, R = W::R, NF = W::NF, ROW = W::ROW, USZ = W::USZ, RS = W::RS, EJ = W::EJ, ESZ = W::ESZ;
+    constexpr int ROW_BYTES = C * kPols * (int)sizeof(TIn);     // one raw time row of the station (both pols)
+    constexpr int BUF_BYTES = kRound * ROW_BYTES;
+    constexpr int ALL = 2 * NF;
+    static_assert(OUT >= 2 && OUT <= 5, "planar outputs");
+    static_assert(ROW_BYTES % 16 == 0, "rows must be whole 16-byte chunks");
+    static_assert(ws256_smem_bytes<TIn>() <= 227 * 1024, "one CTA per SM");
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2 *tw = reinterpret_cast<float2 *>(smem);
+    unsigned char *inbuf = smem + C * sizeof(float2);
+    float2 *u = reinterpret_cast<float2 *>(inbuf + 2 * BUF_BYTES);   // [2][USZ]
+    float2 *et = u + 2 * USZ;                                         // [2][C][EJ]
+    float2 *bgt = et + 2 * ESZ;                                       // [C] bandpass x gain x scale
+    float2 *tw2 = bgt + C;                                            // [k1][n2] = W_C^(n2 k1): pass-1
+                                                                      // lanes (n2) read consecutive entries
+    const int tid = threadIdx.x;
+    const int sb = blockIdx.z;
+    const int n = blockIdx.x / kPols, p = blockIdx.x % kPols;       // (station, pol) fastest
+    const int s0 = s_base + blockIdx.y * rounds_per_cta * kRound;
+    const int rows_total = S + T - 1;
+    const long long L = (long long)rows_total * C;
+    const int nrounds = min(rounds_per_cta, (s_end - s0 + kRound - 1) / kRound);
+
+    for (int i = tid; i < C; i += ALL) {
+        tw[i] = twiddle[i];
+        tw2[i] = twiddle[(i % R) * (i / R)];
+        const float b = bandpass ? bandpass[(long long)n * C + i] : 1.f;
+        const float2 g = gains ? gains[n * kPols + p] : make_float2(1.f, 0.f);
+        bgt[i] = make_float2(b * g.x * scale, b * g.y * scale);
+    }
+    __syncthreads();
+
+    if (tid < NF) {
+        // ---------------- FIR threads: channel c of input (n, p) ----------------
+        auto stage = [&](int buf, int r0, int nrows) {
+            const int chunks = nrows * ROW_BYTES / 16;
+            const unsigned char *src0 = reinterpret_cast<const unsigned char *>(raw) +
+                                        (((long long)sb * N + n) * L + (long long)r0 * C) * kPols * sizeof(TIn);
+            for (int q = tid; q < chunks; q += NF) {
+                const bool ok = r0 + (q * 16) / ROW_BYTES < rows_total;
+                cp_async16(inbuf + buf * BUF_BYTES + q * 16,
+                           ok ? src0 + q * 16 : reinterpret_cast<const unsigned char *>(raw), ok ? 16 : 0);
+            }
+        };
+        const int c = tid;
+        const float2 pst = phase[((long long)sb * N + n) * C + c];   // (phi0, step)
+        float sn1, cs1;
+        sincosf(pst.y, &sn1, &cs1);                                  // exp(i step)
+        const float2 rot = make_float2(cs1, sn1);
+        float2 h[T];
+#pragma unroll
+        for (int k = 0; k < T; ++k) h[k] = make_float2(taps[k * C + c], taps[k * C + c]);
+
+        stage(1, s0, T - 1);
+        cp_async_commit();
+        stage(0, s0 + T - 1, kRound);
+        cp_async_commit();
+        cp_async_wait<1>();
+        fbar_sync(kFBarRaw, NF);
+        float2 win[T];
+        const TIn *in1 = reinterpret_cast<const TIn *>(inbuf + BUF_BYTES);
+#pragma unroll
+        for (int k = 0; k < T - 1; ++k) win[k] = to_f2(in1[k * C * kPols + c * kPols + p]);
+        win[T - 1] = make_float2(0.f, 0.f);
+        fbar_sync(kFBarRaw, NF);
+        if (nrounds > 1) stage(1, s0 + T - 1 + kRound, kRound);
+        cp_async_commit();
+
+        for (int b = 0; b < nrounds; ++b) {
+            const int q = b & 1;
+            const int sr = s0 + b * kRound;
+            cp_async_wait<1>();
+            fbar_sync(kFBarRaw, NF);
+            if (b >= 2) fbar_sync(kFBarEmpty + q, ALL);
+            const TIn *in = reinterpret_cast<const TIn *>(inbuf + q * BUF_BYTES);
+            float2 *uq = u + q * USZ;
+#pragma unroll
+            for (int j = 0; j < kRound; ++j) {
+                win[(T - 1 + j) % T] = to_f2(in[j * C * kPols + c * kPols + p]);
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < T; ++k) acc = __ffma2_rn(h[k], win[(j + k) % T], acc);
+                uq[j * ROW + c] = acc;
+            }
+            // phasors of this round: phi(sr) reduced to [-pi, pi] (two-constant
+            // Cody-Waite split of 2 pi) and __sincosf, then rotations by exp(i step)
+            float2 *eq = et + q * ESZ + c * EJ;
+            float2 e;
+            {
+                const float phi = fmaf((float)sr, pst.y, pst.x);
+                const float kq = rintf(phi * 0.15915494309189535f);
+                float r = fmaf(-kq, 6.28125f, phi);
+                r = fmaf(-kq, 1.9353071795864769e-3f, r);
+                __sincosf(r, &e.y, &e.x);
+            }
+#pragma unroll
+            for (int j = 0; j < kRound; ++j) {
+                const float fw = flags ? flags[(long long)n * S + min(sr + j, S - 1)] : 1.f;
+                eq[j] = make_float2(e.x * fw, e.y * fw);
+                e = cmul(e, rot);
+            }
+            fbar_arrive(kFBarFull + q, ALL);
+            fbar_sync(kFBarRaw, NF);
+            if (b + 2 < nrounds) stage(q, s0 + T - 1 + (b + 2) * kRound, kRound);
+            cp_async_commit();
+        }
+        cp_async_wait<0>();
+    } else {
+        // ---------------- FFT threads ----------------
+        const int t = tid - NF;
+        constexpr int planes = OUT == 4 ? 4 : 2;
+        const long long pstride = (long long)I_pad * s_out;
+        const int i = n * kPols + p;
+        for (int b = 0; b < nrounds; ++b) {
+            const int q = b & 1;
+            const int sr = s0 + b * kRound;
+            float2 *uq = u + q * USZ;
+            const float2 *eq = et + q * ESZ;
+            fbar_sync(kFBarFull + q, ALL);
+            // pass 1: row tr = t / 16 (spectrum), column n2 = t mod 16
+            const int tr = t / R, n2 = t % R;
+            float2 v[R];
+#pragma unroll
+            for (int n1 = 0; n1 < R; ++n1) v[n1] = uq[tr * ROW + R * n1 + n2];
+            fft_reg<R>(v);
+#pragma unroll
+            for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], tw2[k1 * R + n2]);
+            fbar_sync(kFBarFft, NF);                // every FFT thread has read u[q]
+#pragma unroll
+            for (int k1 = 0; k1 < R; ++k1) uq[(k1 * R + n2) * RS + tr] = v[k1];
+            fbar_sync(kFBarFft, NF);                // P1 complete
+            // pass 2: half-warp per k1, lane = spectrum j
+            const int k1 = t / 16, j = t % 16;
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m] = uq[(k1 * R + m) * RS + j];
+            fft_reg<R>(v);
+#pragma unroll
+            for (int k2 = 0; k2 < R; ++k2) {
+                const int kout = k1 + R * ((k2 + R / 2) % R);
+                v[k2] = cmul(v[k2], cmul(bgt[kout], eq[kout * EJ + j]));
+            }
+            if (b + 2 < nrounds) fbar_arrive(kFBarEmpty + q, ALL);
+            const int s = sr + j;
+            const long long base = (long long)sb * C * planes * pstride + (long long)i * s_out + (s - s_base);
+#pragma unroll
+            for (int k2 = 0; k2 < R; ++k2) {
+                const int kout = k1 + R * ((k2 + R / 2) % R);
+                const float2 y = s < s_end ? v[k2] : make_float2(0.f, 0.f);
+                const long long o = base + (long long)kout * planes * pstride;
+                if constexpr (OUT == 5) {
+                    float *out = reinterpret_cast<float *>(corr);
+                    out[o] = y.x;
+                    out[o + pstride] = y.y;
+                } else {
+                    unsigned short *out = reinterpret_cast<unsigned short *>(corr);
+                    const unsigned short hr = to_bits(y.x, OUT), hi = to_bits(y.y, OUT);
+                    out[o] = hr;
+                    out[o + pstride] = hi;
+                    if constexpr (OUT == 4) {
+                        out[o + 2 * pstride] = __half_as_ushort(__float2half_rn(y.x - __half2float(__ushort_as_half(hr))));
+                        out[o + 3 * pstride] = __half_as_ushort(__float2half_rn(y.y - __half2float(__ushort_as_half(hi))));
+                    }
+                }
+            }
+        }
+    }
+}
+
 // Zeros of the planar layout outside what the F-stage wrote: inputs [I, I_pad)
 // and spectra [S16, s_out) of every (subband, channel, plane).
 cudaError_t planar_pad(const Handle &h, void *corr, int out, int S16, int s_out, cudaStream_t st)
@@ -697,6 +905,23 @@ cudaError_t launch_t(const Handle &h, const void *raw, void *corr, const float *
                                             s_base, s_end);
         e = cudaGetLastError();
         if (e != cudaSuccess || OUT == 1) return e;
+        return planar_pad(h, corr, OUT, rounds_total * kRound, s_out, st);
+    } else if constexpr (C == 256 && OUT != 1) {
+        // one CTA per (station, pol) and SM; long runs of rounds amortise the
+        // prologue, shortened only while the grid would be under ~4 waves
+        int rpc = 64;
+        while (rpc > 1 && (long long)((rounds_total + rpc - 1) / rpc) * N * kPols * SB < 152LL * 4) rpc /= 2;
+        dim3 grid(N * kPols, (rounds_total + rpc - 1) / rpc, SB);
+        if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+        constexpr size_t smem = ws256_smem_bytes<TIn>();
+        auto kern = ppf_correct_ws256_kernel<T, TIn, OUT>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, 2 * Ws256::NF, smem, st>>>(reinterpret_cast<const TIn *>(raw), corr, h.d_taps, h.d_twiddle,
+                                                h.d_phase, bandpass, gains, N, S, h.I_pad, s_out, scale, rpc, flags,
+                                                s_base, s_end);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
         return planar_pad(h, corr, OUT, rounds_total * kRound, s_out, st);
     } else {
         const int sgroups = (N + Cfg::NPC - 1) / Cfg::NPC;

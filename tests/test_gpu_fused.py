@@ -114,6 +114,11 @@ def test_ci4_end_to_end(precision, bound, C, S):
     (2, synth.CI16, 4, 64, 16, 4, 2430, [6, 58]),
     (0, synth.CI8, 4, 64, 16, 8, 2430, [2, 3, 61]),
     (0, synth.CI4, 2, 64, 64, 16, 1210, [9, 44]),
+    # 256 channels, planar outputs (one CTA per station and pol, all 48 rounds of
+    # the 8-bit workload's 768 spectra in one CTA)
+    (1, synth.CI8, 5, 64, 256, 16, 768, [3, 50]),
+    (3, synth.CI16, 5, 48, 256, 16, 768, [0, 47]),
+    (4, synth.CI8, 5, 64, 256, 16, 768, [63]),
     # the LOFAR 16-bit shape on 13 subbands: 64 rounds per CTA as in the benchmark
     (0, synth.CI16, 13, 64, 64, 16, 3072, [7, 40]),
 ])
