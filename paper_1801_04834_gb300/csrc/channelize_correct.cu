@@ -13,23 +13,25 @@
 // in-register FFT). After FFT pass 2 each output X(n, p, s, k) is multiplied
 // by bandpass(n, k) * gain(n, p) * exp(i phi), phi = phi0(n, k) + s * step(n, k)
 // (phi0 reduced mod 2 pi and step formed in FP64 by the phase-table kernel,
-// as in fx_correct). Per 16-spectrum round the CTA tabulates the whole
-// per-sample factor w(n, p, k, s) = flag(n, s) * bandpass(n, k) * gain(n, p)
-// * exp(i phi) once: one thread per (station, channel) evaluates exp(i phi)
-// (phi reduced to [-pi, pi] in FP32 with a two-constant Cody-Waite split of
-// 2 pi, then __sincosf, absolute error about 4e-7 on that interval) and
-// multiplies in its two pols' bandpass x gain, kept in registers. FFT pass 2
-// then needs one shared load and one complex multiply per output.
+// as in fx_correct); exp(i phi) is evaluated in FP32 after a reduction to
+// [-pi, pi] with a two-constant Cody-Waite split of 2 pi, then __sincosf
+// (absolute error about 4e-7 on that interval), once per (station, channel,
+// spectrum) and shared by the two pols.
 //
-// Transforms are stored spectrum-major (row j * IC + input), which keeps the
-// FIR stores and both FFT passes free of bank conflicts. Output:
-//   FP32   spectrum-blocked [SB][C][ceil16(S)/16][N][16][2]: for C = 16, 64
-//          by the warp-specialised ppf_correct_ws_kernel below (each warp
-//          store is one station's 16 spectra x 2 pols of a channel, 256
-//          contiguous bytes); for C = 256 from the pass-2 registers;
-//   planar [SB][C][planes][I_pad][S_pad]: turned in shared memory (reusing
-//          the FFT buffer) into per (channel, plane, input) runs of 16
-//          spectra (32 bytes), FP16/BF16 (x operand_scale) or hi/lo FP16.
+// Kernels (all write zeros for spectra past the block's end):
+//   ppf_correct_ws_kernel     C = 16, 64, every output form: FIR and FFT on
+//                             separate warps, pass 2 with lane = transform row
+//                             so a warp store is one 256-byte run of the FP32
+//                             spectrum-blocked layout [SB][C][ceil16(S)/16][N][16][2]
+//                             or 2 inputs x 16 spectra of a planar plane;
+//   ppf_correct_ws256_kernel  C = 256, planar outputs: one CTA per (station,
+//                             pol), pass 2 with lane = spectrum;
+//   ppf_correct_kernel        C = 256, FP32 output: FIR and FFT alternating
+//                             on the same threads, writing from the pass-2
+//                             registers.
+// Planar outputs are [SB][C][planes][I_pad][S_pad] (FP16/BF16 x operand_scale,
+// hi/lo FP16, or FP32 for the TF32-split X-stage); planar_pad zeroes what the
+// F-stage does not write (inputs I..I_pad, spectra past the last round).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -42,9 +44,10 @@ namespace {
 
 using namespace ppf;
 
-// OUT: 1 FP32 interleaved, 2 FP16 planar, 3 BF16 planar, 4 split FP16 planar, 5 FP32 planar
-// per-round factor table: [kRound][IC inputs][PHC], rows padded so that FFT
-// pass 2 (lanes = 8 or 16 consecutive channels x inputs) reads it conflict free
+// OUT: 1 FP32 spectrum-blocked, 2 FP16 planar, 3 BF16 planar, 4 split FP16 planar, 5 FP32 planar.
+// ppf_correct_kernel's per-round factor table: [kRound][IC inputs][PHC], rows
+// padded so that FFT pass 2 (lanes = 8 or 16 consecutive channels x inputs)
+// reads it conflict free
 template <int C>
 constexpr int fused_phc() { return C + (C == 16 ? 4 : 8); }
 
@@ -74,14 +77,9 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
     constexpr int ROW_BYTES = C * kPols * (int)sizeof(TIn);
     constexpr int BUF_BYTES = kRound * NPC * ROW_BYTES;
     constexpr int IC = NPC * kPols;                 // inputs of this CTA
-    // planar staging [IC][C][17] + a pad per input: rows of 17 (odd) keep the
-    // pass-2 stores (lanes = consecutive channels) and the read-out (lanes =
-    // consecutive channels, 16 spectra each) conflict free; the pad moves the
-    // inputs of one half-warp onto different banks
-    constexpr int SIL = C * (kRound + 1) + (C == 16 ? 4 : 8);   // staging block per input
     constexpr int PHC = fused_phc<C>();
     constexpr int PHROW = IC * PHC;                 // factor-table row per spectrum
-    static_assert(OUT == 1 || IC * SIL <= Cfg::NTR * ROW, "staging fits in the FFT buffer");
+    static_assert(OUT == 1, "FP32 spectrum-blocked output (planar outputs: the warp-specialised kernels)");
     static_assert(NT >= 512 ? fused_smem_bytes<C, TIn>() <= 227 * 1024
                             : 2 * (fused_smem_bytes<C, TIn>() + 1024) <= 228 * 1024,
                   "two CTAs per SM (one at 512 threads)");
@@ -237,7 +235,7 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
                 y[it][k2] = cmul(y[it][k2], ph[j * PHROW + il * PHC + kout]);
             }
         }
-        if constexpr (OUT == 1) {
+        {
             // ---- write out from registers into the spectrum-blocked FP32 layout
             // [SB][C][S_pad/16][N][16][2] (zeros past s_end) ----
             float2 *out = reinterpret_cast<float2 *>(corr);
@@ -258,88 +256,6 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
                 }
             }
             // the next round's first barrier orders these reads of u before its FIR stores
-        } else {
-        __syncthreads();                             // every read of u is done
-        // ---- stage the corrected round in u, in the output's order (padded rows) ----
-#pragma unroll
-        for (int it = 0; it < Cfg::FFT_ITERS; ++it) {
-            const int task = it * NT + tid;
-            const int tr = task / R, k1 = task % R;
-            const int j = tr / IC, il = tr % IC;
-#pragma unroll
-            for (int k2 = 0; k2 < R; ++k2) {
-                const int kout = k1 + R * ((k2 + R / 2) % R);
-                u[il * SIL + kout * (kRound + 1) + j] = y[it][k2];    // [IC][C][17]
-            }
-        }
-        __syncthreads();
-        // ---- write out ----
-        if constexpr (OUT == 5) {
-            // FP32 planar: per (channel, input) 16 spectra = 64 bytes per plane
-            float *out = reinterpret_cast<float *>(corr);
-            const long long pstride = (long long)I_pad * S_pad;
-            for (int e = tid; e < C * IC; e += NT) {
-                const int kout = e % C, il = e / C;
-                const int i = 2 * n0 + il;
-                if (i >= I) continue;
-                const float2 *src = u + il * SIL + kout * (kRound + 1);
-                float4 *re = reinterpret_cast<float4 *>(out + (((long long)sb * C + kout) * 2) * pstride +
-                                                        (long long)i * S_pad + (sr - s_base));
-                float4 *im = re + pstride / 4;
-#pragma unroll
-                for (int q = 0; q < kRound / 4; ++q) {
-                    float2 v[4];
-#pragma unroll
-                    for (int t = 0; t < 4; ++t)
-                        v[t] = (sr + 4 * q + t < s_end) ? src[4 * q + t] : make_float2(0.f, 0.f);
-                    re[q] = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
-                    im[q] = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
-                }
-            }
-        } else {
-            constexpr int planes = (OUT == 4) ? 4 : 2;
-            unsigned short *out = reinterpret_cast<unsigned short *>(corr);
-            const long long pstride = (long long)I_pad * S_pad;
-            for (int e = tid; e < C * IC; e += NT) {
-                const int kout = e % C, il = e / C;
-                const int i = 2 * n0 + il;
-                if (i >= I) continue;
-                const float2 *src = u + il * SIL + kout * (kRound + 1);
-                unsigned short re[kRound], im[kRound], rl[kRound], iml[kRound];
-#pragma unroll
-                for (int j = 0; j < kRound; ++j) {
-                    const float2 v = (sr + j < s_end) ? src[j] : make_float2(0.f, 0.f);
-                    re[j] = to_bits(v.x, OUT);
-                    im[j] = to_bits(v.y, OUT);
-                    if constexpr (OUT == 4) {
-                        rl[j] = __half_as_ushort(__float2half_rn(v.x - __half2float(__ushort_as_half(re[j]))));
-                        iml[j] = __half_as_ushort(__float2half_rn(v.y - __half2float(__ushort_as_half(im[j]))));
-                    }
-                }
-                const long long base =
-                    (((long long)sb * C + kout) * planes) * pstride + (long long)i * S_pad + (sr - s_base);
-                auto put = [&](long long off, const unsigned short (&v)[kRound]) {
-                    uint4 w0, w1;
-                    w0.x = v[0] | ((unsigned)v[1] << 16);
-                    w0.y = v[2] | ((unsigned)v[3] << 16);
-                    w0.z = v[4] | ((unsigned)v[5] << 16);
-                    w0.w = v[6] | ((unsigned)v[7] << 16);
-                    w1.x = v[8] | ((unsigned)v[9] << 16);
-                    w1.y = v[10] | ((unsigned)v[11] << 16);
-                    w1.z = v[12] | ((unsigned)v[13] << 16);
-                    w1.w = v[14] | ((unsigned)v[15] << 16);
-                    uint4 *d = reinterpret_cast<uint4 *>(out + off);
-                    d[0] = w0;
-                    d[1] = w1;
-                };
-                put(base, re);
-                put(base + pstride, im);
-                if constexpr (OUT == 4) {
-                    put(base + 2 * pstride, rl);
-                    put(base + 3 * pstride, iml);
-                }
-            }
-        }
         }
     }
     cp_async_wait<0>();
