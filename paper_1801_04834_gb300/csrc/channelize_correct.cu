@@ -571,10 +571,12 @@ __global__ void planar_pad_kernel(unsigned short *__restrict__ corr, long long n
 // threads, one CTA per SM. A round's rows (16 spectra of one input) fit twice
 // in shared memory at this channel count only per input; the CTAs of a
 // station's two pols are neighbours in the grid and read the same raw rows
-// (the second read mostly from L2). FIR round b -> u[b & 1] and the phasors
-// exp(i phi) x flag of its 16 spectra (one __sincosf per channel and round,
-// then rotations by exp(i step), computed in FP32 from the FP64-derived step)
-// -> FULL; FFT round b: pass 1 (row = 16 lanes), transposed into
+// (the second read mostly from L2). FIR round b -> u[b & 1] and the whole
+// per-sample factor bandpass x gain x flag x exp(i phi) of its 16 spectra
+// (one __sincosf per channel and round, then rotations by exp(i step),
+// computed in FP32 from the FP64-derived step; bandpass x gain is constant
+// per channel within a CTA, which serves one input) -> FULL; FFT round b:
+// pass 1 (row = 16 lanes), transposed into
 // P1[k1][n2][row] over u[b & 1] after barrier FFT, pass 2 with lane = spectrum
 // (a half-warp per k1), so a warp store is 2 x 32 bytes of planar rows.
 struct Ws256 {
@@ -651,6 +653,7 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
         };
         const int c = tid;
         const float2 pst = phase[((long long)sb * N + n) * C + c];   // (phi0, step)
+        const float2 bgc = bgt[c];                                   // this input's bandpass x gain x scale
         float sn1, cs1;
         sincosf(pst.y, &sn1, &cs1);                                  // exp(i step)
         const float2 rot = make_float2(cs1, sn1);
@@ -703,7 +706,7 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
 #pragma unroll
             for (int j = 0; j < kRound; ++j) {
                 const float fw = flags ? flags[(long long)n * S + min(sr + j, S - 1)] : 1.f;
-                eq[j] = make_float2(e.x * fw, e.y * fw);
+                eq[j] = cmul(bgc, make_float2(e.x * fw, e.y * fw));     // the whole per-sample factor
                 e = cmul(e, rot);
             }
             fbar_arrive(kFBarFull + q, ALL);
@@ -744,7 +747,7 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
 #pragma unroll
             for (int k2 = 0; k2 < R; ++k2) {
                 const int kout = k1 + R * ((k2 + R / 2) % R);
-                v[k2] = cmul(v[k2], cmul(bgt[kout], eq[kout * EJ + j]));
+                v[k2] = cmul(v[k2], eq[kout * EJ + j]);
             }
             if (b + 2 < nrounds) fbar_arrive(kFBarEmpty + q, ALL);
             const int s = sr + j;
