@@ -313,16 +313,6 @@ constexpr int fused_ws_ctas()
     return 3 * (fused_ws_smem_bytes<C, TIn>() + 1024) <= 228 * 1024 ? 3 : 2;
 }
 
-enum { kFBarRaw = 1, kFBarFft = 2, kFBarFull = 3, kFBarEmpty = 5 };   // FULL/EMPTY use ids +0, +1
-
-__device__ __forceinline__ void fbar_sync(int id, int n)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-__device__ __forceinline__ void fbar_arrive(int id, int n)
-{
-    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
 
 // OUT as ppf_correct_kernel: 1 FP32 spectrum-blocked, 2 FP16 / 3 BF16 / 4 split
 // FP16 / 5 FP32 planar ([SB][C][planes][I_pad][s_out], x scale for 2-4).
@@ -402,13 +392,13 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
         stage(0, s0 + T - 1, kRound);
         cp_async_commit();
         cp_async_wait<1>();
-        fbar_sync(kFBarRaw, NF);
+        named_bar_sync(kBarRaw, NF);
         float2 win[T];
         const TIn *in1 = reinterpret_cast<const TIn *>(inbuf + BUF_BYTES);
 #pragma unroll
         for (int k = 0; k < T - 1; ++k) win[k] = to_f2(in1[k * NF + tid]);
         win[T - 1] = make_float2(0.f, 0.f);
-        fbar_sync(kFBarRaw, NF);
+        named_bar_sync(kBarRaw, NF);
         if (nrounds > 1) stage(1, s0 + T - 1 + kRound, kRound);
         cp_async_commit();
 
@@ -416,8 +406,8 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
             const int q = b & 1;
             const int sr = s0 + b * kRound;
             cp_async_wait<1>();
-            fbar_sync(kFBarRaw, NF);                // raw rows of round b are in
-            if (b >= 2) fbar_sync(kFBarEmpty + q, ALL);   // FFT threads are done with u[q], et[q]
+            named_bar_sync(kBarRaw, NF);                // raw rows of round b are in
+            if (b >= 2) named_bar_sync(kBarEmpty + q, ALL);   // FFT threads are done with u[q], et[q]
             const TIn *in = reinterpret_cast<const TIn *>(inbuf + q * BUF_BYTES);
             float2 *uq = u + q * USZ;
             float2 *fo = rowp(uq, (nl * kPols + p) * kRound) + c;
@@ -444,8 +434,8 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
                 const float fw = flags ? flags[(long long)own_n * S + min(sr + j, S - 1)] : 1.f;
                 eq[j] = make_float2(cs * fw, sn * fw);
             }
-            fbar_arrive(kFBarFull + q, ALL);
-            fbar_sync(kFBarRaw, NF);                // every FIR thread has read raw buffer q
+            named_bar_arrive(kBarFull + q, ALL);
+            named_bar_sync(kBarRaw, NF);                // every FIR thread has read raw buffer q
             if (b + 2 < nrounds) stage(q, s0 + T - 1 + (b + 2) * kRound, kRound);
             cp_async_commit();
         }
@@ -465,7 +455,7 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
             const int sr = s0 + b * kRound;
             float2 *uq = u + q * USZ;
             const float2 *eq = et + q * ESZ;
-            fbar_sync(kFBarFull + q, ALL);          // FIR round b is in u[q], et[q]
+            named_bar_sync(kBarFull + q, ALL);          // FIR round b is in u[q], et[q]
             // pass 1: R-point FFTs over n1 (stride R), times W_C^(n2 k1)
             float2 v1[P1ITERS][R];
 #pragma unroll
@@ -478,14 +468,14 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
 #pragma unroll
                 for (int k1 = 1; k1 < R; ++k1) v1[it][k1] = cmul(v1[it][k1], twr[k1]);
             }
-            fbar_sync(kFBarFft, NF);                // every FFT thread has read its rows of u[q]
+            named_bar_sync(kBarFft, NF);                // every FFT thread has read its rows of u[q]
 #pragma unroll
             for (int it = 0; it < P1ITERS; ++it) {
                 const int task = it * NF + t;
 #pragma unroll
                 for (int k1 = 0; k1 < R; ++k1) uq[(k1 * R + task % R) * RS + task / R] = v1[it][k1];
             }
-            fbar_sync(kFBarFft, NF);                // P1 complete
+            named_bar_sync(kBarFft, NF);                // P1 complete
             // pass 2: lane = row (input il, spectrum j), item = (row group, k1)
 #pragma unroll
             for (int it = 0; it < W::ITEMS / 4; ++it) {
@@ -504,7 +494,7 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
                     const int kout = k1 + R * ((k2 + R / 2) % R);
                     v[k2] = cmul(v[k2], cmul(bg[kout], e[kout * EJ]));
                 }
-                if (it == W::ITEMS / 4 - 1 && b + 2 < nrounds) fbar_arrive(kFBarEmpty + q, ALL);
+                if (it == W::ITEMS / 4 - 1 && b + 2 < nrounds) named_bar_arrive(kBarEmpty + q, ALL);
                 const int s = sr + j, i = 2 * n0 + il;
                 if (i < I) {
                     if constexpr (OUT == 1) {
@@ -666,13 +656,13 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
         stage(0, s0 + T - 1, kRound);
         cp_async_commit();
         cp_async_wait<1>();
-        fbar_sync(kFBarRaw, NF);
+        named_bar_sync(kBarRaw, NF);
         float2 win[T];
         const TIn *in1 = reinterpret_cast<const TIn *>(inbuf + BUF_BYTES);
 #pragma unroll
         for (int k = 0; k < T - 1; ++k) win[k] = to_f2(in1[k * C * kPols + c * kPols + p]);
         win[T - 1] = make_float2(0.f, 0.f);
-        fbar_sync(kFBarRaw, NF);
+        named_bar_sync(kBarRaw, NF);
         if (nrounds > 1) stage(1, s0 + T - 1 + kRound, kRound);
         cp_async_commit();
 
@@ -680,8 +670,8 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
             const int q = b & 1;
             const int sr = s0 + b * kRound;
             cp_async_wait<1>();
-            fbar_sync(kFBarRaw, NF);
-            if (b >= 2) fbar_sync(kFBarEmpty + q, ALL);
+            named_bar_sync(kBarRaw, NF);
+            if (b >= 2) named_bar_sync(kBarEmpty + q, ALL);
             const TIn *in = reinterpret_cast<const TIn *>(inbuf + q * BUF_BYTES);
             float2 *uq = u + q * USZ;
 #pragma unroll
@@ -709,8 +699,8 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
                 eq[j] = cmul(bgc, make_float2(e.x * fw, e.y * fw));     // the whole per-sample factor
                 e = cmul(e, rot);
             }
-            fbar_arrive(kFBarFull + q, ALL);
-            fbar_sync(kFBarRaw, NF);
+            named_bar_arrive(kBarFull + q, ALL);
+            named_bar_sync(kBarRaw, NF);
             if (b + 2 < nrounds) stage(q, s0 + T - 1 + (b + 2) * kRound, kRound);
             cp_async_commit();
         }
@@ -726,7 +716,7 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
             const int sr = s0 + b * kRound;
             float2 *uq = u + q * USZ;
             const float2 *eq = et + q * ESZ;
-            fbar_sync(kFBarFull + q, ALL);
+            named_bar_sync(kBarFull + q, ALL);
             // pass 1: row tr = t / 16 (spectrum), column n2 = t mod 16
             const int tr = t / R, n2 = t % R;
             float2 v[R];
@@ -735,10 +725,10 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
             fft_reg<R>(v);
 #pragma unroll
             for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], tw2[k1 * R + n2]);
-            fbar_sync(kFBarFft, NF);                // every FFT thread has read u[q]
+            named_bar_sync(kBarFft, NF);                // every FFT thread has read u[q]
 #pragma unroll
             for (int k1 = 0; k1 < R; ++k1) uq[(k1 * R + n2) * RS + tr] = v[k1];
-            fbar_sync(kFBarFft, NF);                // P1 complete
+            named_bar_sync(kBarFft, NF);                // P1 complete
             // pass 2: half-warp per k1, lane = spectrum j
             const int k1 = t / 16, j = t % 16;
 #pragma unroll
@@ -749,7 +739,7 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
                 const int kout = k1 + R * ((k2 + R / 2) % R);
                 v[k2] = cmul(v[k2], eq[kout * EJ + j]);
             }
-            if (b + 2 < nrounds) fbar_arrive(kFBarEmpty + q, ALL);
+            if (b + 2 < nrounds) named_bar_arrive(kBarEmpty + q, ALL);
             const int s = sr + j;
             const long long base = (long long)sb * C * planes * pstride + (long long)i * s_out + (s - s_base);
 #pragma unroll

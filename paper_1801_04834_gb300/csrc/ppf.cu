@@ -218,14 +218,6 @@ constexpr size_t ppf_ws_smem_bytes()
            2ull * W::NTR * W::ROW * sizeof(float2);
 }
 
-enum { kBarRaw = 1, kBarFull = 2, kBarEmpty = 4 };   // FULL/EMPTY use ids +0, +1
-
-__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
-__device__ __forceinline__ void bar_arrive(int id, int n)
-{
-    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-
 template <int C, int T, typename TIn>
 __global__ void __launch_bounds__(2 * PpfWsCfg<C>::NF, 3)
 ppf_ws_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *__restrict__ taps,
@@ -284,21 +276,21 @@ ppf_ws_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const floa
         stage(0, s0 + T - 1, kRound);               // round 0
         cp_async_commit();
         cp_async_wait<1>();
-        bar_sync(kBarRaw, NF);
+        named_bar_sync(kBarRaw, NF);
         float2 win[T];
         const TIn *in1 = reinterpret_cast<const TIn *>(inbuf + BUF_BYTES);
 #pragma unroll
         for (int k = 0; k < T - 1; ++k) win[k] = to_f2(in1[k * NF + tid]);
         win[T - 1] = make_float2(0.f, 0.f);
-        bar_sync(kBarRaw, NF);
+        named_bar_sync(kBarRaw, NF);
         if (nrounds > 1) stage(1, s0 + T - 1 + kRound, kRound);
         cp_async_commit();
 
         for (int b = 0; b < nrounds; ++b) {
             const int q = b & 1;
             cp_async_wait<1>();
-            bar_sync(kBarRaw, NF);                  // raw rows of round b are in
-            if (b >= 2) bar_sync(kBarEmpty + q, ALL);   // the FFT threads are done with u[q]
+            named_bar_sync(kBarRaw, NF);                  // raw rows of round b are in
+            if (b >= 2) named_bar_sync(kBarEmpty + q, ALL);   // the FFT threads are done with u[q]
             const TIn *in = reinterpret_cast<const TIn *>(inbuf + q * BUF_BYTES);
             float2 *uq = u + q * NTR * ROW;
 #pragma unroll
@@ -309,8 +301,8 @@ ppf_ws_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const floa
                 for (int k = 0; k < T; ++k) acc = __ffma2_rn(h[k], win[(j + k) % T], acc);
                 uq[(j * IC + nl * kPols + p) * ROW + c] = acc;     // transform row j * IC + input
             }
-            bar_arrive(kBarFull + q, ALL);
-            bar_sync(kBarRaw, NF);                  // every FIR thread has read raw buffer q
+            named_bar_arrive(kBarFull + q, ALL);
+            named_bar_sync(kBarRaw, NF);                  // every FIR thread has read raw buffer q
             if (b + 2 < nrounds) stage(q, s0 + T - 1 + (b + 2) * kRound, kRound);
             cp_async_commit();
         }
@@ -325,7 +317,7 @@ ppf_ws_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const floa
         for (int b = 0; b < nrounds; ++b) {
             const int q = b & 1;
             float2 *uq = u + q * NTR * ROW;
-            bar_sync(kBarFull + q, ALL);            // FIR round b is in u[q]
+            named_bar_sync(kBarFull + q, ALL);            // FIR round b is in u[q]
 #pragma unroll
             for (int it = 0; it < W::ITERS; ++it) {
                 const int task = it * NF + t;
@@ -346,7 +338,7 @@ ppf_ws_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const floa
                 const int k1 = n2;
 #pragma unroll
                 for (int m = 0; m < R; ++m) v[m] = row[(R + 1) * k1 + m];
-                if (it == W::ITERS - 1 && b + 2 < nrounds) bar_arrive(kBarEmpty + q, ALL);
+                if (it == W::ITERS - 1 && b + 2 < nrounds) named_bar_arrive(kBarEmpty + q, ALL);
                 fft_reg<R>(v);
                 const int j = tr / IC, il = tr % IC;
                 const int s = s0 + b * kRound + j;

@@ -38,6 +38,25 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Named CTA barriers (hardware barriers with fixed arrival counts, like
+// __syncthreads, which uses id 0) for the warp-specialised kernels: FIR warps
+// and FFT warps hand rounds over with bar.arrive (producer) / bar.sync
+// (consumer); every participant of a barrier runs the same number of rounds.
+enum {
+    kBarRaw = 1,     // FIR threads: raw rows staged / consumed
+    kBarFft = 2,     // FFT threads among themselves
+    kBarFull = 3,    // FULL[0], FULL[1]: FIR round in the row buffer (ids 3, 4)
+    kBarEmpty = 5,   // EMPTY[0], EMPTY[1]: FFT threads done with it (ids 5, 6)
+};
+__device__ __forceinline__ void named_bar_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_bar_arrive(int id, int n)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 __device__ __forceinline__ float2 to_f2(short2 v) { return make_float2((float)v.x, (float)v.y); }
 __device__ __forceinline__ float2 to_f2(char2 v) { return make_float2((float)v.x, (float)v.y); }
 // 4-bit complex sample: real part in the high nibble, imaginary part in the low
