@@ -48,7 +48,7 @@ struct Handle {
 cudaError_t launch_ppf(const Handle &h, const void *raw, float2 *chan, cudaStream_t st);
 bool ppf_supported(int C, int T);
 
-// channelize_correct.cu (flags: [N][S] lost-data weights or null). A window
+// channelize_correct_impl.cuh (flags: [N][S] lost-data weights or null). A window
 // produces spectra [s_base, s_end) (s_base a multiple of 16) into an output
 // whose spectrum stride is s_out (spectrum s at s - s_base); null = the block.
 struct FWindow {

@@ -1,5 +1,5 @@
 // ppf_common.cuh -- CTA geometry and copy helpers shared by the polyphase
-// filter-bank kernels (ppf.cu: channelise only; channelize_correct.cu:
+// filter-bank kernels (ppf.cu: channelise only; channelize_correct_impl.cuh:
 // channelise + delay/bandpass correction in one pass).
 #pragma once
 #include <cuda_runtime.h>
