@@ -119,6 +119,8 @@ def test_ci4_end_to_end(precision, bound, C, S):
     (1, synth.CI8, 5, 64, 256, 16, 768, [3, 50]),
     (3, synth.CI16, 5, 48, 256, 16, 768, [0, 47]),
     (4, synth.CI8, 5, 64, 256, 16, 768, [63]),
+    (2, synth.CI16, 1, 3, 256, 8, 40, [0, 2]),          # 8 and 4 taps at 256 channels, ragged
+    (1, synth.CI8, 2, 2, 256, 4, 33, [1]),
     # the LOFAR 16-bit shape on 13 subbands: 64 rounds per CTA as in the benchmark
     (0, synth.CI16, 13, 64, 64, 16, 3072, [7, 40]),
 ])
