@@ -282,7 +282,8 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
 //    one channel, 256 contiguous bytes of the spectrum-blocked layout;
 //  * the FIR threads, which have the lighter share of the work, tabulate
 //    exp(i phi) x flag per (station, channel, spectrum) of their round into a
-//    double-buffered table; the FFT threads multiply in bandpass x gain (a
+//    double-buffered table (one __sincosf per owner and round, then rotations
+//    by exp(2 i step)); the FFT threads multiply in bandpass x gain (a
 //    per-CTA table) and the phase factor.
 template <int C>
 struct FusedWsCfg {
@@ -388,6 +389,9 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
         const int own_nc = tid % OWN, own_j0 = tid / OWN;
         const int own_n = min(n0 + own_nc / C, N - 1);
         const float2 pst = phase[((long long)sb * N + own_n) * C + own_nc % C];   // (phi0, step)
+        float sn2, cs2;
+        sincosf(2.f * pst.y, &sn2, &cs2);           // exp(2 i step): this owner's spectra are 2 apart
+        const float2 rot2 = make_float2(cs2, sn2);
         float2 h[T];
 #pragma unroll
         for (int k = 0; k < T; ++k) h[k] = make_float2(taps[k * C + c], taps[k * C + c]);
@@ -426,18 +430,23 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
             }
             // exp(i phi) x flag of this round: phi = phi0 + s step reduced to
             // [-pi, pi] (two-constant Cody-Waite split of 2 pi), then __sincosf
+            // exp(i phi) at this owner's first spectrum of the round (re-anchored
+            // every round), then rotations by exp(2 i step) for the next ones
             float2 *eq = et + q * ESZ + own_nc * EJ;
-#pragma unroll
-            for (int qq = 0; qq < kRound / 2; ++qq) {
-                const int j = own_j0 + 2 * qq;
-                const float phi = fmaf((float)(sr + j), pst.y, pst.x);
+            float2 e;
+            {
+                const float phi = fmaf((float)(sr + own_j0), pst.y, pst.x);
                 const float kq = rintf(phi * 0.15915494309189535f);
                 float r = fmaf(-kq, 6.28125f, phi);
                 r = fmaf(-kq, 1.9353071795864769e-3f, r);
-                float sn, cs;
-                __sincosf(r, &sn, &cs);
+                __sincosf(r, &e.y, &e.x);
+            }
+#pragma unroll
+            for (int qq = 0; qq < kRound / 2; ++qq) {
+                const int j = own_j0 + 2 * qq;
                 const float fw = flags ? flags[(long long)own_n * S + min(sr + j, S - 1)] : 1.f;
-                eq[j] = make_float2(cs * fw, sn * fw);
+                eq[j] = make_float2(e.x * fw, e.y * fw);
+                e = cmul(e, rot2);
             }
             named_bar_arrive(kBarFull + q, ALL);
             named_bar_sync(kBarRaw, NF);                // every FIR thread has read raw buffer q
