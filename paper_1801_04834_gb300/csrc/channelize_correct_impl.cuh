@@ -510,6 +510,10 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
                 }
                 if (it == W::ITEMS / 4 - 1 && b + 2 < nrounds) named_bar_arrive(kBarEmpty + q, ALL);
                 const int s = sr + j, i = 2 * n0 + il;
+                if (sr + kRound > s_end && s >= s_end) {   // only in the block's last round
+#pragma unroll
+                    for (int k2 = 0; k2 < R; ++k2) v[k2] = make_float2(0.f, 0.f);
+                }
                 if (i < I) {
                     if constexpr (OUT == 1) {
                         // one warp store = one station's 16 spectra x 2 pols of a channel (256 B)
@@ -520,7 +524,7 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
 #pragma unroll
                         for (int k2 = 0; k2 < R; ++k2) {
                             const int kout = k1 + R * ((k2 + R / 2) % R);
-                            out[kout * kstride] = s < s_end ? v[k2] : make_float2(0.f, 0.f);
+                            out[kout * kstride] = v[k2];
                         }
                     } else {
                         // planar: one warp store = 2 inputs x 16 spectra of one (channel, plane)
@@ -530,7 +534,7 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
 #pragma unroll
                         for (int k2 = 0; k2 < R; ++k2) {
                             const int kout = k1 + R * ((k2 + R / 2) % R);
-                            const float2 y = s < s_end ? v[k2] : make_float2(0.f, 0.f);
+                            const float2 y = v[k2];
                             const long long o = base + (long long)kout * planes * pstride;
                             if constexpr (OUT == 5) {
                                 float *out = reinterpret_cast<float *>(corr);
@@ -755,11 +759,15 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
             }
             if (b + 2 < nrounds) named_bar_arrive(kBarEmpty + q, ALL);
             const int s = sr + j;
+            if (sr + kRound > s_end && s >= s_end) {       // only in the block's last round
+#pragma unroll
+                for (int k2 = 0; k2 < R; ++k2) v[k2] = make_float2(0.f, 0.f);
+            }
             const long long base = (long long)sb * C * planes * pstride + (long long)i * s_out + (s - s_base);
 #pragma unroll
             for (int k2 = 0; k2 < R; ++k2) {
                 const int kout = k1 + R * ((k2 + R / 2) % R);
-                const float2 y = s < s_end ? v[k2] : make_float2(0.f, 0.f);
+                const float2 y = v[k2];
                 const long long o = base + (long long)kout * planes * pstride;
                 if constexpr (OUT == 5) {
                     float *out = reinterpret_cast<float *>(corr);
