@@ -58,3 +58,47 @@ def test_xstage_fp16_full_shape_sampled():
         e = _rel(vis[sb, k].double().cpu().numpy(), ref)
         assert e < 1e-4, (sb, k, e)
     c.close()
+
+
+def test_xstage_tf32_split_full_shape_sampled():
+    """The FP32-accurate tensor-core X-stage (hi/lo TF32 split) on FP32 planar
+    operands: 48 accumulator chains of 64 spectra summed in IEEE FP32 per
+    channel; held to the FP32 path's bound (1e-5)."""
+    c = _correlator(4)
+    I = 2 * N
+    g = torch.Generator(device="cuda").manual_seed(180104836)
+    ops = torch.zeros(c.corr_shape(), dtype=torch.float32, device="cuda")          # [SB][C][2][I_pad][S_pad]
+    ops[:, :, :, :I, :S] = torch.randn((SB, C, 2, I, S), generator=g, device="cuda") * 30.0
+    vis = c.correlate(ops)
+    torch.cuda.synchronize()
+    for sb, k in SAMPLES:
+        pl = ops[sb, k, :, :I, :S].double().cpu().numpy()
+        held = np.ascontiguousarray(pl.transpose(2, 1, 0)).reshape(1, 1, S, N, 2, 2)
+        ref = oracle.correlate(held)[0, 0]
+        e = _rel(vis[sb, k].double().cpu().numpy(), ref)
+        assert e < 1e-5, (sb, k, e)
+    c.close()
+
+
+def test_xstage_split_fp16_full_shape_sampled():
+    """Split FP16 operands (hi, lo planes) at the full shape: the represented
+    values hi + lo are exact inputs to the oracle; hi hi' + hi lo' + lo hi'
+    leaves out lo lo' (below 2^-22 relative), accumulation in FP32: 1e-4."""
+    c = _correlator(3)
+    I = 2 * N
+    g = torch.Generator(device="cuda").manual_seed(180104837)
+    x = torch.randn((SB, C, 2, I, S), generator=g, device="cuda") * 30.0
+    hi = x.half()
+    lo = (x - hi.float()).half()
+    ops = torch.zeros(c.corr_shape(), dtype=torch.float16, device="cuda")          # [SB][C][4][I_pad][S_pad]
+    ops[:, :, 0:2, :I, :S] = hi
+    ops[:, :, 2:4, :I, :S] = lo
+    vis = c.correlate(ops)
+    torch.cuda.synchronize()
+    for sb, k in SAMPLES:
+        pl = (ops[sb, k, 0:2, :I, :S].double() + ops[sb, k, 2:4, :I, :S].double()).cpu().numpy()
+        held = np.ascontiguousarray(pl.transpose(2, 1, 0)).reshape(1, 1, S, N, 2, 2)
+        ref = oracle.correlate(held)[0, 0]
+        e = _rel(vis[sb, k].double().cpu().numpy(), ref)
+        assert e < 1e-4, (sb, k, e)
+    c.close()
