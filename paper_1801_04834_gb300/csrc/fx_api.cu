@@ -47,7 +47,7 @@ namespace fxi {
 bool xstage_supported(const Handle &h)
 {
     if (h.p.precision == FX_F32) return true;
-    if (h.p.precision == FX_TF32_SPLIT) return h.I_pad <= 128;
+    if (h.p.precision == FX_TF32_SPLIT) return xtf32_supported(h.I_pad, h.S_pad);
     int rl, stg;
     unsigned sb;
     return xtc_plan(h, &rl, &stg, &sb);
@@ -57,9 +57,7 @@ cudaError_t launch_xstage(const Handle &h, const void *corr, float2 *vis, cudaSt
 {
     switch (h.p.precision) {
     case FX_F32: return launch_xcorr_f32(h, static_cast<const float2 *>(corr), vis, st, accumulate);
-    case FX_TF32_SPLIT:
-        if (accumulate) return cudaErrorNotSupported;
-        return launch_xcorr_tf32(h, static_cast<const float *>(corr), vis, st);
+    case FX_TF32_SPLIT: return launch_xcorr_tf32(h, static_cast<const float *>(corr), vis, st, accumulate);
     default: return launch_xcorr_tc(h, corr, vis, st, accumulate);
     }
 }
@@ -114,8 +112,8 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
     if (!is_pow2(scale)) return fail(FX_ERR_INVALID, "operand_scale must be a power of two");
     if ((p.precision == FX_F32 || p.precision == FX_TF32_SPLIT) && scale != 1.f)
         return fail(FX_ERR_INVALID, "operand_scale applies to FP16/BF16 only");
-    if (p.precision == FX_TF32_SPLIT && p.n_stations > 64)
-        return fail(FX_ERR_UNSUPPORTED, "FX_TF32_SPLIT handles at most 64 stations");
+    if (p.precision == FX_TF32_SPLIT && p.n_stations > 512)
+        return fail(FX_ERR_UNSUPPORTED, "FX_TF32_SPLIT handles at most 512 stations");
     const long long I = 2LL * p.n_stations;
     const long long S = p.n_spectra;
     const long long SB = p.n_subbands;

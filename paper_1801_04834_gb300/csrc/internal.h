@@ -100,7 +100,9 @@ cudaError_t launch_beamform(const Handle &h, const void *corr, int n_beams, cons
                             const float *weights, int mode, int tint, float *out, cudaStream_t st);
 
 // xcorr_tf32.cu (FX_TF32_SPLIT)
-cudaError_t launch_xcorr_tf32(const Handle &h, const float *corr, float2 *vis, cudaStream_t st);
+bool xtf32_supported(int I_pad, int S_pad);
+cudaError_t launch_xcorr_tf32(const Handle &h, const float *corr, float2 *vis, cudaStream_t st,
+                             bool accumulate = false);    // accumulate: add to vis
 
 // probe.cu
 cudaError_t launch_ffma_probe(int iterations, int blocks, float *sink, cudaStream_t st);

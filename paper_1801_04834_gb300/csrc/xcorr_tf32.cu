@@ -1,6 +1,7 @@
-// xcorr_tf32.cu -- FP32-accurate X-stage on the tcgen05 tensor cores:
-// FP32 corrected samples split in the kernel into hi + lo TF32 parts,
-// V ~ hi hi' + hi lo' + lo hi' (lo lo' dropped) with FP32 accumulation in TMEM.
+// xcorr_tf32.cu -- FP32-accurate X-stage on the tcgen05 tensor cores, any
+// station count: FP32 corrected samples split in the kernel into hi + lo TF32
+// parts, V ~ hi hi' + hi lo' + lo hi' (lo lo' dropped), FP32 accumulation in
+// TMEM, chunk sums added in IEEE FP32.
 //
 // Paper, Sec. "Signal processing with GPU kernels": the correlator forms
 // V[a][b] = sum_s Y[s][a] conj(Y[s][b]) for all input pairs and integrates over
@@ -9,37 +10,66 @@
 // a TF32 value and lo = x - hi is exact in FP32, so x = hi + lo and the
 // dropped lo lo' term is below 2^-20 of each product, which keeps the FP32
 // path's error bound while running on the tensor cores.
-// On planar operands (re plane R, im plane J) as in the FP16 X-stage:
-//   Re V = R R^T + J J^T          Im V = J R^T - R J^T
-// each product expanded into its three hi/lo terms (12 MMAs per K-step).
 //
-// Layout: corr [SB][C][2][I_pad][S_pad] FP32 (spectra contiguous), I_pad <= 128
-// (up to 64 stations): one work item per (subband, channel), all inputs in one
-// 128-row tile, so A and B are the same tile (M = 128, N = I_pad, K = 8).
-// Stage = 32 spectra (128-byte rows, 128-byte swizzle) of both planes: 32 KB
-// of hi (converted in place) + 32 KB of lo, ring of 3.
+// Complex product as one real MMA of twice the width. With planar operands
+// (re plane R, im plane J) and, for the column inputs, three consecutive
+// shared-memory planes [R; J; -R] of n rows each,
+//   D[a][0:n)  += R_a . R_b + J_a . J_b   = Re V[a][b]
+//   D[a][n:2n) += R_a . J_b - J_a . R_b   = -Im V[a][b]
+// come from two MMAs of N = 2n: A = R rows against B = [R; J] (planes 0-1),
+// and A = J rows against B = [J; -R] (planes 1-2). Each side is split into
+// hi and lo, so one K-step (8 spectra) is six MMAs of M = 128, N = 2n, K = 8:
+// hi.[hi], hi.[lo], lo.[hi] for the R rows and the J rows. At n = 128 each MMA
+// reads 4 KB of A and 8 KB of B from shared memory per 128 x 256 x 8 product,
+// three quarters of the shared-memory bytes per flop of two N = 128 MMAs.
 //
-// Warp roles (persistent, one CTA per SM, 320 threads):
-//   warp 0     TMA producer
-//   warp 1     TMEM allocator + MMA issuer (tcgen05.mma kind::tf32)
-//   warps 2-5  epilogue: tcgen05.ld of their TMEM lane quadrant, upper triangle
-//   warps 6-9  converter: hi = x & ~0x1FFF written in place, lo = x - hi into
-//              the stage's lo half, then a proxy fence so the tensor cores see
-//              the generic-proxy writes
-// Every mbarrier wait is bounded; on expiry the role is recorded in the status
-// word, all roles leave, in-flight copies and MMAs are drained (bounded) and
-// TMEM is freed.
+// Work items. Rows come in blocks of 128 inputs (M = 128); an item is
+// (subband x channel, row block, column block) over the upper block
+// triangle: the diagonal item of a row block covers columns
+// [row0, row0 + min(128, I_pad - row0)), off-diagonal items cover the columns
+// right of it in tiles of at most NT (64 or 128) inputs. 64 stations (128
+// inputs) is one diagonal item per channel; 76 stations (160 inputs) is a
+// 128-column diagonal item, a 32-column off-diagonal item and a 32-row
+// diagonal item.
+//
+// Shared memory, one stage = 16 spectra (64-byte rows, 64-byte swizzle):
+//   B region: planes hi R, hi J, -hi R, lo R, lo J, -lo R of n rows each
+//             (plane pitch n x 64 bytes). On a diagonal item the A operands
+//             are planes 0, 1, 3, 4 of the same region read as 128-row tiles
+//             (rows past n are other planes' data and only reach
+//             accumulator rows the epilogue ignores; the region is sized so
+//             these reads stay inside the stage).
+//   A region (off-diagonal items): hi R, hi J, lo R, lo J of the 128 row
+//             inputs, 8 KB each, before the B region.
+// TMA writes the raw FP32 R and J rows into the hi planes; converter warps
+// split them in place (hi), write lo and the negated planes, fence the async
+// proxy and release the stage to the MMA thread.
 //
 // Accumulation. The tensor core's FP32 accumulator does not round each
 // addition to nearest, so a long chain of MMAs into one accumulator drifts
-// (measured: 2.5e-5 normwise after 768 spectra, growing with the chain). The
-// accumulator is therefore restarted every kChunk stages (64 spectra) and the
-// epilogue adds the chunk sums into the visibilities in IEEE FP32 (the rows
-// of one channel stay in L2 while its chunks are summed).
+// (about 2^-24 of the running value per MMA). The accumulator is restarted
+// every `chunk` stages (64 spectra by default); the epilogue writes the first
+// chunk's sums and adds every later chunk's into the visibilities with
+// vector FP32 reductions in L2 (red.global.add.v4.f32, round to nearest; no
+// read back into the SM, so the epilogue never waits on memory). Each
+// visibility entry is owned by one lane of one CTA, which issues its chunks in
+// order, so the sum order is fixed and results are reproducible.
+//
+// Warp roles (persistent, one CTA per SM, 448 threads):
+//   warp 0      TMA producer
+//   warp 1      TMEM allocator + MMA issuer (tcgen05.mma kind::tf32)
+//   warps 2-9   epilogue: two warps per TMEM lane quadrant (warp % 4), each
+//               taking every other 32-column group of the upper triangle
+//   warps 10-13 converter
+// Two accumulators of 256 columns (double buffered) fill the 512 TMEM columns.
+// Every mbarrier wait is bounded; on expiry the role is recorded in the status
+// word, all roles leave, in-flight copies and MMAs are drained (bounded) and
+// TMEM is freed.
 #include <cuda.h>
 
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "internal.h"
 #include "tc_ptx.cuh"
@@ -49,25 +79,36 @@ namespace {
 
 using namespace tc;
 
-constexpr int kT3Threads = 320;
-constexpr int kT3Stages = 3;
-constexpr int kT3K = 32;                              // spectra per stage (128-byte FP32 rows)
-constexpr unsigned kT3Plane = 128u * 128u;            // 128 rows x 128 B
-constexpr unsigned kT3Hi = 2u * kT3Plane;             // re + im, hi (converted in place)
-constexpr unsigned kT3Stage = 2u * kT3Hi;             // hi + lo
+constexpr int kT3Threads = 448;
+constexpr int kT3EpiWarps = 8;
+constexpr int kT3ConvWarp0 = 2 + kT3EpiWarps;
+constexpr int kT3K = 16;                              // spectra per stage (64-byte FP32 rows)
+constexpr unsigned kT3RowBytes = 64;
+constexpr unsigned kT3APlane = 128u * kT3RowBytes;    // one 128-row plane: 8 KB
+constexpr unsigned kT3BRegionMin = 6u * kT3APlane;    // diagonal item at n = 128: 48 KB
+constexpr int kT3MaxStages = 6;
+constexpr int kT3MaxItems = 64;                       // items per channel
 constexpr int kT3TmemCols = 512;
-constexpr int kT3Bars = 4 * kT3Stages + 5;            // full, conv, empty per stage; accf 2, acce 2, drain
-constexpr int kChunk = 2;                             // stages per accumulator chain (64 spectra)
+constexpr int kT3AccCols = 256;
+constexpr int kT3Bars = 3 * kT3MaxStages + 5;         // full, conv, empty per stage; accf 2, acce 2, drain
+constexpr unsigned kT3SmemBudget = 200u * 1024u;
 
 struct T3Params {
-    CUtensorMap map;          // 3-D (spectrum, input, sb*C*2 + plane), box {32, 128, 1}
+    CUtensorMap map128;       // 3-D (spectrum, input, sb*C*2 + plane), box {16, 128, 1}
+    CUtensorMap map16;        // same tensor, box {16, 16, 1}
+    int4 items[kT3MaxItems];  // per channel: (row0, col0, n, diagonal)
     float2 *vis;
     int *status;
-    long long n_items;        // SB * C
-    int N, I_pad, nk;         // stations, padded inputs, stages per item (a multiple of kChunk)
+    long long n_items;        // SB * C * ipc
     long long B;              // baselines
     long long timeout_cycles;
+    int ipc;                  // items per channel
+    int N, nk, chunk;         // stations, stages per item, stages per accumulator chain
+    int stages;
+    unsigned stage_bytes;
+    unsigned a_off;           // byte offset of the B region when an A region precedes it
     int no_tma;               // failure-detection test hook: issue no loads
+    int accumulate;           // add every chunk to vis (also the first)
 };
 
 __device__ __forceinline__ bool t3wait(unsigned bar, unsigned parity, volatile int *abort_flag, const T3Params &P,
@@ -86,6 +127,14 @@ __device__ __forceinline__ bool t3wait(unsigned bar, unsigned parity, volatile i
     return true;
 }
 
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle (8-row atoms of
+// 512 bytes, SBO = 512), LBO unused for this layout, descriptor version 1.
+__device__ __forceinline__ unsigned long long sdesc64(unsigned addr)
+{
+    return (unsigned long long)((addr & 0x3FFFF) >> 4) | (1ull << 16) | ((unsigned long long)(512 >> 4) << 32) |
+           (1ull << 46) | (4ull << 61);
+}
+
 // Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, M = 128.
 __device__ __forceinline__ unsigned idesc_tf32(int n, bool neg_a)
 {
@@ -102,6 +151,49 @@ __device__ __forceinline__ void mma_tf32(unsigned d_tmem, unsigned long long ade
                  : "memory");
 }
 
+// Vector FP32 reduction into global memory (performed in L2, round to nearest).
+__device__ __forceinline__ void red_add4(float2 *addr, float4 v)
+{
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ unsigned hi_bits(unsigned x) { return x & 0xFFFFE000u; }
+__device__ __forceinline__ unsigned lo_bits(unsigned x, unsigned h)
+{
+    return __float_as_uint(__uint_as_float(x) - __uint_as_float(h));
+}
+
+// Split one R plane and one J plane of `rows` rows in place into hi, writing
+// lo (and for the column operand the negated planes) at the given offsets.
+// All planes share the 64-byte swizzle phase, so equal byte offsets hold the
+// same logical element.
+__device__ __forceinline__ void convert_pair(unsigned char *r_plane, unsigned char *j_plane, unsigned char *r_lo,
+                                             unsigned char *j_lo, unsigned char *r_neg_hi, unsigned char *r_neg_lo,
+                                             int rows, int t)
+{
+    const int nq = rows * (int)(kT3RowBytes / 16);
+    for (int q = t; q < nq; q += 128) {
+        const uint4 x = reinterpret_cast<const uint4 *>(r_plane)[q];
+        const uint4 y = reinterpret_cast<const uint4 *>(j_plane)[q];
+        uint4 xh, xl, yh, yl;
+        xh.x = hi_bits(x.x); xh.y = hi_bits(x.y); xh.z = hi_bits(x.z); xh.w = hi_bits(x.w);
+        yh.x = hi_bits(y.x); yh.y = hi_bits(y.y); yh.z = hi_bits(y.z); yh.w = hi_bits(y.w);
+        xl.x = lo_bits(x.x, xh.x); xl.y = lo_bits(x.y, xh.y); xl.z = lo_bits(x.z, xh.z); xl.w = lo_bits(x.w, xh.w);
+        yl.x = lo_bits(y.x, yh.x); yl.y = lo_bits(y.y, yh.y); yl.z = lo_bits(y.z, yh.z); yl.w = lo_bits(y.w, yh.w);
+        reinterpret_cast<uint4 *>(r_plane)[q] = xh;
+        reinterpret_cast<uint4 *>(j_plane)[q] = yh;
+        reinterpret_cast<uint4 *>(r_lo)[q] = xl;
+        reinterpret_cast<uint4 *>(j_lo)[q] = yl;
+        if (r_neg_hi) {
+            const unsigned s = 0x80000000u;
+            reinterpret_cast<uint4 *>(r_neg_hi)[q] = make_uint4(xh.x ^ s, xh.y ^ s, xh.z ^ s, xh.w ^ s);
+            reinterpret_cast<uint4 *>(r_neg_lo)[q] = make_uint4(xl.x ^ s, xl.y ^ s, xl.z ^ s, xl.w ^ s);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kT3Threads, 1) xcorr_tf32_kernel(const __grid_constant__ T3Params P)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -109,27 +201,27 @@ __global__ void __launch_bounds__(kT3Threads, 1) xcorr_tf32_kernel(const __grid_
     const unsigned pad = (1024 - (base_u32 & 1023)) & 1023;
     unsigned char *tiles = smem_raw + pad;
     const unsigned tiles_u32 = base_u32 + pad;
-    unsigned char *ctrl = tiles + kT3Stages * kT3Stage;
+    unsigned char *ctrl = tiles + (size_t)P.stages * P.stage_bytes;
     const unsigned bar0 = smem_u32(ctrl);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
-    auto conv_bar = [&](int s) { return bar0 + 8u * (kT3Stages + s); };
-    auto empty_bar = [&](int s) { return bar0 + 8u * (2 * kT3Stages + s); };
-    auto accf_bar = [&](int b) { return bar0 + 8u * (3 * kT3Stages + b); };
-    auto acce_bar = [&](int b) { return bar0 + 8u * (3 * kT3Stages + 2 + b); };
-    const unsigned drain_bar = bar0 + 8u * (3 * kT3Stages + 4);
+    auto conv_bar = [&](int s) { return bar0 + 8u * (kT3MaxStages + s); };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (2 * kT3MaxStages + s); };
+    auto accf_bar = [&](int b) { return bar0 + 8u * (3 * kT3MaxStages + b); };
+    auto acce_bar = [&](int b) { return bar0 + 8u * (3 * kT3MaxStages + 2 + b); };
+    const unsigned drain_bar = bar0 + 8u * (3 * kT3MaxStages + 4);
     unsigned *tmem_slot = reinterpret_cast<unsigned *>(ctrl + 8 * kT3Bars);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kT3Stages; ++s) {
+        for (int s = 0; s < P.stages; ++s) {
             mbar_init(full_bar(s), 1);
-            mbar_init(conv_bar(s), 4);
+            mbar_init(conv_bar(s), 4);              // one arrival per converter warp
             mbar_init(empty_bar(s), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(accf_bar(b), 1);
-            mbar_init(acce_bar(b), 4);
+            mbar_init(acce_bar(b), kT3EpiWarps);    // one arrival per epilogue warp
         }
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
@@ -146,7 +238,7 @@ __global__ void __launch_bounds__(kT3Threads, 1) xcorr_tf32_kernel(const __grid_
     __syncthreads();
     tc_fence_after();
     const unsigned tmem_base = *tmem_slot;
-    const int ncols = P.I_pad;                        // N of every MMA and accumulator width
+    const int n_chunks = P.nk / P.chunk;
 
     if (warp == 0) {
         // ================= TMA producer =================
@@ -154,24 +246,41 @@ __global__ void __launch_bounds__(kT3Threads, 1) xcorr_tf32_kernel(const __grid_
             long long it = 0;
             bool ok = true;
             for (long long w = blockIdx.x; w < P.n_items && ok; w += gridDim.x) {
+                const int4 itm = P.items[(int)(w % P.ipc)];
+                const long long gch = w / P.ipc;
+                const int row0 = itm.x, col0 = itm.y, n = itm.z;
+                const bool diag = itm.w != 0;
+                const bool full_diag = diag && n == 128;
+                const unsigned boff = diag ? 0u : P.a_off;
+                const unsigned tx = (diag ? 0u : 2u * kT3APlane) + 2u * (unsigned)n * kT3RowBytes;
                 for (int kc = 0; kc < P.nk; ++kc, ++it) {
-                    const int s = (int)(it % kT3Stages);
-                    if (!t3wait(empty_bar(s), (unsigned)((it / kT3Stages) & 1) ^ 1u, abort_flag, P, 1)) {
+                    const int s = (int)(it % P.stages);
+                    if (!t3wait(empty_bar(s), (unsigned)((it / P.stages) & 1) ^ 1u, abort_flag, P, 1)) {
                         ok = false;
                         break;
                     }
                     if (P.no_tma) continue;
-                    mbar_arrive_expect_tx(full_bar(s), kT3Hi);
-                    const unsigned dst = tiles_u32 + (unsigned)s * kT3Stage;
-                    for (int pl = 0; pl < 2; ++pl)
-                        tma_load_3d(dst + (unsigned)pl * kT3Plane, &P.map, full_bar(s), kc * kT3K, 0,
-                                    (int)(w * 2 + pl));
+                    mbar_arrive_expect_tx(full_bar(s), tx);
+                    const unsigned dst = tiles_u32 + (unsigned)s * P.stage_bytes;
+                    for (int pl = 0; pl < 2; ++pl) {
+                        const int z = (int)(gch * 2 + pl);
+                        if (!diag)         // row inputs: A region planes 0 (R) and 1 (J)
+                            tma_load_3d(dst + (unsigned)pl * kT3APlane, &P.map128, full_bar(s), kc * kT3K, row0, z);
+                        const unsigned bdst = dst + boff + (unsigned)pl * (unsigned)n * kT3RowBytes;
+                        if (full_diag) {
+                            tma_load_3d(bdst, &P.map128, full_bar(s), kc * kT3K, col0, z);
+                        } else {
+                            for (int r = 0; r < n; r += 16)
+                                tma_load_3d(bdst + (unsigned)r * kT3RowBytes, &P.map16, full_bar(s), kc * kT3K,
+                                            col0 + r, z);
+                        }
+                    }
                 }
             }
             if (!ok && !P.no_tma) {
-                const long long first = it > kT3Stages ? it - kT3Stages : 0;
+                const long long first = it > P.stages ? it - P.stages : 0;
                 for (long long u = first; u < it; ++u)
-                    drain_wait(full_bar((int)(u % kT3Stages)), (unsigned)((u / kT3Stages) & 1), P.timeout_cycles);
+                    drain_wait(full_bar((int)(u % P.stages)), (unsigned)((u / P.stages) & 1), P.timeout_cycles);
             }
         }
     } else if (warp == 1) {
@@ -179,55 +288,55 @@ __global__ void __launch_bounds__(kT3Threads, 1) xcorr_tf32_kernel(const __grid_
         if (lane == 0) {
             long long it = 0, acc_it = 0;
             bool ok = true, issued = false;
-            const unsigned idesc = idesc_tf32(ncols, false);
-            const unsigned idesc_neg = idesc_tf32(ncols, true);
             for (long long w = blockIdx.x; w < P.n_items && ok; w += gridDim.x) {
-              for (int ch = 0; ch < P.nk / kChunk && ok; ++ch, ++acc_it) {
-                const int ab = (int)(acc_it & 1);
-                if (!t3wait(acce_bar(ab), (unsigned)((acc_it >> 1) & 1) ^ 1u, abort_flag, P, 2)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const unsigned d_re = tmem_base + (unsigned)(ab * 256);
-                const unsigned d_im = d_re + 128;
-                for (int kc = 0; kc < kChunk; ++kc, ++it) {
-                    const int s = (int)(it % kT3Stages);
-                    if (!t3wait(conv_bar(s), (unsigned)((it / kT3Stages) & 1), abort_flag, P, 2)) {
+                const int4 itm = P.items[(int)(w % P.ipc)];
+                const int n = itm.z;
+                const bool diag = itm.w != 0;
+                const unsigned pitch = (unsigned)n * kT3RowBytes;
+                const unsigned idesc = idesc_tf32(2 * n, false);
+                for (int ch = 0; ch < n_chunks && ok; ++ch, ++acc_it) {
+                    const int ab = (int)(acc_it & 1);
+                    if (!t3wait(acce_bar(ab), (unsigned)((acc_it >> 1) & 1) ^ 1u, abort_flag, P, 2)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const unsigned hi = tiles_u32 + (unsigned)s * kT3Stage;
-                    const unsigned lo = hi + kT3Hi;
+                    const unsigned d = tmem_base + (unsigned)(ab * kT3AccCols);
+                    for (int kc = 0; kc < P.chunk; ++kc, ++it) {
+                        const int s = (int)(it % P.stages);
+                        if (!t3wait(conv_bar(s), (unsigned)((it / P.stages) & 1), abort_flag, P, 2)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const unsigned st = tiles_u32 + (unsigned)s * P.stage_bytes;
+                        const unsigned bb = diag ? st : st + P.a_off;
+                        // A planes: hi R, hi J, lo R, lo J
+                        const unsigned a_hr = diag ? bb : st;
+                        const unsigned a_hj = diag ? bb + pitch : st + kT3APlane;
+                        const unsigned a_lr = diag ? bb + 3 * pitch : st + 2 * kT3APlane;
+                        const unsigned a_lj = diag ? bb + 4 * pitch : st + 3 * kT3APlane;
 #pragma unroll
-                    for (int kk = 0; kk < kT3K / 8; ++kk) {     // 8 FP32 = 32 bytes per K-step
-                        const unsigned acc = (kc | kk) ? 1u : 0u;
-                        const unsigned long long rh = smem_desc(hi + kk * 32);
-                        const unsigned long long jh = smem_desc(hi + kT3Plane + kk * 32);
-                        const unsigned long long rl = smem_desc(lo + kk * 32);
-                        const unsigned long long jl = smem_desc(lo + kT3Plane + kk * 32);
-                        // Re V = R R^T + J J^T
-                        mma_tf32(d_re, rh, rh, idesc, acc);
-                        mma_tf32(d_re, jh, jh, idesc, 1u);
-                        mma_tf32(d_re, rh, rl, idesc, 1u);
-                        mma_tf32(d_re, jh, jl, idesc, 1u);
-                        mma_tf32(d_re, rl, rh, idesc, 1u);
-                        mma_tf32(d_re, jl, jh, idesc, 1u);
-                        // Im V = J R^T - R J^T
-                        mma_tf32(d_im, jh, rh, idesc, acc);
-                        mma_tf32(d_im, rh, jh, idesc_neg, 1u);
-                        mma_tf32(d_im, jh, rl, idesc, 1u);
-                        mma_tf32(d_im, rh, jl, idesc_neg, 1u);
-                        mma_tf32(d_im, jl, rh, idesc, 1u);
-                        mma_tf32(d_im, rl, jh, idesc_neg, 1u);
+                        for (int kk = 0; kk < kT3K / 8; ++kk) {    // 8 FP32 = 32 bytes per K-step
+                            const unsigned acc = (kc | kk) ? 1u : 0u;
+                            const unsigned o = (unsigned)kk * 32u;
+                            const unsigned long long b_h0 = sdesc64(bb + o);               // [hi R; hi J]
+                            const unsigned long long b_h1 = sdesc64(bb + pitch + o);       // [hi J; -hi R]
+                            const unsigned long long b_l0 = sdesc64(bb + 3 * pitch + o);   // [lo R; lo J]
+                            const unsigned long long b_l1 = sdesc64(bb + 4 * pitch + o);   // [lo J; -lo R]
+                            mma_tf32(d, sdesc64(a_hr + o), b_h0, idesc, acc);
+                            mma_tf32(d, sdesc64(a_hj + o), b_h1, idesc, 1u);
+                            mma_tf32(d, sdesc64(a_hr + o), b_l0, idesc, 1u);
+                            mma_tf32(d, sdesc64(a_hj + o), b_l1, idesc, 1u);
+                            mma_tf32(d, sdesc64(a_lr + o), b_h0, idesc, 1u);
+                            mma_tf32(d, sdesc64(a_lj + o), b_h1, idesc, 1u);
+                        }
+                        issued = true;
+                        mma_commit(empty_bar(s));
                     }
-                    issued = true;
-                    mma_commit(empty_bar(s));
+                    if (!ok) break;
+                    mma_commit(accf_bar(ab));
                 }
-                if (!ok) break;
-                mma_commit(accf_bar(ab));
-              }
             }
             if (!ok && issued) {
                 mma_commit(drain_bar);
@@ -235,109 +344,94 @@ __global__ void __launch_bounds__(kT3Threads, 1) xcorr_tf32_kernel(const __grid_
             }
         }
         __syncwarp();
-    } else if (warp >= 6) {
-        // ================= converter (warps 6..9) =================
-        const int ct = threadIdx.x - 6 * 32;            // 0..127
+    } else if (warp >= kT3ConvWarp0) {
+        // ================= converter (warps 10..13) =================
+        const int ct = threadIdx.x - kT3ConvWarp0 * 32; // 0..127
         long long it = 0;
         bool ok = true;
         for (long long w = blockIdx.x; w < P.n_items && ok; w += gridDim.x) {
+            const int4 itm = P.items[(int)(w % P.ipc)];
+            const int n = itm.z;
+            const bool diag = itm.w != 0;
+            const unsigned pitch = (unsigned)n * kT3RowBytes;
             for (int kc = 0; kc < P.nk; ++kc, ++it) {
-                const int s = (int)(it % kT3Stages);
-                const bool got = t3wait(full_bar(s), (unsigned)((it / kT3Stages) & 1), abort_flag, P, 4);
+                const int s = (int)(it % P.stages);
+                const bool got = t3wait(full_bar(s), (unsigned)((it / P.stages) & 1), abort_flag, P, 4);
                 if (!__all_sync(0xffffffffu, got)) {
                     ok = false;
                     break;
                 }
-                uint4 *h4 = reinterpret_cast<uint4 *>(tiles + (size_t)s * kT3Stage);
-                uint4 *l4 = reinterpret_cast<uint4 *>(tiles + (size_t)s * kT3Stage + kT3Hi);
-#pragma unroll 4
-                for (int q = ct; q < (int)(kT3Hi / 16); q += 128) {
-                    const uint4 x = h4[q];
-                    uint4 hv, lv;
-                    hv.x = x.x & 0xFFFFE000u;
-                    hv.y = x.y & 0xFFFFE000u;
-                    hv.z = x.z & 0xFFFFE000u;
-                    hv.w = x.w & 0xFFFFE000u;
-                    lv.x = __float_as_uint(__uint_as_float(x.x) - __uint_as_float(hv.x));
-                    lv.y = __float_as_uint(__uint_as_float(x.y) - __uint_as_float(hv.y));
-                    lv.z = __float_as_uint(__uint_as_float(x.z) - __uint_as_float(hv.z));
-                    lv.w = __float_as_uint(__uint_as_float(x.w) - __uint_as_float(hv.w));
-                    h4[q] = hv;
-                    l4[q] = lv;
-                }
+                unsigned char *st = tiles + (size_t)s * P.stage_bytes;
+                unsigned char *bb = diag ? st : st + P.a_off;
+                if (!diag)   // row inputs: hi in place, lo into planes 2 and 3 of the A region
+                    convert_pair(st, st + kT3APlane, st + 2 * kT3APlane, st + 3 * kT3APlane, nullptr, nullptr, 128,
+                                 ct);
+                convert_pair(bb, bb + pitch, bb + 3 * pitch, bb + 4 * pitch, bb + 2 * pitch, bb + 5 * pitch, n, ct);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(conv_bar(s));
             }
         }
     } else {
-        // ================= epilogue (warps 2..5) =================
-        const int qd = warp & 3;
+        // ================= epilogue (warps 2..9) =================
+        const int qd = warp & 3;                        // TMEM lane quadrant
+        const int half = (warp - 2) >> 2;               // which 32-column groups
         long long acc_it = 0;
         bool live = true;
         for (long long w = blockIdx.x; w < P.n_items && live; w += gridDim.x) {
-          for (int ch = 0; ch < P.nk / kChunk; ++ch, ++acc_it) {
-            const int ab = (int)(acc_it & 1);
-            const bool got = t3wait(accf_bar(ab), (unsigned)((acc_it >> 1) & 1), abort_flag, P, 3);
-            if (!__all_sync(0xffffffffu, got)) {
-                live = false;
-                break;
-            }
-            tc_fence_after();
-            const int ia = 32 * qd + lane;               // this lane's row input
+            const int4 itm = P.items[(int)(w % P.ipc)];
+            const long long gch = w / P.ipc;
+            const int row0 = itm.x, col0 = itm.y, n = itm.z;
+            const int ia = row0 + 32 * qd + lane;        // this lane's row input
             const int i = ia >> 1, p = ia & 1;
-            const int i_warp_min = (32 * qd) >> 1;
-            const unsigned t_re = tmem_base + ((unsigned)(32 * qd) << 16) + (unsigned)(ab * 256);
-            const unsigned t_im = t_re + 128;
-            float2 *vrow = P.vis + w * P.B * 4;
-            // two 16-column chunks at a time: TMEM loads and the loads of the
-            // running sums are all issued before any add or store
-            const int ncc = ncols / 16;
-            for (int cc0 = 0; cc0 < ncc; cc0 += 2) {
-                if (8 * cc0 >= P.N) break;
-                if (8 * cc0 + 15 < i_warp_min) continue;    // both chunks below the diagonal for this warp
-                float re[2][16], im[2][16];
-                float4 old[2][8];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    if (cc0 + u < ncc) {
-                        tmem_ld16(t_re + 16 * (cc0 + u), re[u]);
-                        tmem_ld16(t_im + 16 * (cc0 + u), im[u]);
-                    }
+            const int i_warp_min = (row0 + 32 * qd) >> 1;
+            const int ncc = n / 16;
+            float2 *vrow = P.vis + gch * P.B * 4;
+            for (int ch = 0; ch < n_chunks; ++ch, ++acc_it) {
+                const int ab = (int)(acc_it & 1);
+                const bool got = t3wait(accf_bar(ab), (unsigned)((acc_it >> 1) & 1), abort_flag, P, 3);
+                if (!__all_sync(0xffffffffu, got)) {
+                    live = false;
+                    break;
                 }
-                if (ch > 0) {
+                tc_fence_after();
+                const bool store = (ch == 0) && !P.accumulate;
+                const unsigned t = tmem_base + ((unsigned)(32 * qd) << 16) + (unsigned)(ab * kT3AccCols);
+                if (i_warp_min < P.N) {
+                    for (int cc = 2 * half; cc < ncc; cc += 4) {
+                        const int j0 = (col0 >> 1) + 8 * cc;     // first station of this pair of chunks
+                        if (j0 >= P.N) break;
+                        if (j0 + 15 < i_warp_min) continue;     // both chunks below the diagonal
+                        float re[2][16], ni[2][16];
 #pragma unroll
-                    for (int u = 0; u < 2; ++u)
-#pragma unroll
-                        for (int jj = 0; jj < 8; ++jj) {
-                            const int j = 8 * (cc0 + u) + jj;
-                            if (cc0 + u < ncc && i <= j && j < P.N)
-                                old[u][jj] = *reinterpret_cast<const float4 *>(
-                                    vrow + ((long long)j * (j + 1) / 2 + i) * 4 + 2 * p);
-                        }
-                }
-                tmem_ld_wait();
-#pragma unroll
-                for (int u = 0; u < 2; ++u)
-#pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) {
-                        const int j = 8 * (cc0 + u) + jj;
-                        if (cc0 + u < ncc && i <= j && j < P.N) {
-                            float4 v = make_float4(re[u][2 * jj], im[u][2 * jj], re[u][2 * jj + 1], im[u][2 * jj + 1]);
-                            if (ch > 0) {                // add this chunk to the sum so far (FP32, RN)
-                                v.x += old[u][jj].x;
-                                v.y += old[u][jj].y;
-                                v.z += old[u][jj].z;
-                                v.w += old[u][jj].w;
+                        for (int u = 0; u < 2; ++u) {
+                            if (cc + u < ncc) {
+                                tmem_ld16(t + 16 * (cc + u), re[u]);
+                                tmem_ld16(t + (unsigned)n + 16 * (cc + u), ni[u]);
                             }
-                            *reinterpret_cast<float4 *>(vrow + ((long long)j * (j + 1) / 2 + i) * 4 + 2 * p) = v;
                         }
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int u = 0; u < 2; ++u)
+#pragma unroll
+                            for (int jj = 0; jj < 8; ++jj) {
+                                const int j = j0 + 8 * u + jj;
+                                if (cc + u < ncc && i <= j && j < P.N) {
+                                    const float4 v = make_float4(re[u][2 * jj], -ni[u][2 * jj], re[u][2 * jj + 1],
+                                                                 -ni[u][2 * jj + 1]);
+                                    float2 *dst = vrow + ((long long)j * (j + 1) / 2 + i) * 4 + 2 * p;
+                                    if (store)
+                                        *reinterpret_cast<float4 *>(dst) = v;
+                                    else
+                                        red_add4(dst, v);
+                                }
+                            }
                     }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce_bar(ab));
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acce_bar(ab));
-          }
         }
     }
 
@@ -368,35 +462,85 @@ EncodeTiledFn t3_encode_fn()
     return fn;
 }
 
+// Item list of one channel and the stage geometry it needs.
+struct T3Plan {
+    std::vector<int4> items;
+    unsigned stage_bytes = 0, a_off = 0;
+    int stages = 0;
+};
+
+bool t3_plan(int I_pad, int NT, T3Plan &pl)
+{
+    pl.items.clear();
+    bool off = false;
+    int nmax_off = 0;
+    for (int row0 = 0; row0 < I_pad; row0 += 128) {
+        const int nd = std::min(128, I_pad - row0);
+        pl.items.push_back(make_int4(row0, row0, nd, 1));
+        for (int c0 = row0 + 128; c0 < I_pad; c0 += NT) {
+            const int n = std::min(NT, I_pad - c0);
+            pl.items.push_back(make_int4(row0, c0, n, 0));
+            off = true;
+            nmax_off = std::max(nmax_off, n);
+        }
+    }
+    if ((int)pl.items.size() > kT3MaxItems) return false;
+    pl.a_off = off ? 4u * kT3APlane : 0u;
+    pl.stage_bytes = std::max(kT3BRegionMin, pl.a_off + 6u * (unsigned)nmax_off * kT3RowBytes);
+    pl.stage_bytes = (pl.stage_bytes + 1023u) / 1024u * 1024u;
+    pl.stages = std::min(kT3MaxStages, (int)(kT3SmemBudget / pl.stage_bytes));
+    return pl.stages >= 2;
+}
+
 }  // namespace
 
-cudaError_t launch_xcorr_tf32(const Handle &h, const float *corr, float2 *vis, cudaStream_t st)
+bool xtf32_supported(int I_pad, int S_pad)
+{
+    T3Plan pl;
+    return S_pad % (kT3K * 4) == 0 && t3_plan(I_pad, 64, pl);
+}
+
+cudaError_t launch_xcorr_tf32(const Handle &h, const float *corr, float2 *vis, cudaStream_t st, bool accumulate)
 {
     EncodeTiledFn enc = t3_encode_fn();
     if (!enc) return cudaErrorNotSupported;
-    if (h.I_pad > 128 || h.S_pad % (kT3K * kChunk) != 0) return cudaErrorNotSupported;
+    T3Plan pl;
+    if (!t3_plan(h.I_pad, 64, pl)) return cudaErrorNotSupported;
+    const int chunk = 4;                                // stages per accumulator chain: 64 spectra
+    if (h.S_pad % (kT3K * chunk) != 0) return cudaErrorNotSupported;
     const long long planes = (long long)h.p.n_subbands * h.p.n_channels * 2;
     if (planes > 0x7fffffffLL) return cudaErrorInvalidValue;
     T3Params P;
     memset(&P, 0, sizeof(P));
     const cuuint64_t gdim[3] = {(cuuint64_t)h.S_pad, (cuuint64_t)h.I_pad, (cuuint64_t)planes};
     const cuuint64_t gstride[2] = {(cuuint64_t)h.S_pad * 4, (cuuint64_t)h.S_pad * 4 * h.I_pad};
-    const cuuint32_t box[3] = {(cuuint32_t)kT3K, 128, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    if (enc(&P.map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<float *>(corr), gdim, gstride, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    const cuuint32_t box128[3] = {(cuuint32_t)kT3K, 128, 1};
+    const cuuint32_t box16[3] = {(cuuint32_t)kT3K, 16, 1};
+    if (enc(&P.map128, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<float *>(corr), gdim, gstride, box128, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
+    if (enc(&P.map16, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<float *>(corr), gdim, gstride, box16, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    for (size_t k = 0; k < pl.items.size(); ++k) P.items[k] = pl.items[k];
+    P.ipc = (int)pl.items.size();
     P.vis = vis;
     P.status = h.d_status;
-    P.n_items = planes / 2;
+    P.n_items = planes / 2 * P.ipc;
     P.N = h.p.n_stations;
-    P.I_pad = h.I_pad;
     P.nk = h.S_pad / kT3K;
+    P.chunk = chunk;
     P.B = h.B;
+    P.stages = pl.stages;
+    P.stage_bytes = pl.stage_bytes;
+    P.a_off = pl.a_off;
     P.timeout_cycles = h.tc_timeout_cycles;
     P.no_tma = h.tc_test_no_tma;
-    const size_t smem = 1024 + (size_t)kT3Stages * kT3Stage + 8 * kT3Bars + 16;
+    P.accumulate = accumulate ? 1 : 0;
+    const size_t smem = 1024 + (size_t)pl.stages * pl.stage_bytes + 8 * kT3Bars + 16;
     cudaError_t e = cudaFuncSetAttribute(xcorr_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long grid = std::min<long long>(P.n_items, h.num_sms);

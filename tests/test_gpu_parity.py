@@ -37,6 +37,27 @@ def per_subband_rel(got, ref):
     return np.linalg.norm(g - r, axis=1) / np.linalg.norm(r, axis=1)
 
 
+def baseline_max_rel(got, ref, N):
+    """max over (subband, channel, i <= j, p, q) of |dV_ij^pq| / sqrt(|V_ii^pp| |V_jj^qq|)
+    on vis arrays [SB][C][B][4][2] (the second error metric of the error
+    reading: each cross term is judged against its own stations' powers, not
+    against the autocorrelation-dominated norm)."""
+    g = got[..., 0] + 1j * got[..., 1]
+    r = ref[..., 0] + 1j * ref[..., 1]
+    jj, ii = np.meshgrid(np.arange(N), np.arange(N))
+    up = ii <= jj
+    i, j = ii[up], jj[up]
+    b = j * (j + 1) // 2 + i
+    auto = np.abs(r[:, :, (np.arange(N) * (np.arange(N) + 3)) // 2])      # [SB][C][N][4]
+    worst = 0.0
+    for p in range(2):
+        for q in range(2):
+            den = np.sqrt(auto[:, :, i, 3 * p] * auto[:, :, j, 3 * q])
+            num = np.abs(g[:, :, b, 2 * p + q] - r[:, :, b, 2 * p + q])
+            worst = max(worst, float(np.max(num / np.maximum(den, 1e-300))))
+    return worst
+
+
 def make_corr(blk, precision=0, **kw):
     fxg = fx()
     return fxg.Correlator(blk.n_stations, blk.n_subbands, blk.n_channels, blk.n_spectra,

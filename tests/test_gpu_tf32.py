@@ -14,7 +14,7 @@ import torch
 
 import oracle
 import synth
-from test_gpu_parity import make_corr, per_subband_rel, tone_block
+from test_gpu_parity import baseline_max_rel, make_corr, per_subband_rel, tone_block
 
 pytestmark = pytest.mark.gpu
 FS = synth.SAMPLE_RATE_HZ
@@ -31,6 +31,12 @@ CASES = [  # (fmt, SB, N, C, S)
     (synth.CI8, 1, 48, 256, 64),
     (synth.CI16, 2, 1, 16, 20),
     (synth.CI4, 1, 17, 64, 96),
+    # beyond one 128-input row block: off-diagonal column tiles and a ragged
+    # last row block (76 stations = 152 inputs, 80 = the paper's design target,
+    # 130 = two full 64-column off-diagonal tiles plus a ragged one)
+    (synth.CI16, 1, 76, 16, 70),
+    (synth.CI8, 1, 80, 16, 64),
+    (synth.CI16, 1, 130, 16, 40),
 ]
 
 
@@ -87,9 +93,9 @@ def test_tf32_split_planar_operands_match_fp32_path():
 
 
 def test_tf32_split_limits():
-    blk = synth.make_block(1, synth.CI16, 1, 65, 16, 8)
+    blk = synth.make_block(1, synth.CI16, 1, 513, 16, 8)
     with pytest.raises(RuntimeError):
-        make_corr(blk, precision=4)                             # more than 64 stations
+        make_corr(blk, precision=4)                             # more than 512 stations
     blk = synth.make_block(1, synth.CI16, 1, 4, 16, 8)
     with pytest.raises(RuntimeError):
         make_corr(blk, precision=4, operand_scale=0.5)          # no operand scaling in FP32
@@ -109,16 +115,21 @@ def _einsum_vis(y):
     return out
 
 
-@pytest.mark.parametrize("exact", [True, False])
-def test_tf32_split_kernel_on_given_operands(exact):
+@pytest.mark.parametrize("exact,N", [(True, 24), (False, 24), (False, 64), (False, 76), (True, 100),
+                                     (False, 200)])
+def test_tf32_split_kernel_on_given_operands(exact, N):
     """fx_correlate alone on planar FP32 operands written here: values with
     13 zero low mantissa bits (hi only, lo = 0) and arbitrary FP32 values
     (lo carries the low bits) against an FP64 einsum. Bound: each TMEM
     accumulator chain spans 64 spectra = 48 MMAs, and the tensor core's
     accumulation may lose up to 2^-24 of the running sum per MMA (48 x 2^-24 =
     2.9e-6), plus the dropped lo lo' term (below 2^-20); chains are summed in
-    IEEE FP32. So 4e-6 normwise, against 1e-5 for the FP32 path end to end."""
-    SB, N, C, S = 2, 24, 16, 96
+    IEEE FP32. So 4e-6 normwise, against 1e-5 for the FP32 path end to end.
+    Station counts above 64 exercise off-diagonal column tiles (A and B from
+    different inputs) and ragged diagonal tiles of the last row block.
+    Per baseline, max |dV_ij| / sqrt(|V_ii| |V_jj|) (so cross terms are not
+    hidden by the autocorrelations in the norm) stays below 2e-5."""
+    SB, C, S = 2, 16, 96
     blk = synth.make_block(1, synth.CI16, SB, N, C, S)
     c = make_corr(blk, precision=4)
     rng = np.random.default_rng(11 + exact)
@@ -134,6 +145,8 @@ def test_tf32_split_kernel_on_given_operands(exact):
     vis = c.correlate(torch.from_numpy(planar).cuda())
     torch.cuda.synchronize()
     ref = _einsum_vis(y.astype(np.complex128))
-    e = per_subband_rel(vis.cpu().numpy().astype(np.float64), ref)
+    got = vis.cpu().numpy().astype(np.float64)
+    e = per_subband_rel(got, ref)
     assert np.all(e < 4e-6), e
+    assert baseline_max_rel(got, ref, N) < 2e-5
     c.close()
