@@ -2,24 +2,31 @@
 """Benchmark of the FX correlator hot path on GB300 (one JSON line on rank 0).
 
 A step is one pass of the whole hot path over one block of synthetic
-LOFAR-shaped input already resident in HBM: fx_channelize (FIR + FFT),
-fx_correct (FP64 phase table + FP32 delay/bandpass rotation, transposing
-write) and fx_correlate (X-stage), all through the C ABI.
+LOFAR-shaped input already resident in HBM, through the C ABI:
+fx_channelize_correct (FP64 phase table, then the fused PPF FIR + FFT + delay /
+bandpass correction with the transposing write) and fx_correlate (X-stage).
 
-Default workload: 64 stations x 2 pols, 244 subbands, complex int16 noise
-(sigma 100) + 3 point sources with seeded delays (+-5 us) and per-station
-bandpass ripple, 16-tap PPF to 64 channels, 3072 spectra per block
-(1.00663 s of sky), FP32 path. Inputs (24.7 GB raw) are far larger than L2.
+Default workload (the headline): 64 stations x 2 pols, 244 subbands, complex
+int16 noise (sigma 100) + 3 point sources with seeded delays (+-5 us) and
+per-station bandpass ripple, 16-tap PPF to 64 channels, 3072 spectra per block
+(1.00663 s of sky), FP32-accurate path: the X-stage runs on the tcgen05 tensor
+cores with each FP32 operand split into hi + lo TF32 parts (FX_TF32_SPLIT).
+The CUDA-core FFMA FP32 X-stage and the FP16 / BF16 / split-FP16 tensor-core
+X-stages are timed on the same block, and the 8-bit precision workload (64
+stations, 488 subbands, 256 channels, 768 spectra) is timed at its own shape;
+every result's error is stated against the FP64 oracle on sampled subbands of
+the benchmarked block itself. Inputs (24.7 GB raw) are far larger than L2.
 
 value  = real-time factor = seconds of sky processed by all ranks / wall second
-e2e    = the same, with the raw block copied host->device from pinned memory and
-         the visibilities copied back inside the timed region
+e2e    = the same through fx_process_host, with the raw block copied
+         host->device from pinned memory and the visibilities copied back
+         inside the timed region
 Multi-GPU (torchrun): every rank processes its own 244-subband block (subbands
 are independent; weak scaling, no collective on the data path).
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (the only other place this file runs oracle/ code besides the
-cpu_baseline leg).
+workload. Besides that arm and the cpu_baseline leg, the oracle runs here only
+to state the error of the benchmarked visibilities on sampled subbands.
 """
 from __future__ import annotations
 
@@ -43,27 +50,36 @@ UNIT = "x real time (sky s / wall s)"
 FS = 195312.5
 
 WORKLOADS = {
-    "lofar16_fp32": dict(N=64, SB=244, C=64, S=3072, T=16, fmt=0, precision=0, sigma=100.0,
+    "lofar16_fp32": dict(N=64, SB=244, C=64, S=3072, T=16, fmt=0, precision=4, sigma=100.0,
                          ntones=3, ripple=True, seed_index=1,
-                         desc="LOFAR 16-bit, FP32 path: 64 stations x 2 pols, 244 subbands, "
-                              "16-tap PPF to 64 channels, 3072 spectra (1.00663 s) per block"),
+                         desc="LOFAR 16-bit, FP32-accurate path (hi/lo TF32 split X-stage on tensor cores): "
+                              "64 stations x 2 pols, 244 subbands, 16-tap PPF to 64 channels, "
+                              "3072 spectra (1.00663 s) per block"),
+    "lofar16_ffma": dict(N=64, SB=244, C=64, S=3072, T=16, fmt=0, precision=0, sigma=100.0,
+                         ntones=3, ripple=True, seed_index=1,
+                         desc="LOFAR 16-bit, FP32 path with the CUDA-core FFMA X-stage: 64 stations x 2 pols, "
+                              "244 subbands, 16-tap PPF to 64 channels, 3072 spectra (1.00663 s) per block"),
     "lofar8_fp16": dict(N=64, SB=488, C=256, S=768, T=16, fmt=1, precision=1, sigma=20.0,
                         ntones=1, ripple=False, seed_index=2,
                         desc="LOFAR 8-bit, FP16 X-stage: 64 stations x 2 pols, 488 subbands, "
                              "16-tap PPF to 256 channels, 768 spectra (1.00663 s) per block"),
-    "lofar16_fp32_small": dict(N=64, SB=8, C=64, S=3072, T=16, fmt=0, precision=0, sigma=100.0,
+    "lofar16_fp32_small": dict(N=64, SB=8, C=64, S=3072, T=16, fmt=0, precision=4, sigma=100.0,
                                ntones=3, ripple=True, seed_index=1,
-                               desc="LOFAR 16-bit FP32 path on 8 subbands (profiling size, ~4 GB)"),
+                               desc="LOFAR 16-bit FP32-accurate path on 8 subbands (profiling size, ~4 GB)"),
+    "lofar16_ffma_small": dict(N=64, SB=8, C=64, S=3072, T=16, fmt=0, precision=0, sigma=100.0,
+                               ntones=3, ripple=True, seed_index=1,
+                               desc="LOFAR 16-bit FFMA FP32 path on 8 subbands (profiling size, ~4 GB)"),
     "lofar8_fp16_small": dict(N=64, SB=16, C=256, S=768, T=16, fmt=1, precision=1, sigma=20.0,
                               ntones=1, ripple=False, seed_index=2,
                               desc="LOFAR 8-bit FP16 X-stage on 16 subbands (profiling size, ~2.5 GB)"),
-    "tiny_fp32": dict(N=8, SB=1, C=64, S=768, T=16, fmt=0, precision=0, sigma=100.0,
+    "tiny_fp32": dict(N=8, SB=1, C=64, S=768, T=16, fmt=0, precision=4, sigma=100.0,
                       ntones=1, ripple=False, seed_index=0,
                       desc="8 stations x 2 pols, 1 subband, 64 channels, 768 spectra"),
 }
 
+PRECISION_NAMES = {0: "fp32_ffma", 1: "fp16", 2: "bf16", 3: "split_fp16", 4: "tf32_split"}
+DTYPE_NAMES = {0: "f32", 1: "f16", 2: "bf16", 3: "f16 hi+lo", 4: "f32 as tf32 hi+lo"}
 FP32_LANES_PER_SM = 128
-SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
 
@@ -78,13 +94,31 @@ def useful_xflops(w, n_subbands=None):
     return 8.0 * B * 4 * w["C"] * w["S"] * (n_subbands or w["SB"])
 
 
+def executed_xflops(c, w, precision):
+    """Tensor-core flops the X-stage issues: 2 x 128 x N x 8 per MMA. FP16/BF16:
+    4 real products of the I_pad x I_pad tile per spectrum (both triangles);
+    split FP16: 12; TF32 split: 6 MMAs of 128 x 2n x 8 per 8 spectra per
+    128-row block x n-column tile of the upper block triangle."""
+    ip, sp = c.I_pad, c.S_pad
+    nch = w["C"] * w["SB"]
+    if precision == 4:
+        tiles = 0
+        for row0 in range(0, ip, 128):
+            tiles += 128 * 2 * min(128, ip - row0)
+            for c0 in range(row0 + 128, ip, 64):
+                tiles += 128 * 2 * min(64, ip - c0)
+        return 12.0 * tiles * sp * nch          # 6 MMAs x 2 x (128 x 2n) x 8 flop per 8 spectra
+    mult = {1: 4, 2: 4, 3: 12}[precision]
+    return 2.0 * mult * ip * ip * sp * nch
+
+
 def samples(w):
     return 2 * w["N"] * w["S"] * w["C"] * w["SB"]
 
 
-def fp32_alu_peak_tflops(mhz=SM_MAX_MHZ):
-    """FP32 FMA peak from unit counts and clock: 152 SMs x 128 lanes x 2 flop."""
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+def fp32_alu_peak_tflops(sm_count, mhz=SM_MAX_MHZ):
+    """FP32 FMA peak from the device's SM count and clock: SMs x 128 lanes x 2 flop."""
+    return sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
 def recorded_traffic(kernel: str, workload: str):
@@ -261,6 +295,17 @@ def oracle_sample(w, budget_s=30.0, max_subbands=32):
             "seconds_per_subband": per_sb}
 
 
+def config_of(w, ws):
+    """The `config` dict both arms print (same workload, same keys)."""
+    return {"workload": w["desc"], "stations": w["N"], "subbands_per_gpu": w["SB"], "channels": w["C"],
+            "taps": w["T"], "spectra": w["S"],
+            "input": {0: "complex int16", 1: "complex int8", 2: "complex int4"}[w["fmt"]],
+            "x_stage": PRECISION_NAMES[w["precision"]],
+            "l2": "inputs larger than L2 (raw block %.1f GB)" % (samples(w) * (4 if w["fmt"] == 0 else 2) / 1e9
+                                                               * (w["S"] + w["T"] - 1) / w["S"]),
+            "parallelism": f"subband blocks x {ws} GPU(s), no collective"}
+
+
 def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -274,15 +319,73 @@ def run_reference(args, w):
     value = sky_seconds(w) / (per_sb * w["SB"])
     cb = dict(steps[-1])
     cb["value"] = value
-    cb["sample"] = f"1 of {w['SB']} subbands per step, {args.steps} steps, scaled linearly"
+    cb["sample"] = (f"each step runs the oracle on 1 whole subband of the {w['SB']}-subband block "
+                    f"({per_sb:.2f} s measured; ms_per_step is that time); value scales it linearly to "
+                    f"{w['SB']} subbands ({per_sb * w['SB']:.0f} s per block)")
     cb.pop("seconds_per_subband", None)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_sb * w["SB"] * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_sb * 1e3,
+            "ms_per_block_scaled": per_sb * w["SB"] * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w["desc"]}, "cpu_baseline": cb,
+            "data": "synthetic", "config": config_of(w, args.gpus), "cpu_baseline": cb,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def vis_errors(got, ref, N):
+    """Normwise relative error per subband (max over subbands) and the
+    per-baseline max |dV_ij| / sqrt(|V_ii| |V_jj|), vis arrays [SB][C][B][4][2]."""
+    import numpy as np
+    g = got[..., 0] + 1j * got[..., 1]
+    r = ref[..., 0] + 1j * ref[..., 1]
+    norm = float(np.max(np.linalg.norm((g - r).reshape(g.shape[0], -1), axis=1) /
+                        np.linalg.norm(r.reshape(r.shape[0], -1), axis=1)))
+    jj, ii = np.meshgrid(np.arange(N), np.arange(N))
+    up = ii <= jj
+    i, j = ii[up], jj[up]
+    b = j * (j + 1) // 2 + i
+    auto = np.abs(r[:, :, (np.arange(N) * (np.arange(N) + 3)) // 2])
+    worst = 0.0
+    for p in range(2):
+        for q in range(2):
+            den = np.sqrt(auto[:, :, i, 3 * p] * auto[:, :, j, 3 * q])
+            worst = max(worst, float(np.max(np.abs(g[:, :, b, 2 * p + q] - r[:, :, b, 2 * p + q]) /
+                                            np.maximum(den, 1e-300))))
+    return {"normwise": norm, "baseline_max": worst}
+
+
+def oracle_reference(w, raw, taps, centres, tau, ripple, sbs):
+    """FP64 oracle visibilities of the subbands `sbs` of the benchmarked block
+    (raw samples copied to the host), to state each result's error."""
+    import numpy as np
+
+    import oracle
+    r = raw[sbs].cpu().numpy()
+    bp = None if ripple is None else 1.0 / ripple
+    return oracle.fx(w["fmt"], r, w["T"], w["C"], w["S"], taps, FS, np.asarray(centres)[sbs], tau, tau,
+                     bandpass=bp)
+
+
+def measure_peaks(dev):
+    """Burst dense tensor throughput of torch matmuls on this GPU (8192^3,
+    best of 10): TF32 (FP32 inputs, allow_tf32), FP16 and BF16."""
+    import torch
+    n, out = 8192, {}
+    stream = torch.cuda.current_stream()
+    old = torch.backends.cuda.matmul.allow_tf32
+    for name, dt, tf in (("tf32", torch.float32, True), ("fp16", torch.float16, False),
+                         ("bf16", torch.bfloat16, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf
+        a = torch.randn(n, n, device=dev, dtype=dt)
+        b = torch.randn(n, n, device=dev, dtype=dt)
+        torch.matmul(a, b)
+        best = min(_time(lambda: torch.matmul(a, b), 1, stream) for _ in range(10))
+        out[name + "_tflops"] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = old
+    out["how"] = "torch.matmul 8192^3, best of 10, CUDA events, this run"
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -301,11 +404,12 @@ def run_fx(args, w):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    prec = w["precision"]
 
     raw, taps, centres, delays, bandpass, tau, ripple = workload_inputs(w, dev)
     c = fxg.Correlator(w["N"], w["SB"], w["C"], w["S"], taps=taps, centres=centres, n_taps=w["T"],
-                       fmt=w["fmt"], precision=w["precision"])
-    chan = torch.empty(c.chan_shape(), dtype=torch.float32, device=dev)
+                       fmt=w["fmt"], precision=prec)
     corr = torch.empty(c.corr_shape(), dtype=c.corr_dtype(), device=dev)
     vis = torch.empty(c.vis_shape(), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -340,8 +444,23 @@ def run_fx(args, w):
     total_ms = start.elapsed_time(stop)
     ms_fc = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     ms_x = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    max_ms = max_over_ranks(total_ms, ws, dev)
+    ms_step = max_ms / args.steps
+    value = aggregate_value(sky_seconds(w) * args.steps, ws, max_ms / 1e3)
 
-    # the same step through the three separate calls (paper's kernel split)
+    # error of the benchmarked visibilities against the FP64 oracle on two
+    # sampled subbands of this very block
+    sbs = sorted({min(1, w["SB"] - 1), max(0, w["SB"] - 2)})
+    ref = None
+    parity = {"subbands": sbs, "oracle": "FP64 C oracle on the raw samples of these subbands"}
+    if rank == 0 and not args.no_parity:
+        ref = oracle_reference(w, raw, taps, centres, tau, ripple, sbs)
+        parity[PRECISION_NAMES[prec]] = vis_errors(vis[sbs].double().cpu().numpy(), ref, w["N"])
+
+    # the same step through the three separate calls (the paper's kernel split):
+    # the stand-alone channeliser is the PPF's HBM roofline
+    chan = torch.empty(c.chan_shape(), dtype=torch.float32, device=dev)
+
     def step3(ev):
         ev[0].record(stream)
         c.channelize(raw, chan)
@@ -358,41 +477,38 @@ def run_fx(args, w):
     ms_f = statistics.mean(e[0].elapsed_time(e[1]) for e in ev3[1:])
     ms_c = statistics.mean(e[1].elapsed_time(e[2]) for e in ev3[1:])
     ms_3 = statistics.mean(e[0].elapsed_time(e[3]) for e in ev3[1:])
-    # FP32 X-stage in its other forms, same operands
-    ms_x_forms = {}
-    if w["precision"] == 0:
-        for form in ("2x4", "3mult"):
-            c2 = fxg.Correlator(w["N"], w["SB"], w["C"], w["S"], taps=taps, centres=centres, n_taps=w["T"],
-                                fmt=w["fmt"], precision=0, xf32_form=form)
-            vis2 = torch.empty_like(vis)
-            c2.correlate(corr, vis2)
-            ms_x_forms[form] = _time(lambda: c2.correlate(corr, vis2), args.steps, stream)
-            ms_x_forms[form + "_rel_diff"] = float(torch.linalg.vector_norm((vis2 - vis).double()) /
-                                                   torch.linalg.vector_norm(vis.double()))
-            c2.close()
-            del vis2
-    max_ms = max_over_ranks(total_ms, ws, dev)
-    ms_step = max_ms / args.steps
-    value = aggregate_value(sky_seconds(w) * args.steps, ws, max_ms / 1e3)
+    del chan
 
+    peaks_run = measure_peaks(dev)
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
     xflops = useful_xflops(w)
     sz = c.sizes
-    if w["precision"] == 0:
-        x_ach = xflops / (ms_x * 1e-3) / 1e12
-        roof = {"kernel": "xcorr_f32_kernel", "bound": "alu", "achieved": x_ach,
-                "peak": fp32_alu_peak_tflops(), "unit": "TFLOP/s",
-                "frac": x_ach / fp32_alu_peak_tflops(),
+    x_ach = xflops / (ms_x * 1e-3) / 1e12
+    if prec == 4:
+        ex = executed_xflops(c, w, prec)
+        tpk = peaks_run["tf32_tflops"]
+        roof = {"kernel": "xcorr_tf32_kernel", "bound": "tensor", "achieved": x_ach, "peak": tpk,
+                "unit": "TFLOP/s", "frac": x_ach / tpk,
+                "traffic": recorded_traffic("xcorr_tf32_kernel", args.workload),
+                "peak_source": "dense TF32 tensor throughput measured in this run (torch TF32 matmul 8192^3, "
+                               "burst); MEASURED_PEAKS.json holds no TF32 figure",
+                "algorithmic": f"{xflops:.4e} useful flop per launch (8 per complex MAC, upper triangle)",
+                "executed_TFLOPs": ex / (ms_x * 1e-3) / 1e12, "executed_frac": ex / (ms_x * 1e-3) / 1e12 / tpk,
+                "executed_note": "the split form issues 3 TF32 products (hi hi', hi lo', lo hi') of whole "
+                                 "128-input tiles: %.2fx the useful flops" % (ex / xflops)}
+    elif prec == 0:
+        fpk = fp32_alu_peak_tflops(sm_count)
+        roof = {"kernel": "xcorr_f32_kernel", "bound": "alu", "achieved": x_ach, "peak": fpk,
+                "unit": "TFLOP/s", "frac": x_ach / fpk,
                 "traffic": recorded_traffic("xcorr_f32_kernel", args.workload),
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "peak_source": f"derived: {sm_count} SMs (device property) x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "algorithmic": f"{xflops:.4e} useful flop per launch (8 per complex MAC)"}
     else:
         x_bytes = sz.corr_bytes + sz.vis_bytes
-        x_ach = x_bytes / (ms_x * 1e-3) / 1e9
-        roof = {"kernel": "xcorr_tc_kernel", "bound": "hbm", "achieved": x_ach, "peak": hbm,
-                "unit": "GB/s", "frac": x_ach / hbm,
-                "traffic": recorded_traffic("xcorr_tc_kernel", args.workload),
+        xb = x_bytes / (ms_x * 1e-3) / 1e9
+        roof = {"kernel": "xcorr_tc_kernel", "bound": "hbm", "achieved": xb, "peak": hbm,
+                "unit": "GB/s", "frac": xb / hbm, "traffic": recorded_traffic("xcorr_tc_kernel", args.workload),
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
                 "algorithmic": f"{x_bytes:.4e} B per launch (operands + visibilities)"}
     f_bytes = sz.raw_bytes + sz.chan_bytes
@@ -401,24 +517,50 @@ def run_fx(args, w):
     kernels = {
         "channelize_correct_ms": ms_fc, "channelize_correct_GBps": fc_bytes / (ms_fc * 1e-3) / 1e9,
         "channelize_correct_hbm_frac": fc_bytes / (ms_fc * 1e-3) / 1e9 / hbm,
-        "correlate_ms": ms_x, "correlate_useful_TFLOPs": xflops / (ms_x * 1e-3) / 1e12,
+        "correlate_ms": ms_x, "correlate_useful_TFLOPs": x_ach,
         "three_call_path": {
             "step_ms": ms_3, "rtf": sky_seconds(w) / (ms_3 * 1e-3),
             "channelize_ms": ms_f, "channelize_GBps": f_bytes / (ms_f * 1e-3) / 1e9,
             "channelize_hbm_frac": f_bytes / (ms_f * 1e-3) / 1e9 / hbm,
             "correct_ms": ms_c, "correct_GBps": c_bytes / (ms_c * 1e-3) / 1e9,
             "correct_hbm_frac": c_bytes / (ms_c * 1e-3) / 1e9 / hbm},
+        "fp32_alu_peak_TFLOPs": fp32_alu_peak_tflops(sm_count),
     }
-    if ms_x_forms:
-        kernels["correlate_form"] = "4x4-station tiles" if w["N"] >= 16 else "2x4-station tiles"
-        kernels["correlate_other_forms_ms"] = ms_x_forms
     # measured FP32 FMA throughput (registers only) beside the derived ALU peak
     sink = torch.zeros(1, dtype=torch.float32, device=dev)
-    nblk, iters = 8 * torch.cuda.get_device_properties(dev).multi_processor_count, 4096
-    probe = lambda: c.lib.fx_ffma_probe(iters, nblk, ctypes.c_void_p(sink.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    nblk, iters = 8 * sm_count, 4096
+    probe = lambda: c.lib.fx_ffma_probe(iters, nblk, ctypes.c_void_p(sink.data_ptr()),
+                                        ctypes.c_void_p(stream.cuda_stream))
     probe()
     ms_probe = _time(probe, 3, stream)
     kernels["fp32_fma_probe_tflops"] = nblk * 256.0 * iters * 512 / (ms_probe * 1e-3) / 1e12
+
+    # ---- the other X-stage forms on the same block, each with the fused
+    # F-stage writing its own operand layout; errors against the same oracle ----
+    variants = {}
+    if not args.no_variants:
+        for vp in (0, 4, 1, 2, 3):
+            if vp == prec:
+                continue
+            name = PRECISION_NAMES[vp]
+            try:
+                variants[name] = precision_variant(args, w, vp, raw, taps, centres, delays, bandpass, stream,
+                                                   sbs, ref)
+            except Exception as ex:  # report, do not hide
+                variants[name] = {"error": str(ex)[:200]}
+        head = {"step_ms": ms_step, "correlate_ms": ms_x}
+        for name, v in variants.items():
+            if "step_ms" in v:
+                v["step_speedup_vs_" + PRECISION_NAMES[prec]] = head["step_ms"] / v["step_ms"]
+                v["xstage_speedup_vs_" + PRECISION_NAMES[prec]] = head["correlate_ms"] / v["correlate_ms"]
+        ff = variants.get("fp32_ffma")
+        if ff and "step_ms" in ff:
+            for name, v in variants.items():
+                if "step_ms" in v and name != "fp32_ffma":
+                    v["step_speedup_vs_fp32_ffma"] = ff["step_ms"] / v["step_ms"]
+                    v["xstage_speedup_vs_fp32_ffma"] = ff["correlate_ms"] / v["correlate_ms"]
+            kernels["step_speedup_vs_fp32_ffma"] = ff["step_ms"] / ms_step
+            kernels["xstage_speedup_vs_fp32_ffma"] = ff["correlate_ms"] / ms_x
 
     # ---- end to end: pinned host raw in, visibilities out, copies timed ----
     # fx_process_host: host raw in, host visibilities out, subband chunks with
@@ -430,9 +572,11 @@ def run_fx(args, w):
         h_vis = torch.empty(vis.shape, dtype=vis.dtype, pin_memory=True)
         h_tau = torch.as_tensor(tau, dtype=torch.float64)
         h_bp = None if bandpass is None else bandpass.cpu()
+        del corr
+        torch.cuda.empty_cache()
         chunk = max(1, min(w["SB"], args.host_chunk))
         ch = fxg.Correlator(w["N"], w["SB"], w["C"], w["S"], taps=taps, centres=centres, n_taps=w["T"],
-                            fmt=w["fmt"], precision=w["precision"], host_chunk_subbands=chunk)
+                            fmt=w["fmt"], precision=prec, host_chunk_subbands=chunk)
 
         def e2e_step():
             ch.process_host(h_raw, h_tau, h_tau, bandpass=h_bp, out=h_vis)
@@ -460,96 +604,24 @@ def run_fx(args, w):
         ch.close()
         del h_raw, h_vis
 
-    # ---- tensor-core variants of the X-stage on the same block ----
-    variants = {}
-    if not args.no_variants and w["precision"] == 0:
-        ref_vis = vis.double()
-        del corr
-        for name, prec in (("fp16", 1), ("split_fp16", 3), ("bf16", 2), ("tf32_split", 4)):
-            try:
-                cv = fxg.Correlator(w["N"], w["SB"], w["C"], w["S"], taps=taps, centres=centres,
-                                    n_taps=w["T"], fmt=w["fmt"], precision=prec)
-                corr_v = torch.empty(cv.corr_shape(), dtype=cv.corr_dtype(), device=dev)
-                vis_v = torch.empty_like(vis)
-                cv.correct(chan, delays, delays, bandpass=bandpass, out=corr_v)
-                cv.correlate(corr_v, vis_v)
-                torch.cuda.synchronize()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                for _ in range(args.steps):
-                    cv.correlate(corr_v, vis_v)
-                b.record(stream)
-                torch.cuda.synchronize()
-                vx = a.elapsed_time(b) / args.steps
-                err = float(torch.linalg.vector_norm(vis_v.double() - ref_vis) /
-                            torch.linalg.vector_norm(ref_vis))
-                # the whole step in this precision: phase table + fused F-stage + X-stage
-                a.record(stream)
-                for _ in range(args.steps):
-                    cv.channelize_correct(raw, delays, delays, bandpass=bandpass, out=corr_v)
-                    cv.correlate(corr_v, vis_v)
-                b.record(stream)
-                torch.cuda.synchronize()
-                vs = a.elapsed_time(b) / args.steps
-                xb = cv.sizes.corr_bytes + cv.sizes.vis_bytes
-                # executed tensor work: full I_pad x I_pad (both triangles) per spectrum and channel,
-                # 4 real products (x3 for the split forms); TF32 peak = half the BF16 peak
-                ip, sp = cv.I_pad, cv.S_pad
-                mult = {1: 4, 2: 4, 3: 12, 4: 12}[prec]
-                exec_fl = 2.0 * mult * ip * ip * sp * w["C"] * w["SB"]
-                tpeak = float(peaks.get("bf16_tflops", 1890.0)) * (0.5 if prec == 4 else 1.0)
-                variants[name] = {"correlate_ms": vx, "useful_TFLOPs": xflops / (vx * 1e-3) / 1e12,
-                                  "executed_TFLOPs": exec_fl / (vx * 1e-3) / 1e12,
-                                  "tensor_frac_executed": exec_fl / (vx * 1e-3) / 1e12 / tpeak,
-                                  "tensor_frac_useful": xflops / (vx * 1e-3) / 1e12 / tpeak,
-                                  "speedup_vs_fp32_xstage": ms_x / vx,
-                                  "hbm_GBps": xb / (vx * 1e-3) / 1e9, "hbm_frac": xb / (vx * 1e-3) / 1e9 / hbm,
-                                  "rel_err_vs_fp32_path": err,
-                                  "step_ms": vs, "step_rtf": sky_seconds(w) / (vs * 1e-3)}
-                del corr_v, vis_v
-                cv.close()
-            except Exception as ex:  # report, do not hide
-                variants[name] = {"error": str(ex)[:200]}
-        # F-stage and X-stage piece by piece through two L2-sized operand buffers
-        # (fx_channelize_correlate); pieces of 48 MB or less
-        for name, prec, G, TC in (("chunked_fp16", 1, 4, 384), ("chunked_fp32", 0, 4, 192)):
-            try:
-                if w["S"] % TC or w["SB"] < G:
-                    continue
-                cv = fxg.Correlator(w["N"], w["SB"], w["C"], w["S"], taps=taps, centres=centres,
-                                    n_taps=w["T"], fmt=w["fmt"], precision=prec, chunk_subbands=G,
-                                    chunk_spectra=TC)
-                vis_v = torch.empty_like(vis)
-                cv.channelize_correlate(raw, delays, delays, bandpass=bandpass, out=vis_v)
-                torch.cuda.synchronize()
-                vs = _time(lambda: cv.channelize_correlate(raw, delays, delays, bandpass=bandpass, out=vis_v),
-                           args.steps, stream)
-                err = float(torch.linalg.vector_norm(vis_v.double() - ref_vis) / torch.linalg.vector_norm(ref_vis))
-                variants[name] = {"piece": f"{G} subbands x {TC} spectra", "step_ms": vs,
-                                  "step_rtf": sky_seconds(w) / (vs * 1e-3), "rel_err_vs_fp32_path": err}
-                del vis_v
-                cv.close()
-            except Exception as ex:  # report, do not hide
-                variants[name] = {"error": str(ex)[:200]}
-
-    del raw, chan
+    del raw
+    torch.cuda.empty_cache()
+    precision_form = None
+    if not args.no_precision_form and w["SB"] > 8:
+        try:
+            precision_form = measure_precision_form(args, dev)
+        except Exception as ex:
+            precision_form = {"error": str(ex)[:300]}
+        torch.cuda.empty_cache()
     extras = {}
     if not args.no_extras:
-        torch.cuda.empty_cache()
-        try:
-            extras["batching"] = measure_batching(args, dev)
-        except Exception as ex:
-            extras["batching"] = {"error": str(ex)[:300]}
-        torch.cuda.empty_cache()
-        try:
-            extras["differentiation"] = measure_adjoint(args, dev)
-        except Exception as ex:
-            extras["differentiation"] = {"error": str(ex)[:300]}
-        torch.cuda.empty_cache()
-        try:
-            extras["beamformer"] = measure_beamformer(args, dev)
-        except Exception as ex:
-            extras["beamformer"] = {"error": str(ex)[:300]}
+        for key, fn in (("batching", measure_batching), ("differentiation", measure_adjoint),
+                        ("beamformer", measure_beamformer)):
+            torch.cuda.empty_cache()
+            try:
+                extras[key] = fn(args, dev)
+            except Exception as ex:
+                extras[key] = {"error": str(ex)[:300]}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -559,18 +631,16 @@ def run_fx(args, w):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if w["precision"] == 0 else "f16",
-        "data": "synthetic",
-        "config": {"workload": w["desc"], "stations": w["N"], "subbands_per_gpu": w["SB"],
-                   "channels": w["C"], "taps": w["T"], "spectra": w["S"],
-                   "input": "complex int16" if w["fmt"] == 0 else "complex int8",
-                   "l2": "inputs larger than L2 (raw block %.1f GB)" % (sz.raw_bytes / 1e9),
-                   "parallelism": f"subband blocks x {ws} GPU(s), no collective"},
+        "vs_baseline": None, "dtype": DTYPE_NAMES[prec], "data": "synthetic",
+        "config": config_of(w, ws),
         "roofline": roof,
         "kernels": kernels,
+        "parity_vs_oracle": parity,
         "samples_per_s": samples(w) * ws / (ms_step * 1e-3),
-        "x_stage_useful_TFLOPs": xflops / (ms_x * 1e-3) / 1e12,
+        "x_stage_useful_TFLOPs": x_ach,
+        "peaks_measured_here": peaks_run,
         "variants": variants,
+        "precision_form": precision_form,
         **extras,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -584,6 +654,89 @@ def run_fx(args, w):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def precision_variant(args, w, vp, raw, taps, centres, delays, bandpass, stream, sbs, ref):
+    """One X-stage precision on a resident raw block: the fused F-stage in that
+    precision's operand layout + the X-stage, timed as a step and alone, with
+    the error of the result against the oracle visibilities `ref` of `sbs`."""
+    import torch
+
+    import paper_1801_04834_gb300 as fxg
+    dev = raw.device
+    cv = fxg.Correlator(w["N"], w["SB"], w["C"], w["S"], taps=taps, centres=centres, n_taps=w["T"],
+                        fmt=w["fmt"], precision=vp)
+    corr_v = torch.empty(cv.corr_shape(), dtype=cv.corr_dtype(), device=dev)
+    vis_v = torch.empty(cv.vis_shape(), dtype=torch.float32, device=dev)
+
+    def fstage():
+        cv.channelize_correct(raw, delays, delays, bandpass=bandpass, out=corr_v)
+
+    def xstage():
+        cv.correlate(corr_v, vis_v)
+
+    for _ in range(2):
+        fstage()
+        xstage()
+    step_ms = _time(lambda: (fstage(), xstage()), args.steps, stream)
+    f_ms = _time(fstage, args.steps, stream)
+    x_ms = _time(xstage, args.steps, stream)
+    fstage()
+    xstage()
+    torch.cuda.synchronize()
+    xflops = useful_xflops(w)
+    peaks, _ = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    fc_bytes = cv.sizes.raw_bytes + cv.sizes.corr_bytes
+    out = {"step_ms": step_ms, "step_rtf": sky_seconds(w) / (step_ms * 1e-3),
+           "channelize_correct_ms": f_ms, "channelize_correct_hbm_frac": fc_bytes / (f_ms * 1e-3) / 1e9 / hbm,
+           "correlate_ms": x_ms, "correlate_useful_TFLOPs": xflops / (x_ms * 1e-3) / 1e12}
+    if vp != 0:
+        ex = executed_xflops(cv, w, vp)
+        out["correlate_executed_TFLOPs"] = ex / (x_ms * 1e-3) / 1e12
+    if vp in (1, 2, 3):
+        xb = cv.sizes.corr_bytes + cv.sizes.vis_bytes
+        out["correlate_hbm_frac"] = xb / (x_ms * 1e-3) / 1e9 / hbm
+    if ref is not None:
+        out["error_vs_oracle"] = vis_errors(vis_v[sbs].double().cpu().numpy(), ref, w["N"])
+    del corr_v, vis_v
+    cv.close()
+    return out
+
+
+def measure_precision_form(args, dev):
+    """The precision workload at its own shape (LOFAR 8-bit mode): 64 stations
+    x 2 pols, 488 subbands of complex int8 samples (sigma 20, clipped) + one
+    point source, 16-tap PPF to 256 channels in FP32, 768 spectra per block.
+    The X-stage in FP16, BF16 and split FP16 (FP32 accumulation), against the
+    two FP32 paths (TF32 split on the tensor cores, FFMA on the CUDA cores) at
+    the same shape; each result's error against the FP64 oracle on two
+    sampled subbands of this block."""
+    import torch
+    w = WORKLOADS["lofar8_fp16"]
+    raw, taps, centres, delays, bandpass, tau, ripple = workload_inputs(w, dev)
+    stream = torch.cuda.current_stream()
+    sbs = [1, w["SB"] - 2]
+    ref = None if args.no_parity else oracle_reference(w, raw, taps, centres, tau, ripple, sbs)
+    res = {"workload": w["desc"], "subbands_checked": sbs}
+    for vp in (4, 0, 1, 2, 3):
+        name = PRECISION_NAMES[vp]
+        try:
+            res[name] = precision_variant(args, w, vp, raw, taps, centres, delays, bandpass, stream, sbs, ref)
+        except Exception as ex:
+            res[name] = {"error": str(ex)[:200]}
+        torch.cuda.empty_cache()
+    for base in ("tf32_split", "fp32_ffma"):
+        b = res.get(base, {})
+        if "step_ms" not in b:
+            continue
+        for vp in (1, 2, 3):
+            v = res.get(PRECISION_NAMES[vp], {})
+            if "step_ms" in v:
+                v["step_speedup_vs_" + base] = b["step_ms"] / v["step_ms"]
+                v["xstage_speedup_vs_" + base] = b["correlate_ms"] / v["correlate_ms"]
+    del raw
+    return res
 
 
 def _time(fn, reps, stream):
@@ -790,6 +943,9 @@ def main(argv=None):
                     help="subbands per chunk of the host pipeline (e2e)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batching, differentiation and beamformer measurements")
+    ap.add_argument("--no-parity", action="store_true", help="skip the oracle error checks")
+    ap.add_argument("--no-precision-form", action="store_true",
+                    help="skip the 8-bit precision workload at its own shape")
     ap.add_argument("--beam-subbands", type=int, default=244,
                     help="subbands of the beamformer measurement (244 = the paper's requirement)")
     args = ap.parse_args(argv)

@@ -51,7 +51,13 @@ def test_workload_counts():
     # 8 * 2080 baselines * 4 products * 64 channels * 3072 spectra * 244 subbands
     assert bench.useful_xflops(w) == pytest.approx(3.1930e12, rel=1e-4)
     assert bench.samples(w) == 128 * 3072 * 64 * 244
-    assert bench.fp32_alu_peak_tflops() == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+    assert bench.fp32_alu_peak_tflops(152) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+    # both arms print the same config dict
+    assert bench.config_of(w, 1) == bench.config_of(w, 1) and bench.config_of(w, 1)["x_stage"] == "tf32_split"
+    # executed tensor work of the TF32 split at 64 stations: 6 MMAs of 128 x 256 x 8 per 8 spectra per channel
+    class _C:
+        I_pad, S_pad = 128, 3072
+    assert bench.executed_xflops(_C, w, 4) == pytest.approx(6 * 2 * 128 * 256 * 8 * 384 * 64 * 244)
     assert bench.aggregate_value(10.0, 1, 2.0) == 5.0
 
 
