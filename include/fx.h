@@ -272,8 +272,9 @@ fx_status fx_stream_block(fx_handle *h, const void *d_new, const int *d_coarse_s
 /* Zero the streaming history (the stream restarts with zeros before it). */
 fx_status fx_stream_reset(fx_handle *h, fx_stream stream);
 
-/* ---- FP32 throughput probe ------------------------------------------------
- * Launches `blocks` CTAs of 256 threads that each run `iterations` x 128
+/* ---- FP32 throughput probe (a measurement aid, not part of the method) ----
+ * Not a step of the correlator: it exists only to measure the FP32 FMA peak
+ * that the FFMA X-stage's roofline is judged against. Launches `blocks` CTAs of 256 threads that each run `iterations` x 128
  * packed FP32 FMAs (FFMA2) per thread on registers only: 512 flop per
  * iteration per thread, blocks * 256 * iterations * 512 flop in total. The
  * caller times it (events on `stream`) to measure the FP32 FMA peak that the
@@ -409,17 +410,24 @@ fx_status fx_poll_status(fx_handle *h, int *code);
  * cause. The paper has no counterpart; it is a packaging variant of the
  * delay/bandpass step.
  *
- * The per-call FP64 phase table lives in a fixed device array built into the
- * library, FX_NOALLOC_MAX_PHASES entries (8 MiB, held by every GPU that loads
- * the library until the process exits); a request with
- * n_subbands * n_stations * n_channels above that limit is rejected with
- * FX_ERR_INVALID before anything is launched. The first call on each device
- * looks up that array's device address (with that device current) and caches
- * it, so make the first call on a device before any stream capture. Every call
- * reuses the same array and overwrites all of the entries it reads, so no
- * state carries over between calls; calls whose work overlaps on the GPU
- * (different streams, or different host threads without ordering) race on
- * the array and must be serialised by the caller.
+ * The per-call phase table (FP32 pairs: the phase at the block start reduced
+ * mod 2 pi and the per-spectrum step, both computed in FP64) lives in a fixed
+ * device array built into the library, FX_NOALLOC_MAX_PHASES entries (8 MiB
+ * per GPU, held until the process exits); a request with
+ * n_subbands * n_stations * n_channels above that limit, or with more than
+ * 4096 stations, 65535 subbands or 4194240 spectra, is rejected with
+ * FX_ERR_INVALID before anything is launched. The array is committed on a
+ * device when the library's correction code is first loaded there (under
+ * CUDA's lazy loading: the first call of this entry point or of any
+ * correction launch on that device), and the first call on each device also
+ * looks up the array's device address (with that device current) and caches
+ * it; either may synchronise. So make one warm-up call per device outside any
+ * real-time thread and before any stream capture. The cached address belongs
+ * to the device's context; after cudaDeviceReset the next call looks it up
+ * again. Every call reuses the same array and overwrites all of the entries
+ * it reads, so no state carries over between calls; calls whose work overlaps
+ * on the GPU (different streams, or different host threads without ordering)
+ * race on the array and must be serialised by the caller.
  *
  * Arguments as for fx_correct with an FX_F32 handle: d_subband_centre_hz [SB]
  * double (device), d_delay_begin/d_delay_end [N] double seconds (device),

@@ -17,6 +17,7 @@
 //                stored as FP32. FP64 work is SB*N*C, not per sample.
 //   correct_*    FP32 per sample: phi = phi0 + s * step, sincos, rotate,
 //                times bandpass * gain, transpose. Memory bound.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -247,24 +248,46 @@ cudaError_t launch_phase_table(const Handle &h, const double *tau_b, const doubl
     return cudaGetLastError();
 }
 
+// The context current on this thread (driver entry point fetched through the
+// runtime, so the library needs no -lcuda), or null.
+static CUcontext current_context()
+{
+    typedef CUresult (*GetCurrentFn)(CUcontext *);
+    static GetCurrentFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            return reinterpret_cast<GetCurrentFn>(p);
+        return static_cast<GetCurrentFn>(nullptr);
+    }();
+    CUcontext ctx = nullptr;
+    if (fn) fn(&ctx);
+    return ctx;
+}
+
 // Device address of g_noalloc_phase on the current device. In host code the
 // array's name is only a host-side stand-in, so the address is looked up with
 // cudaGetSymbolAddress once per device (the first call on that device does
-// it) and cached.
+// it, with that device current) and cached together with the context it
+// belongs to; if the device's context was replaced since (cudaDeviceReset),
+// the lookup is done again.
 static cudaError_t noalloc_phase_ptr(float2 **out)
 {
     static std::mutex mu;
     static float2 *ptrs[kMaxDevices] = {};
+    static CUcontext ctxs[kMaxDevices] = {};
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(mu);
-    if (!ptrs[dev]) {
+    if (!ptrs[dev] || (ctxs[dev] && ctxs[dev] != current_context())) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_phase);
         if (e != cudaSuccess) return e;
         ptrs[dev] = static_cast<float2 *>(p);
+        ctxs[dev] = current_context();
     }
     *out = ptrs[dev];
     return cudaSuccess;

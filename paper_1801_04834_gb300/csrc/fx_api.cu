@@ -623,10 +623,10 @@ extern "C" fx_status fx_correct_f32_noalloc(int n_stations, int n_subbands, int 
         return fail(FX_ERR_INVALID,
                     "%s: subbands x stations x channels = %lld exceeds the built-in phase table of %u entries",
                     who, entries, FX_NOALLOC_MAX_PHASES);
-    if (n_subbands > 65535 || n_spectra > (1 << 24) || n_stations > 4096)
-        return fail(FX_ERR_INVALID, "%s: sizes out of range", who);
-    if ((size_t)sizeof(float2) * 32 * (2 * n_stations + 1) > 227 * 1024)
-        return fail(FX_ERR_UNSUPPORTED, "%s: too many stations", who);
+    // the correction kernel's grid: (stations, runs of four 16-spectrum blocks, subbands)
+    if (n_subbands > 65535 || n_stations > 4096 || ((n_spectra + 15) / 16 + 3) / 4 > 65535)
+        return fail(FX_ERR_INVALID, "%s: sizes out of range (subbands <= 65535, stations <= 4096, "
+                    "spectra <= 4194240)", who);
     if (!d_subband_centre_hz || !d_delay_begin || !d_delay_end || !d_chan || !d_corr)
         return fail(FX_ERR_INVALID, "%s: NULL buffer", who);
     if (((uintptr_t)d_chan & 15) || ((uintptr_t)d_corr & 15) || ((uintptr_t)d_gains & 7) ||

@@ -54,7 +54,8 @@ def baseline_max_rel(got, ref, N):
         for q in range(2):
             den = np.sqrt(auto[:, :, i, 3 * p] * auto[:, :, j, 3 * q])
             num = np.abs(g[:, :, b, 2 * p + q] - r[:, :, b, 2 * p + q])
-            worst = max(worst, float(np.max(num / np.maximum(den, 1e-300))))
+            # stations whose data were all flagged have zero autos: judged against the largest power
+            worst = max(worst, float(np.max(num / np.maximum(den, 1e-9 * auto.max() + 1e-300))))
     return worst
 
 

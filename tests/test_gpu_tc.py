@@ -19,7 +19,7 @@ import torch
 
 import oracle
 import synth
-from test_gpu_parity import make_corr, per_subband_rel, tone_block
+from test_gpu_parity import baseline_max_rel, make_corr, per_subband_rel, tone_block
 
 pytestmark = pytest.mark.gpu
 FS = synth.SAMPLE_RATE_HZ
@@ -112,10 +112,15 @@ def test_correct_planar_parity(kind, N, C, S):
     assert rel < tol, rel
 
 
-@pytest.mark.parametrize("kind,bound", [("f16", 5e-3), ("split", 1e-4), ("bf16", 3e-2)])
-def test_end_to_end_tc(kind, bound):
+@pytest.mark.parametrize("kind,bound,bl_bound", [("f16", 5e-3, 1e-3), ("split", 1e-4, 1e-4), ("bf16", 3e-2, 1e-2)])
+def test_end_to_end_tc(kind, bound, bl_bound):
     """64 stations x 2 pols, 2 subbands, int8 noise sigma 20 + a tone, 256
-    channels, 48 spectra (a slice of the 8-bit LOFAR workload's shape)."""
+    channels, 48 spectra (a slice of the 8-bit LOFAR workload's shape).
+    Normwise per subband below `bound`; per baseline, max |dV_ij| /
+    sqrt(|V_ii| |V_jj|) below `bl_bound` (operand rounding 2^-11 (FP16) or
+    2^-8 (BF16) relative, averaged down by sqrt(S) and taken at its worst
+    entry; split FP16 keeps 2^-22), so a wrong cross term cannot hide
+    behind the autocorrelations."""
     blk, tau, _ = tone_block(synth.BASE_SEED + 2, synth.CI8, 2, 64, 256, 48, sigma=20.0, amp=10.0)
     ref = oracle.fx(blk.fmt, blk.raw, 16, 256, 48, blk.taps, FS, blk.centres, tau, tau)
     c = make_corr(blk, precision=PREC[kind])
@@ -125,6 +130,27 @@ def test_end_to_end_tc(kind, bound):
     e = per_subband_rel(vis, ref)
     print(f"{kind}: relative visibility error per subband {e}")
     assert np.all(e < bound), e
+    assert baseline_max_rel(vis, ref, 64) < bl_bound
+
+
+@pytest.mark.parametrize("kind,bound,bl_bound", [("f16", 5e-3, 1e-3), ("split", 1e-4, 1e-4), ("bf16", 3e-2, 1e-2)])
+def test_end_to_end_tc_8bit_workload_shape(kind, bound, bl_bound):
+    """The precision workload's per-subband shape (64 stations x 2 pols, 256
+    channels, 768 spectra, int8 noise sigma 20 + one tone) on two subbands
+    through the production step (fused F-stage + tensor-core X-stage) against
+    the FP64 oracle: normwise below the stated tolerance (5e-3 FP16, 1e-4 split
+    FP16; BF16 reported at 3e-2) and per baseline max |dV_ij| /
+    sqrt(|V_ii| |V_jj|) below `bl_bound`."""
+    blk, tau, _ = tone_block(synth.BASE_SEED + 2, synth.CI8, 2, 64, 256, 768, sigma=20.0, amp=10.0)
+    ref = oracle.fx(blk.fmt, blk.raw, 16, 256, 768, blk.taps, FS, blk.centres, tau, tau)
+    c = make_corr(blk, precision=PREC[kind])
+    raw = torch.from_numpy(blk.raw).cuda()
+    t = torch.from_numpy(tau).cuda()
+    vis = c.correlate(c.channelize_correct(raw, t, t)).cpu().numpy().astype(np.float64)
+    e = per_subband_rel(vis, ref)
+    assert np.all(e < bound), e
+    assert baseline_max_rel(vis, ref, 64) < bl_bound
+    c.close()
 
 
 def test_tc_failure_detection_timeout():

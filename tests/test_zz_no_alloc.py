@@ -1,5 +1,6 @@
 """The allocation-free correction entry point (fx_correct_f32_noalloc) against
-the handle-based fx_correct, through the C ABI.
+the handle-based fx_correct and against the FP64 oracle's correction, through
+the C ABI.
 
 fx_correct_f32_noalloc exists for callers that may not allocate device memory
 (a fixed memory budget owned by the host program, a plugin host that forbids
@@ -16,6 +17,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -35,11 +37,15 @@ def _noalloc(lib, N, SB, C, S, centres, tb, te, bp, g, chan, out):
                                       _p(chan), _p(out), None)
 
 
-def test_noalloc_matches_fx_correct_on_two_calls():
+@pytest.mark.parametrize("N,SB,C,S", [(6, 3, 64, 37), (500, 1, 16, 20)])
+def test_noalloc_matches_fx_correct_on_two_calls(N, SB, C, S):
+    """Two calls in a row with different inputs, each equal to fx_correct
+    (same kernels, so within 2e-6) and to the oracle's correction (FP32
+    rotation of an FP64-formed phase: 2e-6 normwise). 500 stations is above
+    any shared-memory limit the correction could have per station."""
     import paper_1801_04834_gb300 as fxg
     from paper_1801_04834_gb300 import _abi
     lib = _abi.load()
-    N, SB, C, S = 6, 3, 64, 37
     centres = synth.subband_centres(SB)
     blk = synth.Block(0, SB, N, 2, C, 16, S, None, synth.kaiser_sinc_taps(16, C), centres)
     c = fxg.Correlator(N, SB, C, S, taps=blk.taps, centres=centres)
@@ -47,11 +53,14 @@ def test_noalloc_matches_fx_correct_on_two_calls():
     out = torch.empty(c.corr_shape(), dtype=torch.float32, device="cuda")
     for call in range(2):                       # two calls in a row, different inputs
         rng = np.random.default_rng(100 + call)
-        chan = _dev(synth.channelised_noise(200 + call, SB, N, 2, C, S, sigma=300.0))
+        chan_h = synth.channelised_noise(200 + call, SB, N, 2, C, S, sigma=300.0)
+        chan = _dev(chan_h)
         tb = rng.uniform(-5e-6, 5e-6, N)
         te = tb + rng.uniform(-2e-8, 2e-8, N)
-        bp = _dev(rng.uniform(0.7, 1.3, (N, C))) if call == 0 else None
-        g = _dev(synth.random_gains(rng, N))
+        bp_h = rng.uniform(0.7, 1.3, (N, C)) if call == 0 else None
+        bp = None if bp_h is None else _dev(bp_h)
+        g_h = synth.random_gains(rng, N)
+        g = _dev(g_h)
         d_tb, d_te = _dev(tb, torch.float64), _dev(te, torch.float64)
         ref = c.correct(chan, d_tb, d_te, bandpass=bp, gains=g)
         out.fill_(float("nan"))
@@ -60,6 +69,10 @@ def test_noalloc_matches_fx_correct_on_two_calls():
         torch.cuda.synchronize()
         rel = (torch.linalg.vector_norm((out - ref).double()) / torch.linalg.vector_norm(ref.double())).item()
         assert rel < 2e-6, f"call {call}: relative difference {rel}"
+        oref = oracle.correct(chan_h, FS, centres, tb, te, bandpass=bp_h, gains=g_h)
+        got = fxg.f32_unblock(out, S).cpu().numpy().astype(np.float64)
+        orel = np.linalg.norm(got - oref) / np.linalg.norm(oref)
+        assert orel < 2e-6, f"call {call}: relative error against the oracle {orel}"
     c.close()
 
 
@@ -75,3 +88,7 @@ def test_noalloc_rejects_oversize_and_bad_args():
     assert rc == _abi.FX_ERR_UNSUPPORTED
     rc = lib.fx_correct_f32_noalloc(4, 1, 64, 8, FS, None, _p(t), _p(t), None, None, _p(t), _p(t), None)
     assert rc == _abi.FX_ERR_INVALID
+    # more spectra than the correction's grid covers: rejected before any launch
+    rc = lib.fx_correct_f32_noalloc(1, 1, 16, 4194241, FS, _p(t), _p(t), _p(t), None, None, _p(t), _p(t), None)
+    assert rc == _abi.FX_ERR_INVALID
+    assert "out of range" in _abi.last_error()
