@@ -394,10 +394,14 @@ void fx_batch_destroy(fx_batch *b);
 
 /* Synchronises the device, then reports asynchronous failures of earlier
  * calls: FX_ERR_CUDA for a CUDA error, FX_ERR_TIMEOUT if a bounded device-side
- * wait of the tensor-core X-stage gave up (each wait has a budget of about two
- * seconds; the kernel then drains its in-flight copies, frees its tensor
- * memory and exits, and that call's visibilities are incomplete). *code (may
- * be NULL) receives the role that gave up: 1 loader, 2 MMA issuer, 3 epilogue.
+ * wait gave up (each wait has a budget of about two seconds). In the
+ * tensor-core X-stages the kernel then drains its in-flight copies, frees its
+ * tensor memory and exits, and that call's visibilities are incomplete; in
+ * the F-stage kernels (raw rows staged by bulk copies) the wait for a round's
+ * rows gives up and the kernel finishes on stale rows, so that call's output
+ * is invalid. *code (may be NULL) receives the role that gave up: 1 loader,
+ * 2 MMA issuer, 3 epilogue, 4 operand converter (TF32-split X-stage), 5 the
+ * F-stage's raw-row wait.
  * The status word is cleared by the call. Not capturable in a CUDA graph. */
 fx_status fx_poll_status(fx_handle *h, int *code);
 

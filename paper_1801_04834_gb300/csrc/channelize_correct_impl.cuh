@@ -309,7 +309,7 @@ constexpr size_t fused_ws_smem_bytes()
 {
     using W = FusedWsCfg<C>;
     return (size_t)C * sizeof(float2) + 2ull * kRound * W::NPC * C * kPols * sizeof(TIn) +
-           (2ull * W::USZ + 2ull * W::ESZ + (size_t)W::IC * C) * sizeof(float2);
+           (2ull * W::USZ + 2ull * W::ESZ + (size_t)W::IC * C) * sizeof(float2) + 16;   // + 2 mbarriers
 }
 
 // CTAs per SM the shared memory allows: 3 at C = 64, 2 at C = 16 (four stations' rows)
@@ -328,7 +328,7 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
                       const float2 *__restrict__ twiddle, const float2 *__restrict__ phase,
                       const float *__restrict__ bandpass, const float2 *__restrict__ gains, int N, int S, int I_pad,
                       int s_out, float scale, int rounds_per_cta, const float *__restrict__ flags, int s_base,
-                      int s_end)
+                      int s_end, int *__restrict__ status, long long budget)
 {
     using W = FusedWsCfg<C>;
     constexpr int R = W::R, NPC = W::NPC, NF = W::NF, IC = W::IC, ROW = W::ROW, PADG = W::PADG, USZ = W::USZ;
@@ -345,6 +345,8 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
     float2 *u = reinterpret_cast<float2 *>(inbuf + 2 * BUF_BYTES);   // [2][USZ]
     float2 *et = u + 2 * USZ;                                         // [2][NPC][C][EJ]
     float2 *bgt = et + 2 * ESZ;                                       // [IC][C] bandpass x gain
+    // raw-row mbarriers (one station per CTA: its rows arrive by bulk copy)
+    const unsigned rbar = tc::smem_u32(bgt + IC * C);
 
     const int tid = threadIdx.x;
     const int sb = blockIdx.z;
@@ -363,10 +365,29 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
         const float2 g = gains ? gains[n * kPols + il % kPols] : make_float2(1.f, 0.f);
         bgt[e] = make_float2(b * g.x * scale, b * g.y * scale);
     }
+    if constexpr (NPC == 1) {
+        if (tid == 0) {
+            tc::mbar_init(rbar, 1);
+            tc::mbar_init(rbar + 8, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+    }
     __syncthreads();
 
     if (tid < NF) {
         // ---------------- FIR threads: (station nl, channel c, pol p) ----------------
+        // one station (C = 64): thread 0 moves each round's raw rows (one
+        // contiguous run) with a bulk copy completing on rbar[buf]; several
+        // stations (C = 16): 16-byte cp.async by all FIR threads
+        const unsigned char *rows0 = reinterpret_cast<const unsigned char *>(raw) +
+                                     (((long long)sb * N + n0) * L) * kPols * sizeof(TIn);
+        auto issue = [&](int buf, int r0, int nrows) {
+            if (tid == 0) {
+                const int nv = max(0, min(nrows, rows_total - r0));
+                bulk_rows_issue(inbuf + buf * BUF_BYTES, rows0 + (long long)r0 * ROW_BYTES,
+                                (unsigned)(nv * ROW_BYTES), rbar + 8u * buf);
+            }
+        };
         auto stage = [&](int buf, int r0, int nrows) {
             const int chunks = nrows * ROW_BYTES / 16;
             for (int q = tid; q < NPC * chunks; q += NF) {
@@ -396,26 +417,41 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
 #pragma unroll
         for (int k = 0; k < T; ++k) h[k] = make_float2(taps[k * C + c], taps[k * C + c]);
 
-        stage(1, s0, T - 1);
-        cp_async_commit();
-        stage(0, s0 + T - 1, kRound);
-        cp_async_commit();
-        cp_async_wait<1>();
-        named_bar_sync(kBarRaw, NF);
+        if constexpr (NPC == 1) {
+            issue(1, s0, T - 1);                        // history rows: buffer 1, phase 0
+            issue(0, s0 + T - 1, kRound);               // round 0: buffer 0, phase 0
+            raw_wait(rbar + 8, 0, status, budget);
+        } else {
+            stage(1, s0, T - 1);
+            cp_async_commit();
+            stage(0, s0 + T - 1, kRound);
+            cp_async_commit();
+            cp_async_wait<1>();
+            named_bar_sync(kBarRaw, NF);
+        }
         float2 win[T];
         const TIn *in1 = reinterpret_cast<const TIn *>(inbuf + BUF_BYTES);
 #pragma unroll
         for (int k = 0; k < T - 1; ++k) win[k] = to_f2(in1[k * NF + tid]);
         win[T - 1] = make_float2(0.f, 0.f);
         named_bar_sync(kBarRaw, NF);
-        if (nrounds > 1) stage(1, s0 + T - 1 + kRound, kRound);
-        cp_async_commit();
+        if constexpr (NPC == 1) {
+            if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (nrounds > 1) issue(1, s0 + T - 1 + kRound, kRound);    // round 1: buffer 1, phase 1
+        } else {
+            if (nrounds > 1) stage(1, s0 + T - 1 + kRound, kRound);
+            cp_async_commit();
+        }
 
         for (int b = 0; b < nrounds; ++b) {
             const int q = b & 1;
             const int sr = s0 + b * kRound;
-            cp_async_wait<1>();
-            named_bar_sync(kBarRaw, NF);                // raw rows of round b are in
+            if constexpr (NPC == 1) {
+                raw_wait(rbar + 8u * q, (unsigned)(((b + q) / 2) & 1), status, budget);   // round b's rows
+            } else {
+                cp_async_wait<1>();
+                named_bar_sync(kBarRaw, NF);            // raw rows of round b are in
+            }
             if (b >= 2) named_bar_sync(kBarEmpty + q, ALL);   // FFT threads are done with u[q], et[q]
             const TIn *in = reinterpret_cast<const TIn *>(inbuf + q * BUF_BYTES);
             float2 *uq = u + q * USZ;
@@ -450,10 +486,15 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
             }
             named_bar_arrive(kBarFull + q, ALL);
             named_bar_sync(kBarRaw, NF);                // every FIR thread has read raw buffer q
-            if (b + 2 < nrounds) stage(q, s0 + T - 1 + (b + 2) * kRound, kRound);
-            cp_async_commit();
+            if constexpr (NPC == 1) {
+                if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if (b + 2 < nrounds) issue(q, s0 + T - 1 + (b + 2) * kRound, kRound);
+            } else {
+                if (b + 2 < nrounds) stage(q, s0 + T - 1 + (b + 2) * kRound, kRound);
+                cp_async_commit();
+            }
         }
-        cp_async_wait<0>();
+        if constexpr (NPC != 1) cp_async_wait<0>();
     } else {
         // ---------------- FFT threads ----------------
         const int t = tid - NF;
@@ -602,7 +643,7 @@ constexpr size_t ws256_smem_bytes()
 {
     using W = Ws256;
     return (size_t)W::C * sizeof(float2) + 2ull * kRound * W::C * kPols * sizeof(TIn) +
-           (2ull * W::USZ + 2ull * W::ESZ + 2ull * W::C) * sizeof(float2);
+           (2ull * W::USZ + 2ull * W::ESZ + 2ull * W::C) * sizeof(float2) + 16;   // + 2 mbarriers
 }
 
 template <int T, typename TIn, int OUT>
@@ -611,7 +652,7 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
                          const float2 *__restrict__ twiddle, const float2 *__restrict__ phase,
                          const float *__restrict__ bandpass, const float2 *__restrict__ gains, int N, int S,
                          int I_pad, int s_out, float scale, int rounds_per_cta, const float *__restrict__ flags,
-                         int s_base, int s_end)
+                         int s_base, int s_end, int *__restrict__ status, long long budget)
 {
     using W = Ws256;
     constexpr int C = W::C, R = W::R, NF = W::NF, ROW = W::ROW, USZ = W::USZ, RS = W::RS, EJ = W::EJ, ESZ = W::ESZ;
@@ -630,6 +671,7 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
     float2 *bgt = et + 2 * ESZ;                                       // [C] bandpass x gain x scale
     float2 *tw2 = bgt + C;                                            // [k1][n2] = W_C^(n2 k1): pass-1
                                                                       // lanes (n2) read consecutive entries
+    const unsigned rbar = tc::smem_u32(tw2 + C);                      // raw-row mbarriers [2]
     const int tid = threadIdx.x;
     const int sb = blockIdx.z;
     const int n = blockIdx.x / kPols, p = blockIdx.x % kPols;       // (station, pol) fastest
@@ -645,18 +687,24 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
         const float2 g = gains ? gains[n * kPols + p] : make_float2(1.f, 0.f);
         bgt[i] = make_float2(b * g.x * scale, b * g.y * scale);
     }
+    if (tid == 0) {
+        tc::mbar_init(rbar, 1);
+        tc::mbar_init(rbar + 8, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
 
     if (tid < NF) {
         // ---------------- FIR threads: channel c of input (n, p) ----------------
-        auto stage = [&](int buf, int r0, int nrows) {
-            const int chunks = nrows * ROW_BYTES / 16;
-            const unsigned char *src0 = reinterpret_cast<const unsigned char *>(raw) +
-                                        (((long long)sb * N + n) * L + (long long)r0 * C) * kPols * sizeof(TIn);
-            for (int q = tid; q < chunks; q += NF) {
-                const bool ok = r0 + (q * 16) / ROW_BYTES < rows_total;
-                cp_async16(inbuf + buf * BUF_BYTES + q * 16,
-                           ok ? src0 + q * 16 : reinterpret_cast<const unsigned char *>(raw), ok ? 16 : 0);
+        // the station's raw rows of a round are one contiguous run: thread 0
+        // moves it with a bulk copy completing on rbar[buf]
+        const unsigned char *rows0 = reinterpret_cast<const unsigned char *>(raw) +
+                                     (((long long)sb * N + n) * L) * kPols * sizeof(TIn);
+        auto issue = [&](int buf, int r0, int nrows) {
+            if (tid == 0) {
+                const int nv = max(0, min(nrows, rows_total - r0));
+                bulk_rows_issue(inbuf + buf * BUF_BYTES, rows0 + (long long)r0 * ROW_BYTES,
+                                (unsigned)(nv * ROW_BYTES), rbar + 8u * buf);
             }
         };
         const int c = tid;
@@ -669,26 +717,22 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
 #pragma unroll
         for (int k = 0; k < T; ++k) h[k] = make_float2(taps[k * C + c], taps[k * C + c]);
 
-        stage(1, s0, T - 1);
-        cp_async_commit();
-        stage(0, s0 + T - 1, kRound);
-        cp_async_commit();
-        cp_async_wait<1>();
-        named_bar_sync(kBarRaw, NF);
+        issue(1, s0, T - 1);                            // history rows: buffer 1, phase 0
+        issue(0, s0 + T - 1, kRound);                   // round 0: buffer 0, phase 0
+        raw_wait(rbar + 8, 0, status, budget);
         float2 win[T];
         const TIn *in1 = reinterpret_cast<const TIn *>(inbuf + BUF_BYTES);
 #pragma unroll
         for (int k = 0; k < T - 1; ++k) win[k] = to_f2(in1[k * C * kPols + c * kPols + p]);
         win[T - 1] = make_float2(0.f, 0.f);
         named_bar_sync(kBarRaw, NF);
-        if (nrounds > 1) stage(1, s0 + T - 1 + kRound, kRound);
-        cp_async_commit();
+        if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (nrounds > 1) issue(1, s0 + T - 1 + kRound, kRound);     // round 1: buffer 1, phase 1
 
         for (int b = 0; b < nrounds; ++b) {
             const int q = b & 1;
             const int sr = s0 + b * kRound;
-            cp_async_wait<1>();
-            named_bar_sync(kBarRaw, NF);
+            raw_wait(rbar + 8u * q, (unsigned)(((b + q) / 2) & 1), status, budget);   // round b's rows
             if (b >= 2) named_bar_sync(kBarEmpty + q, ALL);
             const TIn *in = reinterpret_cast<const TIn *>(inbuf + q * BUF_BYTES);
             float2 *uq = u + q * USZ;
@@ -718,11 +762,10 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
                 e = cmul(e, rot);
             }
             named_bar_arrive(kBarFull + q, ALL);
-            named_bar_sync(kBarRaw, NF);
-            if (b + 2 < nrounds) stage(q, s0 + T - 1 + (b + 2) * kRound, kRound);
-            cp_async_commit();
+            named_bar_sync(kBarRaw, NF);                // every FIR thread has read raw buffer q
+            if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (b + 2 < nrounds) issue(q, s0 + T - 1 + (b + 2) * kRound, kRound);
         }
-        cp_async_wait<0>();
     } else {
         // ---------------- FFT threads ----------------
         const int t = tid - NF;
@@ -833,7 +876,7 @@ cudaError_t launch_t(const Handle &h, const void *raw, void *corr, const float *
         if (e != cudaSuccess) return e;
         kern<<<grid, 2 * W::NF, smem, st>>>(reinterpret_cast<const TIn *>(raw), corr, h.d_taps, h.d_twiddle,
                                             h.d_phase, bandpass, gains, N, S, h.I_pad, s_out, scale, rpc, flags,
-                                            s_base, s_end);
+                                            s_base, s_end, h.d_status, h.tc_timeout_cycles);
         e = cudaGetLastError();
         if (e != cudaSuccess || OUT == 1) return e;
         return planar_pad(h, corr, OUT, rounds_total * kRound, s_out, st);
@@ -850,7 +893,7 @@ cudaError_t launch_t(const Handle &h, const void *raw, void *corr, const float *
         if (e != cudaSuccess) return e;
         kern<<<grid, 2 * Ws256::NF, smem, st>>>(reinterpret_cast<const TIn *>(raw), corr, h.d_taps, h.d_twiddle,
                                                 h.d_phase, bandpass, gains, N, S, h.I_pad, s_out, scale, rpc, flags,
-                                                s_base, s_end);
+                                                s_base, s_end, h.d_status, h.tc_timeout_cycles);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         return planar_pad(h, corr, OUT, rounds_total * kRound, s_out, st);

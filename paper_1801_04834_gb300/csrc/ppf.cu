@@ -215,13 +215,14 @@ constexpr size_t ppf_ws_smem_bytes()
 {
     using W = PpfWsCfg<C>;
     return (size_t)C * sizeof(float2) + 2ull * kRound * W::NPC * C * kPols * sizeof(TIn) +
-           2ull * W::NTR * W::ROW * sizeof(float2);
+           2ull * W::NTR * W::ROW * sizeof(float2) + 16;   // + 2 raw-row mbarriers
 }
 
 template <int C, int T, typename TIn>
 __global__ void __launch_bounds__(2 * PpfWsCfg<C>::NF, 3)
 ppf_ws_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *__restrict__ taps,
-              const float2 *__restrict__ twiddle, int N, int S, int rounds_per_cta)
+              const float2 *__restrict__ twiddle, int N, int S, int rounds_per_cta, int *__restrict__ status,
+              long long budget)
 {
     using W = PpfWsCfg<C>;
     constexpr int R = W::R, NPC = W::NPC, NF = W::NF, ROW = W::ROW, NTR = W::NTR;
@@ -236,6 +237,7 @@ ppf_ws_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const floa
     float2 *tw = reinterpret_cast<float2 *>(smem);
     unsigned char *inbuf = smem + C * sizeof(float2);
     float2 *u = reinterpret_cast<float2 *>(inbuf + 2 * BUF_BYTES);   // [2][NTR][ROW]
+    const unsigned rbar = tc::smem_u32(u + 2 * NTR * ROW);            // raw-row mbarriers [2]
 
     const int tid = threadIdx.x;
     const int sb = blockIdx.z;
@@ -246,10 +248,29 @@ ppf_ws_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const floa
     const int nrounds = min(rounds_per_cta, (S - s0 + kRound - 1) / kRound);
 
     for (int i = tid; i < C; i += ALL) tw[i] = twiddle[i];
+    if constexpr (NPC == 1) {
+        if (tid == 0) {
+            tc::mbar_init(rbar, 1);
+            tc::mbar_init(rbar + 8, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+    }
     __syncthreads();
 
     if (tid < NF) {
         // ---- FIR threads: thread = (station nl, channel c, pol p) ----
+        // one station (C = 64): thread 0 moves each round's raw rows (one
+        // contiguous run) with a bulk copy completing on rbar[buf]; several
+        // stations (C = 16): 16-byte cp.async by all FIR threads
+        const unsigned char *rows0 = reinterpret_cast<const unsigned char *>(raw) +
+                                     (((long long)sb * N + n0) * L) * kPols * sizeof(TIn);
+        auto issue = [&](int buf, int r0, int nrows) {
+            if (tid == 0) {
+                const int nv = max(0, min(nrows, rows_total - r0));
+                bulk_rows_issue(inbuf + buf * BUF_BYTES, rows0 + (long long)r0 * ROW_BYTES,
+                                (unsigned)(nv * ROW_BYTES), rbar + 8u * buf);
+            }
+        };
         auto stage = [&](int buf, int r0, int nrows) {
             const int chunks = nrows * ROW_BYTES / 16;
             for (int q = tid; q < NPC * chunks; q += NF) {
@@ -271,25 +292,40 @@ ppf_ws_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const floa
 #pragma unroll
         for (int k = 0; k < T; ++k) h[k] = make_float2(taps[k * C + c], taps[k * C + c]);
 
-        stage(1, s0, T - 1);                        // FIR history
-        cp_async_commit();
-        stage(0, s0 + T - 1, kRound);               // round 0
-        cp_async_commit();
-        cp_async_wait<1>();
-        named_bar_sync(kBarRaw, NF);
+        if constexpr (NPC == 1) {
+            issue(1, s0, T - 1);                        // FIR history: buffer 1, phase 0
+            issue(0, s0 + T - 1, kRound);               // round 0: buffer 0, phase 0
+            raw_wait(rbar + 8, 0, status, budget);
+        } else {
+            stage(1, s0, T - 1);                        // FIR history
+            cp_async_commit();
+            stage(0, s0 + T - 1, kRound);               // round 0
+            cp_async_commit();
+            cp_async_wait<1>();
+            named_bar_sync(kBarRaw, NF);
+        }
         float2 win[T];
         const TIn *in1 = reinterpret_cast<const TIn *>(inbuf + BUF_BYTES);
 #pragma unroll
         for (int k = 0; k < T - 1; ++k) win[k] = to_f2(in1[k * NF + tid]);
         win[T - 1] = make_float2(0.f, 0.f);
         named_bar_sync(kBarRaw, NF);
-        if (nrounds > 1) stage(1, s0 + T - 1 + kRound, kRound);
-        cp_async_commit();
+        if constexpr (NPC == 1) {
+            if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (nrounds > 1) issue(1, s0 + T - 1 + kRound, kRound);    // round 1: buffer 1, phase 1
+        } else {
+            if (nrounds > 1) stage(1, s0 + T - 1 + kRound, kRound);
+            cp_async_commit();
+        }
 
         for (int b = 0; b < nrounds; ++b) {
             const int q = b & 1;
-            cp_async_wait<1>();
-            named_bar_sync(kBarRaw, NF);                  // raw rows of round b are in
+            if constexpr (NPC == 1) {
+                raw_wait(rbar + 8u * q, (unsigned)(((b + q) / 2) & 1), status, budget);   // round b's rows
+            } else {
+                cp_async_wait<1>();
+                named_bar_sync(kBarRaw, NF);              // raw rows of round b are in
+            }
             if (b >= 2) named_bar_sync(kBarEmpty + q, ALL);   // the FFT threads are done with u[q]
             const TIn *in = reinterpret_cast<const TIn *>(inbuf + q * BUF_BYTES);
             float2 *uq = u + q * NTR * ROW;
@@ -303,10 +339,15 @@ ppf_ws_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const floa
             }
             named_bar_arrive(kBarFull + q, ALL);
             named_bar_sync(kBarRaw, NF);                  // every FIR thread has read raw buffer q
-            if (b + 2 < nrounds) stage(q, s0 + T - 1 + (b + 2) * kRound, kRound);
-            cp_async_commit();
+            if constexpr (NPC == 1) {
+                if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if (b + 2 < nrounds) issue(q, s0 + T - 1 + (b + 2) * kRound, kRound);
+            } else {
+                if (b + 2 < nrounds) stage(q, s0 + T - 1 + (b + 2) * kRound, kRound);
+                cp_async_commit();
+            }
         }
-        cp_async_wait<0>();
+        if constexpr (NPC != 1) cp_async_wait<0>();
     } else {
         // ---- FFT threads: task = (transform row, column); R lanes of one warp per row ----
         const int t = tid - NF;
@@ -369,7 +410,8 @@ cudaError_t launch_ws(const Handle &h, const void *raw, float2 *chan, cudaStream
     auto kern = ppf_ws_kernel<C, T, TIn>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, 2 * W::NF, smem, st>>>(reinterpret_cast<const TIn *>(raw), chan, h.d_taps, h.d_twiddle, N, S, rpc);
+    kern<<<grid, 2 * W::NF, smem, st>>>(reinterpret_cast<const TIn *>(raw), chan, h.d_taps, h.d_twiddle, N, S, rpc,
+                                        h.d_status, h.tc_timeout_cycles);
     return cudaGetLastError();
 }
 

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "tc_ptx.cuh"
 
 namespace fxi {
 namespace ppf {
@@ -37,6 +38,40 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, int
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Raw rows by the bulk-copy (TMA) engine: one contiguous run of a station's
+// time rows (global and shared addresses 16-byte aligned, a multiple of 16
+// bytes) lands in shared memory and completes on an mbarrier with its byte
+// count, so the FIR threads issue no per-chunk copies.
+__device__ __forceinline__ void bulk_rows(void *smem_dst, const void *gsrc, unsigned bytes, unsigned bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     tc::smem_u32(smem_dst)),
+                 "l"(gsrc), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// Expect `bytes` on `bar` (one arrival) and start the copy; a zero-byte run
+// (rows past the block's end) only completes the phase.
+__device__ __forceinline__ void bulk_rows_issue(void *smem_dst, const void *gsrc, unsigned bytes, unsigned bar)
+{
+    tc::mbar_arrive_expect_tx(bar, bytes);
+    if (bytes) bulk_rows(smem_dst, gsrc, bytes, bar);
+}
+// Bounded wait for a raw-row phase: after `budget` clock cycles the wait gives
+// up, records code 5 (F-stage loader) in the status word and returns, so the
+// kernel finishes (on stale rows) instead of hanging; fx_poll_status reports it.
+constexpr int kStatusLoader = 5;
+__device__ __forceinline__ void raw_wait(unsigned bar, unsigned parity, int *status, long long budget)
+{
+    if (tc::mbar_try_wait(bar, parity)) return;
+    const long long t0 = clock64();
+    while (!tc::mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > budget) {
+            if (status) atomicCAS(status, 0, kStatusLoader);
+            return;
+        }
+    }
+}
 
 // Named CTA barriers (hardware barriers with fixed arrival counts, like
 // __syncthreads, which uses id 0) for the warp-specialised kernels: FIR warps
