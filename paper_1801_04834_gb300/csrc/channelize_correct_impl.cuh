@@ -622,9 +622,10 @@ __global__ void planar_pad_kernel(unsigned short *__restrict__ corr, long long n
 // station's two pols are neighbours in the grid and read the same raw rows
 // (the second read mostly from L2). FIR round b -> u[b & 1] and the whole
 // per-sample factor bandpass x gain x flag x exp(i phi) of its 16 spectra
-// (one __sincosf per channel and round, then rotations by exp(i step),
-// computed in FP32 from the FP64-derived step; bandpass x gain is constant
-// per channel within a CTA, which serves one input) -> FULL; FFT round b:
+// (one __sincosf per channel and round, multiplied once by bandpass x gain,
+// then rotations by exp(i step) computed in FP32 from the FP64-derived step;
+// bandpass x gain is constant per channel within a CTA, which serves one
+// input) -> FULL; FFT round b:
 // pass 1 (row = 16 lanes), transposed into
 // P1[k1][n2][row] over u[b & 1] after barrier FFT, pass 2 with lane = spectrum
 // (a half-warp per k1), so a warp store is 2 x 32 bytes of planar rows.
@@ -755,11 +756,20 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
                 r = fmaf(-kq, 1.9353071795864769e-3f, r);
                 __sincosf(r, &e.y, &e.x);
             }
+            e = cmul(bgc, e);                           // the anchor carries bandpass x gain
+            if (flags) {
 #pragma unroll
-            for (int j = 0; j < kRound; ++j) {
-                const float fw = flags ? flags[(long long)n * S + min(sr + j, S - 1)] : 1.f;
-                eq[j] = cmul(bgc, make_float2(e.x * fw, e.y * fw));     // the whole per-sample factor
-                e = cmul(e, rot);
+                for (int j = 0; j < kRound; ++j) {
+                    const float fw = flags[(long long)n * S + min(sr + j, S - 1)];
+                    eq[j] = make_float2(e.x * fw, e.y * fw);     // the whole per-sample factor
+                    e = cmul(e, rot);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < kRound; ++j) {
+                    eq[j] = e;
+                    e = cmul(e, rot);
+                }
             }
             named_bar_arrive(kBarFull + q, ALL);
             named_bar_sync(kBarRaw, NF);                // every FIR thread has read raw buffer q
