@@ -78,7 +78,7 @@ typedef enum { FX_CI16 = 0, FX_CI8 = 1, FX_CI4 = 2 } fx_format;
  * FIR and FFT always run in FP32; the X-stage always accumulates in FP32.
  * FX_TF32_SPLIT: FP32 corrected samples in the planar layout; the X-stage
  * splits each into hi + lo TF32 parts on the tensor cores (hi hi' + hi lo' +
- * lo hi', FP32 accumulation), which holds FP32's error bound; at most 64
+ * lo hi', FP32 accumulation), which holds FP32's error bound; at most 512
  * stations, operand_scale must be 1. */
 typedef enum { FX_F32 = 0, FX_F16 = 1, FX_BF16 = 2, FX_F16_SPLIT = 3, FX_TF32_SPLIT = 4 } fx_precision;
 
@@ -204,7 +204,11 @@ fx_status fx_channelize_correct(fx_handle *h, const void *d_raw, const double *d
  *   vis[sb][k][b(i,j)][2p+q] = sum_{s<S} Y[i,p] conj(Y[j,q])  for i <= j.
  * d_corr: corr layout of the handle's precision; d_vis: vis layout. FP32
  * operands run on the CUDA cores; FP16/BF16/split operands on the tcgen05
- * tensor cores with FP32 accumulation (split: hi*hi' + hi*lo' + lo*hi'). */
+ * tensor cores with FP32 accumulation (split: hi*hi' + hi*lo' + lo*hi');
+ * FX_TF32_SPLIT operands (FP32 planar) on the tcgen05 tensor cores as hi/lo
+ * TF32 parts with FP32 accumulation, accumulator chains restarted every 64
+ * spectra and summed in IEEE FP32 (FP32 accuracy, any station count up to
+ * 512; results reproducible run to run). */
 fx_status fx_correlate(fx_handle *h, const void *d_corr, float *d_vis, fx_stream stream);
 
 /* End to end from host memory: raw samples in, visibilities out, for all
