@@ -404,8 +404,9 @@ void fx_batch_destroy(fx_batch *b);
  * the F-stage kernels (raw rows staged by bulk copies) the wait for a round's
  * rows gives up and the kernel finishes on stale rows, so that call's output
  * is invalid. *code (may be NULL) receives the role that gave up: 1 loader,
- * 2 MMA issuer, 3 epilogue, 4 operand converter (TF32-split X-stage), 5 the
- * F-stage's raw-row wait.
+ * 2 MMA issuer, 3 epilogue, 4 operand converter (TF32-split X-stage), 6 the
+ * F-stage's raw-row wait (code 5, a clamped coarse shift of fx_stream_block,
+ * returns FX_ERR_INVALID instead).
  * The status word is cleared by the call. Not capturable in a CUDA graph. */
 fx_status fx_poll_status(fx_handle *h, int *code);
 

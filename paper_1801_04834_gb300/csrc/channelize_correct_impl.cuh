@@ -328,7 +328,7 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
                       const float2 *__restrict__ twiddle, const float2 *__restrict__ phase,
                       const float *__restrict__ bandpass, const float2 *__restrict__ gains, int N, int S, int I_pad,
                       int s_out, float scale, int rounds_per_cta, const float *__restrict__ flags, int s_base,
-                      int s_end, int *__restrict__ status, long long budget)
+                      int s_end, int *__restrict__ status, long long budget, int no_loads)
 {
     using W = FusedWsCfg<C>;
     constexpr int R = W::R, NPC = W::NPC, NF = W::NF, IC = W::IC, ROW = W::ROW, PADG = W::PADG, USZ = W::USZ;
@@ -382,7 +382,7 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
         const unsigned char *rows0 = reinterpret_cast<const unsigned char *>(raw) +
                                      (((long long)sb * N + n0) * L) * kPols * sizeof(TIn);
         auto issue = [&](int buf, int r0, int nrows) {
-            if (tid == 0) {
+            if (tid == 0 && !no_loads) {            // no_loads: failure-detection test hook
                 const int nv = max(0, min(nrows, rows_total - r0));
                 bulk_rows_issue(inbuf + buf * BUF_BYTES, rows0 + (long long)r0 * ROW_BYTES,
                                 (unsigned)(nv * ROW_BYTES), rbar + 8u * buf);
@@ -653,7 +653,7 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
                          const float2 *__restrict__ twiddle, const float2 *__restrict__ phase,
                          const float *__restrict__ bandpass, const float2 *__restrict__ gains, int N, int S,
                          int I_pad, int s_out, float scale, int rounds_per_cta, const float *__restrict__ flags,
-                         int s_base, int s_end, int *__restrict__ status, long long budget)
+                         int s_base, int s_end, int *__restrict__ status, long long budget, int no_loads)
 {
     using W = Ws256;
     constexpr int C = W::C, R = W::R, NF = W::NF, ROW = W::ROW, USZ = W::USZ, RS = W::RS, EJ = W::EJ, ESZ = W::ESZ;
@@ -702,7 +702,7 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
         const unsigned char *rows0 = reinterpret_cast<const unsigned char *>(raw) +
                                      (((long long)sb * N + n) * L) * kPols * sizeof(TIn);
         auto issue = [&](int buf, int r0, int nrows) {
-            if (tid == 0) {
+            if (tid == 0 && !no_loads) {            // no_loads: failure-detection test hook
                 const int nv = max(0, min(nrows, rows_total - r0));
                 bulk_rows_issue(inbuf + buf * BUF_BYTES, rows0 + (long long)r0 * ROW_BYTES,
                                 (unsigned)(nv * ROW_BYTES), rbar + 8u * buf);
@@ -886,7 +886,7 @@ cudaError_t launch_t(const Handle &h, const void *raw, void *corr, const float *
         if (e != cudaSuccess) return e;
         kern<<<grid, 2 * W::NF, smem, st>>>(reinterpret_cast<const TIn *>(raw), corr, h.d_taps, h.d_twiddle,
                                             h.d_phase, bandpass, gains, N, S, h.I_pad, s_out, scale, rpc, flags,
-                                            s_base, s_end, h.d_status, h.tc_timeout_cycles);
+                                            s_base, s_end, h.d_status, h.tc_timeout_cycles, h.tc_test_no_tma);
         e = cudaGetLastError();
         if (e != cudaSuccess || OUT == 1) return e;
         return planar_pad(h, corr, OUT, rounds_total * kRound, s_out, st);
@@ -903,7 +903,8 @@ cudaError_t launch_t(const Handle &h, const void *raw, void *corr, const float *
         if (e != cudaSuccess) return e;
         kern<<<grid, 2 * Ws256::NF, smem, st>>>(reinterpret_cast<const TIn *>(raw), corr, h.d_taps, h.d_twiddle,
                                                 h.d_phase, bandpass, gains, N, S, h.I_pad, s_out, scale, rpc, flags,
-                                                s_base, s_end, h.d_status, h.tc_timeout_cycles);
+                                                s_base, s_end, h.d_status, h.tc_timeout_cycles,
+                                                h.tc_test_no_tma);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         return planar_pad(h, corr, OUT, rounds_total * kRound, s_out, st);

@@ -222,7 +222,7 @@ template <int C, int T, typename TIn>
 __global__ void __launch_bounds__(2 * PpfWsCfg<C>::NF, 3)
 ppf_ws_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const float *__restrict__ taps,
               const float2 *__restrict__ twiddle, int N, int S, int rounds_per_cta, int *__restrict__ status,
-              long long budget)
+              long long budget, int no_loads)
 {
     using W = PpfWsCfg<C>;
     constexpr int R = W::R, NPC = W::NPC, NF = W::NF, ROW = W::ROW, NTR = W::NTR;
@@ -265,7 +265,7 @@ ppf_ws_kernel(const TIn *__restrict__ raw, float2 *__restrict__ chan, const floa
         const unsigned char *rows0 = reinterpret_cast<const unsigned char *>(raw) +
                                      (((long long)sb * N + n0) * L) * kPols * sizeof(TIn);
         auto issue = [&](int buf, int r0, int nrows) {
-            if (tid == 0) {
+            if (tid == 0 && !no_loads) {            // no_loads: failure-detection test hook
                 const int nv = max(0, min(nrows, rows_total - r0));
                 bulk_rows_issue(inbuf + buf * BUF_BYTES, rows0 + (long long)r0 * ROW_BYTES,
                                 (unsigned)(nv * ROW_BYTES), rbar + 8u * buf);
@@ -411,7 +411,7 @@ cudaError_t launch_ws(const Handle &h, const void *raw, float2 *chan, cudaStream
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, 2 * W::NF, smem, st>>>(reinterpret_cast<const TIn *>(raw), chan, h.d_taps, h.d_twiddle, N, S, rpc,
-                                        h.d_status, h.tc_timeout_cycles);
+                                        h.d_status, h.tc_timeout_cycles, h.tc_test_no_tma);
     return cudaGetLastError();
 }
 

@@ -58,9 +58,9 @@ __device__ __forceinline__ void bulk_rows_issue(void *smem_dst, const void *gsrc
     if (bytes) bulk_rows(smem_dst, gsrc, bytes, bar);
 }
 // Bounded wait for a raw-row phase: after `budget` clock cycles the wait gives
-// up, records code 5 (F-stage loader) in the status word and returns, so the
+// up, records code 6 (F-stage loader) in the status word and returns, so the
 // kernel finishes (on stale rows) instead of hanging; fx_poll_status reports it.
-constexpr int kStatusLoader = 5;
+constexpr int kStatusLoader = 6;
 __device__ __forceinline__ void raw_wait(unsigned bar, unsigned parity, int *status, long long budget)
 {
     if (tc::mbar_try_wait(bar, parity)) return;

@@ -1,5 +1,6 @@
 """CUDA-graph capture of the production step, and the bounded-wait failure
-path of the tensor-core beamformer and TF32-split X-stage.
+path of the tensor-core beamformer, the TF32-split X-stage and the F-stage's
+raw-row waits.
 
 Failure detection is tested without a GPU fault: with FX_FLAG_TEST_NO_LOADS
 the kernels' TMA producer issues no loads, so the consumers' mbarrier waits
@@ -82,6 +83,30 @@ def test_tf32_failure_detection_timeout():
     c.correlate(corr)
     rc, code = c.poll_status()
     assert rc == fxg._abi.FX_ERR_TIMEOUT and code in (1, 2, 3, 4), (rc, code)
+    assert c.poll_status() == (0, 0)
+    c.close()
+    _normal_call_works()
+
+
+@pytest.mark.parametrize("C,precision,call", [(64, 4, "channelize_correct"), (64, 0, "channelize_correct"),
+                                              (256, 1, "channelize_correct"), (64, 0, "channelize")])
+def test_fstage_failure_detection_timeout(C, precision, call):
+    """The F-stage kernels wait for each round's raw rows (moved by bulk copies)
+    with a bounded wait. With FX_FLAG_TEST_NO_LOADS no copy is issued, every
+    wait runs out (about a millisecond each), the kernel records role 6 and
+    finishes on stale rows without hanging; fx_poll_status reports
+    FX_ERR_TIMEOUT with code 6, clears it, and the context stays usable."""
+    import paper_1801_04834_gb300 as fxg
+    blk = synth.make_block(2, synth.CI16, 1, 2, C, 32)
+    c = make_corr(blk, precision=precision, extra_flags=fxg._abi.FX_FLAG_TEST_NO_LOADS)
+    raw = torch.from_numpy(blk.raw).cuda()
+    t = torch.zeros(2, dtype=torch.float64, device="cuda")
+    if call == "channelize":
+        c.channelize(raw)
+    else:
+        c.channelize_correct(raw, t, t)
+    rc, code = c.poll_status()
+    assert rc == fxg._abi.FX_ERR_TIMEOUT and code == 6, (rc, code)
     assert c.poll_status() == (0, 0)
     c.close()
     _normal_call_works()
