@@ -59,9 +59,10 @@ class Oracle:
         L.fxo_correlate.argtypes = [P, I, I, I, I, I, P]
         L.fxo_fx.argtypes = [I, P, I, I, I, I, I, I, P, D, P, P, P, P, P, P]
         L.fxo_vjp.argtypes = [P, I, I, I, I, I, D, P, P, P, P, P, P, P]
+        L.fxo_vjp_interp.argtypes = [P, I, I, I, I, I, D, P, P, P, P, P, P, P, P, P]
         L.fxo_beamform.argtypes = [P, I, I, I, I, I, D, P, I, P, P, I, I, P]
         L.fxo_beamform_incoherent.argtypes = [P, I, I, I, I, I, P, I, I, P]
-        for f in (L.fxo_channelize, L.fxo_correct, L.fxo_correlate, L.fxo_fx, L.fxo_vjp,
+        for f in (L.fxo_channelize, L.fxo_correct, L.fxo_correlate, L.fxo_fx, L.fxo_vjp, L.fxo_vjp_interp,
                   L.fxo_beamform, L.fxo_beamform_incoherent, L.fxo_threads):
             f.restype = I
         self._L = L
@@ -134,6 +135,21 @@ class Oracle:
                                     _ptr(_f64(grad_vis)), _ptr(gg), _ptr(gt)), "vjp")
         return gg, gt
 
+    def vjp_interp(self, chan, fs, centres, tau_begin, tau_end, grad_vis, bandpass=None, gains=None):
+        """Gradient of a real loss through correct+correlate with delays moving
+        linearly from tau_begin to tau_end over the block. Returns (grad_gains
+        [N][P][2], grad_tau_begin [N], grad_tau_end [N])."""
+        chan = _f64(chan)
+        SB, N, P, S, C, _ = chan.shape
+        gg = np.empty((N, P, 2))
+        gb = np.empty(N)
+        ge = np.empty(N)
+        self._check(self._L.fxo_vjp_interp(_ptr(chan), SB, N, P, C, S, fs, _ptr(_f64(centres)),
+                                           _ptr(_f64(tau_begin)), _ptr(_f64(tau_end)), _ptr(_f64(bandpass)),
+                                           _ptr(_f64(gains)), _ptr(_f64(grad_vis)), _ptr(gg), _ptr(gb),
+                                           _ptr(ge)), "vjp_interp")
+        return gg, gb, ge
+
     def beamform(self, corr, fs, centres, delays, weights=None, mode=0, tint=1):
         """Coherent beams from corr [SB][C][S][N][P][2]; delays [NB][N] seconds,
         weights [N] real. mode 0: voltages [SB][NB][C][S][4]; 1: Stokes I
@@ -196,6 +212,10 @@ def fx(*a, **k):
 
 def vjp(*a, **k):
     return default().vjp(*a, **k)
+
+
+def vjp_interp(*a, **k):
+    return default().vjp_interp(*a, **k)
 
 
 def beamform(*a, **k):

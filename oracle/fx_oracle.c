@@ -15,6 +15,8 @@
  *   fxo_correlate   explicit sum over time of Y_ip * conj(Y_jq), i <= j
  *   fxo_vjp         gradient of a real loss through correct + correlate,
  *                   by the chain rule entry by entry (constant delays)
+ *   fxo_vjp_interp  the same with delays interpolated over the block, by the
+ *                   chain rule sample by sample (gradients for both ends)
  *   fxo_beamform    coherent beams: per-sample phase-shifted station sum,
  *                   then complex voltages or Stokes I / IQUV
  *   fxo_beamform_incoherent  Stokes per station, then the weighted station sum
@@ -322,6 +324,106 @@ int fxo_vjp(const double *chan, int SB, int N, int P, int C, int S, double fs,
     }
     free(gg);
     free(gt);
+    return 0;
+}
+
+/* Gradient of a real loss L(V) through correct + correlate when each
+ * station's delay moves linearly over the block (Sec. "Signal processing
+ * with GPU kernels": the phase is formed at the block's start and end and
+ * interpolated in between), by the chain rule sample by sample:
+ *   Y_a(s) = g_a b_i(k) exp(2 pi i f_k tau_i(s)) X_a(s),
+ *   tau_i(s) = tau_begin[i] + (tau_end[i] - tau_begin[i]) s / S,
+ *   dY_a(s)/dtau_begin[i] = 2 pi i f_k (1 - s/S) Y_a(s),
+ *   dY_a(s)/dtau_end[i]   = 2 pi i f_k (s/S) Y_a(s),
+ *   dY_a(s)/dRe(g_a) = U_a(s), dY_a(s)/dIm(g_a) = i U_a(s), U_a = Y_a / g_a,
+ * and V_ab = sum_s Y_a(s) conj(Y_b(s)), dL = sum Re(conj(G) dV) with
+ * G = dL/dRe(V) + i dL/dIm(V). Outputs grad_gains [N][P][2],
+ * grad_tau_begin [N], grad_tau_end [N]. */
+int fxo_vjp_interp(const double *chan, int SB, int N, int P, int C, int S, double fs,
+                   const double *centres, const double *tau_begin, const double *tau_end,
+                   const double *bandpass, const double *gains, const double *grad_vis,
+                   double *grad_gains, double *grad_tb, double *grad_te)
+{
+    if (P != 2) return -1;
+    const size_t B = (size_t)N * (N + 1) / 2;
+    for (int a = 0; a < N * P * 2; ++a) grad_gains[a] = 0.0;
+    for (int n = 0; n < N; ++n) grad_tb[n] = grad_te[n] = 0.0;
+    const int slots = SB * C;
+    const size_t per = (size_t)N * P * 2 + 2 * (size_t)N;          /* gains, tau_begin, tau_end */
+    double *acc = calloc((size_t)slots * per, sizeof(double));
+    double *ure = malloc(sizeof(double) * (size_t)slots * N * P * S);
+    double *uim = malloc(sizeof(double) * (size_t)slots * N * P * S);
+    if (!acc || !ure || !uim) { free(acc); free(ure); free(uim); return -3; }
+
+#pragma omp parallel for collapse(2) schedule(dynamic)
+    for (int sb = 0; sb < SB; ++sb)
+        for (int k = 0; k < C; ++k) {
+            const size_t slot = (size_t)sb * C + k;
+            double *my = acc + slot * per;
+            double *my_tb = my + (size_t)N * P * 2, *my_te = my_tb + N;
+            double *Ur = ure + slot * N * P * S, *Ui = uim + slot * N * P * S;
+            const double f = channel_freq(centres, sb, k, C, fs);
+            /* U_a(s) = b_i exp(2 pi i f tau_i(s)) X_a(s): the corrected sample before the gain */
+            for (int n = 0; n < N; ++n)
+                for (int p = 0; p < P; ++p)
+                    for (int s = 0; s < S; ++s) {
+                        const double *x = chan + ((((size_t)sb * N + n) * P + p) * S + s) * (size_t)C * 2 + 2 * k;
+                        const double tau = tau_begin[n] + (tau_end[n] - tau_begin[n]) * (double)s / (double)S;
+                        const double ph = TWO_PI * f * tau;
+                        const double bw = bandpass ? bandpass[(size_t)n * C + k] : 1.0;
+                        const double er = bw * cos(ph), ei = bw * sin(ph);
+                        const size_t u = ((size_t)n * P + p) * S + s;
+                        Ur[u] = er * x[0] - ei * x[1];
+                        Ui[u] = er * x[1] + ei * x[0];
+                    }
+            for (int j = 0; j < N; ++j)
+                for (int i = 0; i <= j; ++i)
+                    for (int p = 0; p < 2; ++p)
+                        for (int q = 0; q < 2; ++q) {
+                            const double gar = gains ? gains[((size_t)i * P + p) * 2] : 1.0;
+                            const double gai = gains ? gains[((size_t)i * P + p) * 2 + 1] : 0.0;
+                            const double gbr = gains ? gains[((size_t)j * P + q) * 2] : 1.0;
+                            const double gbi = gains ? gains[((size_t)j * P + q) * 2 + 1] : 0.0;
+                            const size_t b = (size_t)j * (j + 1) / 2 + i;
+                            const double *G = grad_vis + (((slot * B) + b) * 4 + (2 * p + q)) * 2;
+                            const double Gr = G[0], Gi = G[1];
+                            for (int s = 0; s < S; ++s) {
+                                const size_t ua = ((size_t)i * P + p) * S + s, ub = ((size_t)j * P + q) * S + s;
+                                /* Y = g U */
+                                const double yar = gar * Ur[ua] - gai * Ui[ua], yai = gar * Ui[ua] + gai * Ur[ua];
+                                const double ybr = gbr * Ur[ub] - gbi * Ui[ub], ybi = gbr * Ui[ub] + gbi * Ur[ub];
+                                /* P = Y_a conj(Y_b) */
+                                const double pr = yar * ybr + yai * ybi, pi = yai * ybr - yar * ybi;
+                                /* dL for dV = c * P, c = i w: Re(conj(G) i w P) = w (-Gr Pi + Gi Pr) */
+                                const double w = TWO_PI * f;
+                                const double t = w * (-Gr * pi + Gi * pr);
+                                const double fe = (double)s / (double)S, fb = 1.0 - fe;
+                                my_tb[i] += fb * t;
+                                my_te[i] += fe * t;
+                                my_tb[j] -= fb * t;
+                                my_te[j] -= fe * t;
+                                /* gains: dV/dRe(g_a) = U_a conj(Y_b), dV/dIm(g_a) = i U_a conj(Y_b) */
+                                const double d1r = Ur[ua] * ybr + Ui[ua] * ybi, d1i = Ui[ua] * ybr - Ur[ua] * ybi;
+                                my[((size_t)i * P + p) * 2] += Gr * d1r + Gi * d1i;
+                                my[((size_t)i * P + p) * 2 + 1] += Gr * (-d1i) + Gi * d1r;
+                                /* dV/dRe(g_b) = Y_a conj(U_b), dV/dIm(g_b) = -i Y_a conj(U_b) */
+                                const double d2r = yar * Ur[ub] + yai * Ui[ub], d2i = yai * Ur[ub] - yar * Ui[ub];
+                                my[((size_t)j * P + q) * 2] += Gr * d2r + Gi * d2i;
+                                my[((size_t)j * P + q) * 2 + 1] += Gr * d2i + Gi * (-d2r);
+                            }
+                        }
+        }
+    for (int t = 0; t < slots; ++t) {
+        const double *my = acc + (size_t)t * per;
+        for (int a = 0; a < N * P * 2; ++a) grad_gains[a] += my[a];
+        for (int n = 0; n < N; ++n) {
+            grad_tb[n] += my[(size_t)N * P * 2 + n];
+            grad_te[n] += my[(size_t)N * P * 2 + N + n];
+        }
+    }
+    free(acc);
+    free(ure);
+    free(uim);
     return 0;
 }
 

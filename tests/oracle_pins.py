@@ -20,6 +20,9 @@ What pins what:
   linearity          sums over two halves of the block add up to the whole
   gradient_fd        vjp vs central finite differences of the loss
   gradient_truth     zero loss and zero gradient at the true parameters
+  gradient_interp    vjp_interp (delays moving over the block) vs finite
+                     differences in the gains and both delay ends; at equal
+                     ends it agrees with vjp
   ci4_decode         4-bit nibble decoding (hand-decoded bytes, int16 equivalence)
   flags              lost-data weights and per-baseline valid-spectrum counts
   beam_point_source  beam steered at a plane wave sums in phase (closed form);
@@ -308,6 +311,56 @@ def pin_gradient_truth(o):
     assert L2 > 0
 
 
+def _loss_interp(o, chan, centres, gains, tb, te, bandpass, w, M):
+    V = cplx(o.correlate(o.correct(chan, FS, centres, tb, te, bandpass=bandpass, gains=gains)))
+    return float(np.sum(w * np.abs(V - M) ** 2)), V
+
+
+def pin_gradient_interp(o):
+    """vjp_interp (delays moving linearly over the block) against central
+    finite differences of L = sum w |V - M|^2 in the gains and in both delay
+    ends, and, at equal ends, against vjp: the same gain gradient, and the two
+    delay gradients add up to the constant-delay one (moving both ends
+    together moves the whole delay)."""
+    chan, centres, gains, tb, bandpass, w, M = _grad_problem(12)
+    rng = np.random.default_rng(13)
+    te = tb + rng.uniform(-30e-9, 30e-9, len(tb))
+    L0, V = _loss_interp(o, chan, centres, gains, tb, te, bandpass, w, M)
+    G = 2 * w * (V - M)
+    Gv = np.stack([G.real, G.imag], -1)
+    gg, gb, ge = o.vjp_interp(chan, FS, centres, tb, te, Gv, bandpass=bandpass, gains=gains)
+    h = 1e-3
+    fd_g = np.zeros_like(gains)
+    for idx in np.ndindex(gains.shape):
+        gp, gm = gains.copy(), gains.copy()
+        gp[idx] += h
+        gm[idx] -= h
+        fd_g[idx] = (_loss_interp(o, chan, centres, gp, tb, te, bandpass, w, M)[0]
+                     - _loss_interp(o, chan, centres, gm, tb, te, bandpass, w, M)[0]) / (2 * h)
+    ht = 1e-12
+    fd_b, fd_e = np.zeros_like(tb), np.zeros_like(te)
+    for n in range(len(tb)):
+        for arr, out, which in ((tb, fd_b, 0), (te, fd_e, 1)):
+            ap, am = arr.copy(), arr.copy()
+            ap[n] += ht
+            am[n] -= ht
+            args_p = (ap, te) if which == 0 else (tb, ap)
+            args_m = (am, te) if which == 0 else (tb, am)
+            out[n] = (_loss_interp(o, chan, centres, gains, *args_p, bandpass, w, M)[0]
+                      - _loss_interp(o, chan, centres, gains, *args_m, bandpass, w, M)[0]) / (2 * ht)
+    assert np.linalg.norm(gg - fd_g) <= 1e-5 * np.linalg.norm(fd_g), "gain gradient vs FD"
+    assert np.linalg.norm(gb - fd_b) <= 1e-4 * np.linalg.norm(fd_b), "begin-delay gradient vs FD"
+    assert np.linalg.norm(ge - fd_e) <= 1e-4 * np.linalg.norm(fd_e), "end-delay gradient vs FD"
+    # equal ends: consistent with the constant-delay gradient
+    _, V1 = _loss_interp(o, chan, centres, gains, tb, tb, bandpass, w, M)
+    G1 = 2 * w * (V1 - M)
+    G1v = np.stack([G1.real, G1.imag], -1)
+    gg1, gb1, ge1 = o.vjp_interp(chan, FS, centres, tb, tb, G1v, bandpass=bandpass, gains=gains)
+    gg0, gt0 = o.vjp(chan, FS, centres, tb, G1v, bandpass=bandpass, gains=gains)
+    assert np.allclose(gg1, gg0, rtol=1e-9, atol=1e-9 * np.abs(gg0).max()), "gains at constant delay"
+    assert np.allclose(gb1 + ge1, gt0, rtol=1e-9, atol=1e-9 * np.abs(gt0).max()), "delays at constant delay"
+
+
 def pin_fx_chain(o):
     """The whole-chain entry equals its three steps run one after another."""
     blk, tau, _ = _point_source_setup(11, N=3, C=8, S=5, SB=1)
@@ -501,7 +554,7 @@ def pin_incoherent(o):
                            o.beamform(noise, FS, centres, np.zeros((1, N)), e, mode=2, tint=3), rtol=1e-12)
 
 
-ALL_PINS = [pin_fir_delta, pin_tone, pin_dft_vs_numpy, pin_point_source, pin_bandpass,
+ALL_PINS = [pin_gradient_interp, pin_fir_delta, pin_tone, pin_dft_vs_numpy, pin_point_source, pin_bandpass,
             pin_delay_ramp, pin_correlate_einsum, pin_hermitian, pin_linearity,
             pin_gradient_fd, pin_gradient_truth, pin_fx_chain, pin_ci4_decode, pin_flags,
             pin_beam_point_source, pin_beam_station_sum, pin_stokes, pin_incoherent]

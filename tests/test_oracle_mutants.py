@@ -42,6 +42,11 @@ MUTANTS = [
     ("vjp_tau_sign", "my_gt[j] -= Gre * dtre + Gim * dtim;", "my_gt[j] += Gre * dtre + Gim * dtim;"),
     ("vjp_imag_gain_sign", "my_gg[((size_t)i * P + p) * 2 + 1] += Gre * (-d1im) + Gim * d1re;",
      "my_gg[((size_t)i * P + p) * 2 + 1] += Gre * d1im + Gim * d1re;"),
+    ("vjp_interp_weights_swapped", "const double fe = (double)s / (double)S, fb = 1.0 - fe;",
+     "const double fb = (double)s / (double)S, fe = 1.0 - fb;"),
+    ("vjp_interp_second_end_sign", "my_te[j] -= fe * t;", "my_te[j] += fe * t;"),
+    ("vjp_interp_gain_conj", "const double d1r = Ur[ua] * ybr + Ui[ua] * ybi, d1i = Ui[ua] * ybr - Ur[ua] * ybi;",
+     "const double d1r = Ur[ua] * ybr - Ui[ua] * ybi, d1i = Ui[ua] * ybr + Ur[ua] * ybi;"),
     ("beam_phase_sign", "const double wre = a * cos(phi), wim = a * sin(phi);",
      "const double wre = a * cos(phi), wim = -a * sin(phi);"),
     ("beam_weight_dropped", "const double a = weights ? weights[n] : 1.0;", "const double a = 1.0;"),
