@@ -857,12 +857,19 @@ def measure_adjoint(args, dev):
     c.backward(R, g, t, G)
     bwd_ms = _time(lambda: c.backward(R, g, t, G), args.steps, stream)
     app_ms = _time(lambda: c.apply_gains(R, g, t, out=vis), args.steps, stream)
+    # delays moving over the block: backward from the channelised block (recomputes
+    # the corrected block, K and M1 with the X-stage, then the contraction)
+    te = t + torch.as_tensor(rng.uniform(-20e-9, 20e-9, N), device=dev)
+    wv = torch.empty((2,) + c.vis_shape(), dtype=torch.float32, device=dev)
+    interp = lambda: c.backward_interp(chan, g, t, te, G, work_corr=corr, work_vis=wv)
+    interp()
+    interp_ms = _time(interp, args.steps, stream)
     peaks, _ = measured_peaks()
     vb = c.sizes.vis_bytes
     c.close()
     return {"workload": "76 stations x 2 pols, 32 subbands, 64 channels, 768 spectra, FP32",
             "forward_ms": fwd_ms, "raw_vis_recompute_ms": raw_ms, "backward_ms": bwd_ms,
-            "apply_gains_ms": app_ms,
+            "apply_gains_ms": app_ms, "backward_moving_delays_ms": interp_ms,
             "backward_hbm_frac": 2 * vb / (bwd_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
             "train_step_ms_recompute": raw_ms + bwd_ms + fwd_ms}
 

@@ -347,6 +347,32 @@ fx_status fx_correct_correlate_backward(fx_handle *h, const float *d_raw_vis, co
                                         const double *d_delays, const float *d_grad_vis,
                                         float *d_grad_gains, double *d_grad_delays, fx_stream stream);
 
+/* Adjoint of correct + correlate when each station's delay moves linearly
+ * from d_delay_begin to d_delay_end over the block (the forward correction's
+ * interpolation, Sec. "Signal processing with GPU kernels": phases formed at
+ * the block's ends and interpolated in between). V then no longer factors
+ * through R; with unit gains K = sum_s Y_a conj(Y_b) and
+ * M1 = sum_s (s/S) Y_a conj(Y_b) of the delay- and bandpass-corrected block Y,
+ * V_ab = g_a conj(g_b) K_ab, dV_ab/dtau_end = +-i 2 pi f_k g_a conj(g_b) M1_ab
+ * and dV_ab/dtau_begin = +-i 2 pi f_k g_a conj(g_b) (K_ab - M1_ab) (+ for the
+ * first station of the entry, - for the second). The call recomputes Y from
+ * the channelised block (d_chan, chan layout) into d_work_corr (corr layout
+ * of the handle's precision, caller-owned, corr_bytes of fx_query_sizes,
+ * 128-byte aligned), forms K and M1 with the X-stage into d_work_vis
+ * (2 x vis_bytes, caller-owned; K first) and writes d_grad_gains [N][P]
+ * complex float, d_grad_delay_begin [N] and d_grad_delay_end [N] double
+ * (each may be NULL) from d_grad_vis = (dL/dRe V, dL/dIm V). d_bandpass
+ * [N][C] or NULL, d_gains [N][P] complex or NULL (= ones). Needs an FX_F32
+ * or FX_TF32_SPLIT handle with n_stations <= 512; stream-ordered, allocation
+ * free. At equal ends the two delay gradients add up to
+ * fx_correct_correlate_backward's. */
+fx_status fx_correct_correlate_backward_interp(fx_handle *h, const float *d_chan, const double *d_delay_begin,
+                                               const double *d_delay_end, const float *d_bandpass,
+                                               const float *d_gains, const float *d_grad_vis, void *d_work_corr,
+                                               float *d_work_vis, float *d_grad_gains,
+                                               double *d_grad_delay_begin, double *d_grad_delay_end,
+                                               fx_stream stream);
+
 /* ---- batching form ----------------------------------------------------------
  * Many uneven correlation jobs (each its own station count, subbands,
  * channels and spectra) in one persistent tensor-core launch. The paper maps

@@ -72,6 +72,7 @@ SIGNATURES = {
     "fx_batch_poll_status": (I, [P, ctypes.POINTER(ctypes.c_int)]),
     "fx_batch_destroy": (None, [P]),
     "fx_correct_correlate_backward": (I, [P, P, P, P, P, P, P, P]),
+    "fx_correct_correlate_backward_interp": (I, [P, P, P, P, P, P, P, P, P, P, P, P, P]),
     "fx_correct_f32_noalloc": (I, [I, I, I, I, D, P, P, P, P, P, P, P, P]),
 }
 FX_NOALLOC_MAX_PHASES = 1 << 20

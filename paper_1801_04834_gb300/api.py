@@ -347,6 +347,35 @@ class Correlator:
             "fx_correct_correlate_backward")
         return gg, gt
 
+    def backward_interp(self, chan, gains, delay_begin, delay_end, grad_vis, bandpass=None, stream=None,
+                        work_corr=None, work_vis=None):
+        """(dL/d gains [N][2][2] float32, dL/d delay_begin [N], dL/d delay_end [N]
+        float64) for delays moving linearly over the block, from the channelised
+        block and grad_vis = (dL/dRe V, dL/dIm V) (fx_correct_correlate_backward_interp;
+        the work buffers are allocated here when not given)."""
+        gg = torch.empty((self.N, 2, 2), dtype=torch.float32, device=self.device)
+        gb = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        ge = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        if work_corr is None:
+            work_corr = torch.empty(self.corr_shape(), dtype=self.corr_dtype(), device=self.device)
+        if work_vis is None:
+            work_vis = torch.empty((2,) + self.vis_shape(), dtype=torch.float32, device=self.device)
+        vb = self.sizes.vis_bytes
+        check(self.lib.fx_correct_correlate_backward_interp(
+            self.handle, self._dev(chan, "chan", torch.float32, self.sizes.chan_bytes),
+            self._dev(delay_begin, "delay_begin", torch.float64, 8 * self.N),
+            self._dev(delay_end, "delay_end", torch.float64, 8 * self.N),
+            self._opt(bandpass, "bandpass", torch.float32, 4 * self.N * self.C),
+            self._opt(gains, "gains", torch.float32, 16 * self.N),
+            self._dev(grad_vis, "grad_vis", torch.float32, vb),
+            self._dev(work_corr, "work_corr", self.corr_dtype(), self.sizes.corr_bytes),
+            self._dev(work_vis, "work_vis", torch.float32, 2 * vb),
+            self._dev(gg, "grad_gains", torch.float32, 16 * self.N),
+            self._dev(gb, "grad_delay_begin", torch.float64, 8 * self.N),
+            self._dev(ge, "grad_delay_end", torch.float64, 8 * self.N), _stream_ptr(stream)),
+            "fx_correct_correlate_backward_interp")
+        return gg, gb, ge
+
     def close(self):
         if getattr(self, "handle", None):
             self.lib.fx_destroy(self.handle)

@@ -11,6 +11,13 @@ kept), with `recompute=False` they are formed in the forward pass and kept
 (one extra correction + correlation up front, after which `chan` may be
 freed: R is ~1/(S/2N) of its size).
 
+With `delays_end` given, each station's delay moves linearly from `delays`
+(block start) to `delays_end` (block end), as fx_correct interpolates it;
+the visibility no longer factors through R, and the backward pass calls
+fx_correct_correlate_backward_interp, which recomputes the corrected block
+from `chan` and returns gradients for both ends (the channelised block is
+always kept by reference in this mode).
+
 `apply_gains(c, raw_vis, gains, delays)` is the cheap forward from R (for
 calibration loops that re-evaluate V for many gains/delays on fixed data).
 
@@ -65,7 +72,27 @@ class _ApplyGains(torch.autograd.Function):
         return gg, gt, None, None
 
 
-def correct_correlate(c, chan, gains, delays, bandpass=None, recompute=True):
+class _CorrectCorrelateInterp(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, gains, delays, delays_end, c, chan, bandpass):
+        g = gains.detach().contiguous()
+        d0 = delays.detach().contiguous()
+        d1 = delays_end.detach().contiguous()
+        vis = c.correlate(c.correct(chan, d0, d1, bandpass=bandpass, gains=g))
+        ctx.c, ctx.chan, ctx.bandpass = c, chan, bandpass
+        ctx.save_for_backward(g, d0, d1)
+        return vis
+
+    @staticmethod
+    def backward(ctx, grad_vis):
+        g, d0, d1 = ctx.saved_tensors
+        gg, gb, ge = ctx.c.backward_interp(ctx.chan, g, d0, d1, grad_vis.contiguous(), bandpass=ctx.bandpass)
+        return gg, gb, ge, None, None, None
+
+
+def correct_correlate(c, chan, gains, delays, bandpass=None, recompute=True, delays_end=None):
+    if delays_end is not None:
+        return _CorrectCorrelateInterp.apply(gains, delays, delays_end, c, chan, bandpass)
     return _CorrectCorrelate.apply(gains, delays, c, chan, bandpass, recompute)
 
 

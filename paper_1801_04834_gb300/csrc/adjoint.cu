@@ -166,6 +166,121 @@ __global__ void adjoint_reduce_kernel(const double *__restrict__ partial, int nb
     if (grad_tau) grad_tau[n] = t;
 }
 
+// ---- delays moving over the block ------------------------------------------
+// With tau_n(s) = tau_begin + (tau_end - tau_begin) s / S the visibility no
+// longer factors through R. With unit gains, K = sum_s Y_a conj(Y_b) and
+// M1 = sum_s (s/S) Y_a conj(Y_b) of the delay- and bandpass-corrected data Y,
+//   V_ab = g_a conj(g_b) K_ab,
+//   dV_ab/dtau_end[i]   = +i w g_a conj(g_b) M1_ab          (i = station of a)
+//   dV_ab/dtau_begin[i] = +i w g_a conj(g_b) (K_ab - M1_ab)
+// (minus for the station of b, w = 2 pi f_k), and the gain terms are those of
+// the constant-delay adjoint with R replaced by K and e = 1. M1 is the X-stage
+// of the corrected block with spectrum s scaled by sqrt(s/S) on both sides.
+
+// corr *= sqrt(s / S) per spectrum (FP32 spectrum-blocked or FP32 planar layout)
+__global__ void weight_spectra_kernel(float *__restrict__ corr, long long n, int planar, int N, int NB, int S,
+                                      int S_pad)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        int s;
+        if (planar) {
+            s = (int)(e % S_pad);                       // [SB][C][2][I_pad][S_pad] floats
+        } else {
+            const long long f2 = e >> 1;                // [SB][C][NB][N][16][P] float2
+            const int r = (int)((f2 >> 1) & 15);
+            const long long bk = (f2 / (32LL * N)) % NB;
+            s = (int)(bk * 16 + r);
+        }
+        corr[e] = s < S ? corr[e] * sqrtf((float)s / (float)S) : 0.f;
+    }
+}
+
+// Per-CTA partial gradients for moving delays: (dL/dRe g_a, dL/dIm g_a,
+// dL/dtau_begin and dL/dtau_end contributions of input a).
+__global__ void adjoint_interp_partial_kernel(const float2 *__restrict__ K, const float2 *__restrict__ M1,
+                                              const float2 *__restrict__ G, const float2 *__restrict__ gains,
+                                              const double *__restrict__ centres, double *__restrict__ partial,
+                                              int N, int C, long long total_ch, double fs)
+{
+    extern __shared__ float2 gsh[];                 // g[I]
+    const int I = 2 * N;
+    const long long B = (long long)N * (N + 1) / 2;
+    const int a = threadIdx.x;
+    const int ia = a >> 1, pa = a & 1;
+    for (int t = threadIdx.x; t < I; t += blockDim.x) gsh[t] = gains ? gains[t] : make_float2(1.f, 0.f);
+    __syncthreads();
+    double gre = 0.0, gim = 0.0, gtb = 0.0, gte = 0.0;
+    if (a < I) {
+        const float2 ga = gsh[a];
+        for (long long ch = blockIdx.x; ch < total_ch; ch += gridDim.x) {
+            const int k = (int)(ch % C), sb = (int)(ch / C);
+            const float w = (float)(kTwoPi * (centres[sb] + (double)(k - C / 2) * fs / (double)C));
+            const float2 *kv = K + ch * B * 4, *mv = M1 + ch * B * 4, *gv = G + ch * B * 4;
+            float sre = 0.f, sim = 0.f, sb_ = 0.f, se = 0.f;
+            for (int bi = 0; bi < I; ++bi) {
+                const int jb = bi >> 1, pb = bi & 1;
+                const float2 gb = gsh[bi];
+                if (ia <= jb) {                                   // entry (a first, b second)
+                    const long long idx = ((long long)jb * (jb + 1) / 2 + ia) * 4 + 2 * pa + pb;
+                    const float2 Kv = kv[idx], Mv = mv[idx], Gv = gv[idx];
+                    const float2 d1 = cm(cj(gb), Kv);
+                    sre += Gv.x * d1.x + Gv.y * d1.y;
+                    sim += -Gv.x * d1.y + Gv.y * d1.x;
+                    const float2 cab = cm(ga, cj(gb));
+                    const float2 Vm = cm(cab, Mv), Vb = cm(cab, make_float2(Kv.x - Mv.x, Kv.y - Mv.y));
+                    se += w * (-Gv.x * Vm.y + Gv.y * Vm.x);
+                    sb_ += w * (-Gv.x * Vb.y + Gv.y * Vb.x);
+                }
+                if (jb <= ia) {                                   // entry (b first, a second)
+                    const long long idx = ((long long)ia * (ia + 1) / 2 + jb) * 4 + 2 * pb + pa;
+                    const float2 Kv = kv[idx], Mv = mv[idx], Gv = gv[idx];
+                    const float2 d2 = cm(gb, Kv);
+                    sre += Gv.x * d2.x + Gv.y * d2.y;
+                    sim += Gv.x * d2.y - Gv.y * d2.x;
+                    const float2 cba = cm(gb, cj(ga));
+                    const float2 Vm = cm(cba, Mv), Vb = cm(cba, make_float2(Kv.x - Mv.x, Kv.y - Mv.y));
+                    se -= w * (-Gv.x * Vm.y + Gv.y * Vm.x);
+                    sb_ -= w * (-Gv.x * Vb.y + Gv.y * Vb.x);
+                }
+            }
+            gre += sre;
+            gim += sim;
+            gtb += sb_;
+            gte += se;
+        }
+        double *out = partial + ((long long)blockIdx.x * I + a) * 4;
+        out[0] = gre;
+        out[1] = gim;
+        out[2] = gtb;
+        out[3] = gte;
+    }
+}
+
+__global__ void adjoint_interp_reduce_kernel(const double *__restrict__ partial, int nblk, int N,
+                                             float2 *__restrict__ grad_gains, double *__restrict__ grad_tb,
+                                             double *__restrict__ grad_te)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int I = 2 * N;
+    double tb = 0.0, te = 0.0;
+    for (int p = 0; p < 2; ++p) {
+        const int a = 2 * n + p;
+        double re = 0.0, im = 0.0;
+        for (int b = 0; b < nblk; ++b) {
+            const double *q = partial + ((long long)b * I + a) * 4;
+            re += q[0];
+            im += q[1];
+            tb += q[2];
+            te += q[3];
+        }
+        if (grad_gains) grad_gains[a] = make_float2((float)re, (float)im);
+    }
+    if (grad_tb) grad_tb[n] = tb;
+    if (grad_te) grad_te[n] = te;
+}
+
 }  // namespace
 
 int adjoint_blocks(const Handle &h)
@@ -202,6 +317,44 @@ cudaError_t launch_adjoint(const Handle &h, const float2 *R, const float2 *G, co
     if (e != cudaSuccess) return e;
     adjoint_reduce_kernel<<<(h.p.n_stations + 127) / 128, 128, 0, st>>>(h.d_adj_partial, nblk, h.p.n_stations,
                                                                         grad_gains, grad_tau);
+    return cudaGetLastError();
+}
+
+}  // namespace fxi
+
+namespace fxi {
+
+cudaError_t launch_weight_spectra(const Handle &h, void *corr, cudaStream_t st)
+{
+    const int planar = h.p.precision == FX_TF32_SPLIT;
+    if (!planar && h.p.precision != FX_F32) return cudaErrorNotSupported;
+    const int NB = (h.p.n_spectra + 15) / 16;
+    const long long n = planar ? (long long)h.p.n_subbands * h.p.n_channels * 2 * h.I_pad * h.S_pad
+                               : (long long)h.p.n_subbands * h.p.n_channels * NB * h.p.n_stations * 16 * kPols * 2;
+    const long long want = (n + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 8LL * h.num_sms * 8 ? want : 8LL * h.num_sms * 8);
+    if (blocks == 0) return cudaSuccess;
+    weight_spectra_kernel<<<blocks, 256, 0, st>>>(static_cast<float *>(corr), n, planar, h.p.n_stations, NB,
+                                                  h.p.n_spectra, h.S_pad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_interp(const Handle &h, const float2 *K, const float2 *M1, const float2 *G,
+                                  const float2 *gains, float2 *grad_gains, double *grad_tb, double *grad_te,
+                                  cudaStream_t st)
+{
+    const int I = h.I;
+    if (I > 1024) return cudaErrorNotSupported;
+    const long long total = (long long)h.p.n_subbands * h.p.n_channels;
+    const int nblk = adjoint_blocks(h);
+    const int threads = (I + 31) / 32 * 32;
+    adjoint_interp_partial_kernel<<<nblk, threads, sizeof(float2) * I, st>>>(
+        K, M1, G, gains, h.d_centres, h.d_adj_partial, h.p.n_stations, h.p.n_channels, total, h.p.sample_rate_hz);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    adjoint_interp_reduce_kernel<<<(h.p.n_stations + 127) / 128, 128, 0, st>>>(h.d_adj_partial, nblk,
+                                                                               h.p.n_stations, grad_gains,
+                                                                               grad_tb, grad_te);
     return cudaGetLastError();
 }
 

@@ -170,7 +170,7 @@ extern "C" fx_status fx_create(const fx_params *pp, fx_handle **out)
     FX_TRY(cudaMalloc(&h->d_phase, sizeof(float2) * SB * N * C));
     FX_TRY(cudaMalloc(&h->d_status, sizeof(int) * 4));
     FX_TRY(cudaMalloc(&h->d_xf32_tiles, sizeof(int2) * ntiles));
-    FX_TRY(cudaMalloc(&h->d_adj_partial, sizeof(double) * 3 * (size_t)fxi::adjoint_blocks(*h) * h->I));
+    FX_TRY(cudaMalloc(&h->d_adj_partial, sizeof(double) * 4 * (size_t)fxi::adjoint_blocks(*h) * h->I));
     FX_TRY(cudaMemcpy(h->d_taps, p.h_taps, sizeof(float) * T * C, cudaMemcpyHostToDevice));
     FX_TRY(cudaMemcpy(h->d_twiddle, tw.data(), sizeof(float2) * C, cudaMemcpyHostToDevice));
     FX_TRY(cudaMemcpy(h->d_centres, p.h_subband_centre_hz, sizeof(double) * SB,
@@ -525,6 +525,42 @@ extern "C" fx_status fx_correct_correlate_backward(fx_handle *h, const float *d_
                                             reinterpret_cast<float2 *>(d_grad_gains), d_grad_delays,
                                             (cudaStream_t)stream),
                         who);
+}
+
+extern "C" fx_status fx_correct_correlate_backward_interp(
+    fx_handle *h, const float *d_chan, const double *d_delay_begin, const double *d_delay_end,
+    const float *d_bandpass, const float *d_gains, const float *d_grad_vis, void *d_work_corr, float *d_work_vis,
+    float *d_grad_gains, double *d_grad_delay_begin, double *d_grad_delay_end, fx_stream stream)
+{
+    const char *who = "fx_correct_correlate_backward_interp";
+    fx_status st = check_handle(h, who);
+    if (st) return st;
+    if (h->p.precision != FX_F32 && h->p.precision != FX_TF32_SPLIT)
+        return fail(FX_ERR_UNSUPPORTED, "%s: needs an FX_F32 or FX_TF32_SPLIT handle", who);
+    if (!d_chan || !d_delay_begin || !d_delay_end || !d_grad_vis || !d_work_corr || !d_work_vis)
+        return fail(FX_ERR_INVALID, "%s: NULL buffer", who);
+    if (h->I > 1024) return fail(FX_ERR_UNSUPPORTED, "%s: at most 512 stations", who);
+    if (!fxi::xstage_supported(*h)) return fail(FX_ERR_UNSUPPORTED, "%s: X-stage not supported for this shape", who);
+    if (((uintptr_t)d_chan & 15) || ((uintptr_t)d_work_corr & 127) || ((uintptr_t)d_work_vis & 15) ||
+        ((uintptr_t)d_grad_vis & 7) || ((uintptr_t)d_gains & 7) || ((uintptr_t)d_bandpass & 3) ||
+        ((uintptr_t)d_delay_begin & 7) || ((uintptr_t)d_delay_end & 7) || ((uintptr_t)d_grad_gains & 7) ||
+        ((uintptr_t)d_grad_delay_begin & 7) || ((uintptr_t)d_grad_delay_end & 7))
+        return fail(FX_ERR_INVALID, "%s: misaligned buffer", who);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t vis_len = (size_t)h->p.n_subbands * h->p.n_channels * h->B * 4;   // float2 per visibility block
+    float2 *K = reinterpret_cast<float2 *>(d_work_vis), *M1 = K + vis_len;
+    cudaError_t e = fxi::launch_phase_table(*h, d_delay_begin, d_delay_end, s);
+    if (e == cudaSuccess)   // the corrected block with unit gains: Y
+        e = fxi::launch_correct(*h, reinterpret_cast<const float2 *>(d_chan), d_bandpass, nullptr, d_work_corr, s);
+    if (e == cudaSuccess) e = fxi::launch_xstage(*h, d_work_corr, K, s);              // K = sum Y Y^H
+    if (e == cudaSuccess) e = fxi::launch_weight_spectra(*h, d_work_corr, s);         // Y sqrt(s/S)
+    if (e == cudaSuccess) e = fxi::launch_xstage(*h, d_work_corr, M1, s);             // M1 = sum (s/S) Y Y^H
+    if (e == cudaSuccess)
+        e = fxi::launch_adjoint_interp(*h, K, M1, reinterpret_cast<const float2 *>(d_grad_vis),
+                                       reinterpret_cast<const float2 *>(d_gains),
+                                       reinterpret_cast<float2 *>(d_grad_gains), d_grad_delay_begin,
+                                       d_grad_delay_end, s);
+    return after_launch(e, who);
 }
 
 extern "C" fx_status fx_batch_create(const fx_job *jobs, int n_jobs, int precision, float operand_scale,

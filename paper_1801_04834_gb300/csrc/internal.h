@@ -27,7 +27,7 @@ struct Handle {
     int2 *d_xf32_tiles = nullptr;      // tile list of the FP32 correlator
     int xf32_ntiles = 0;
     int xf32_mode = 1;                 // its form: 0 2x4 tiles, 1 4x4 tiles, 2 2x4 tiles with 3 multiplications
-    double *d_adj_partial = nullptr;   // [adjoint CTAs][I][3] per-CTA gradient sums
+    double *d_adj_partial = nullptr;   // [adjoint CTAs][I][4] per-CTA gradient sums
     // streaming (FX_FLAG_STREAMING): FIR history ping-pong + assembled block
     int hist_len = 0;                  // samples of history per (subband, station)
     void *d_hist[2] = {nullptr, nullptr};
@@ -91,6 +91,10 @@ cudaError_t launch_apply_gains(const Handle &h, const float2 *R, const float2 *g
                                float2 *V, cudaStream_t st);
 cudaError_t launch_adjoint(const Handle &h, const float2 *R, const float2 *G, const float2 *gains,
                            const double *tau, float2 *grad_gains, double *grad_tau, cudaStream_t st);
+cudaError_t launch_weight_spectra(const Handle &h, void *corr, cudaStream_t st);
+cudaError_t launch_adjoint_interp(const Handle &h, const float2 *K, const float2 *M1, const float2 *G,
+                                  const float2 *gains, float2 *grad_gains, double *grad_tb, double *grad_te,
+                                  cudaStream_t st);
 
 // beamform.cu
 size_t bf_weight_bytes(const Handle &h, int n_beams);

@@ -169,3 +169,61 @@ def test_adjoint_full_size_sampled():
     gg_ref, gt_ref = oracle.vjp(chan_s, FS, centres[sampled], t, G_s, bandpass=bp, gains=g_full)
     assert relerr(gg.cpu().numpy().astype(np.float64), gg_ref) < 1e-4
     assert relerr(gt.cpu().numpy(), gt_ref) < 1e-4
+
+
+@pytest.mark.parametrize("precision", [0, 4])
+@pytest.mark.parametrize("SB,N,C,S", [(2, 12, 16, 40), (1, 76, 64, 24), (2, 5, 256, 9)])
+def test_adjoint_moving_delays_vs_oracle(SB, N, C, S, precision):
+    """Delays moving linearly over the block (begin != end):
+    fx_correct_correlate_backward_interp against the oracle's sample-by-sample
+    chain rule (fxo_vjp_interp, itself pinned by finite differences in both
+    delay ends), 1e-4 normwise for the gains and each delay end; the FP32
+    (CUDA-core) and TF32-split (tensor-core) X-stages both form K and M1."""
+    chan, centres, g, tb, bp, M, w = problem(31 + N, SB, N, C, S)
+    rng = np.random.default_rng(N)
+    te = tb + rng.uniform(-20e-9, 20e-9, N)
+    V = cplx(oracle.correlate(oracle.correct(chan, FS, centres, tb, te, bandpass=bp, gains=g)))
+    G = 2 * w * (V - M)
+    Gr = np.stack([G.real, G.imag], -1)
+    gg_ref, gb_ref, ge_ref = oracle.vjp_interp(chan, FS, centres, tb, te, Gr, bandpass=bp, gains=g)
+    c = fxg().Correlator(N, SB, C, S, taps=synth.kaiser_sinc_taps(16, C), centres=centres, precision=precision)
+    gg, gb, ge = c.backward_interp(dev(chan), dev(g), dev(tb, torch.float64), dev(te, torch.float64), dev(Gr),
+                                   bandpass=dev(bp))
+    gg, gb, ge = gg.cpu().numpy().astype(np.float64), gb.cpu().numpy(), ge.cpu().numpy()
+    assert relerr(gg, gg_ref) < 1e-4, relerr(gg, gg_ref)
+    assert relerr(gb, gb_ref) < 1e-4, relerr(gb, gb_ref)
+    assert relerr(ge, ge_ref) < 1e-4, relerr(ge, ge_ref)
+    c.close()
+
+
+def test_adjoint_moving_delays_autograd_and_constant_limit():
+    """torch.autograd through correct_correlate(..., delays_end=...): the
+    gradients reach gains and both delay ends and equal the oracle's; at equal
+    ends the two delay gradients add up to the constant-delay adjoint's."""
+    SB, N, C, S = 1, 8, 16, 48
+    chan, centres, g, tb, bp, M, w = problem(41, SB, N, C, S)
+    rng = np.random.default_rng(3)
+    te = tb + rng.uniform(-20e-9, 20e-9, N)
+    c = make(SB, N, C, S, centres)
+    from paper_1801_04834_gb300 import autograd as ag
+    gt_ = dev(g).requires_grad_(True)
+    tb_ = dev(tb, torch.float64).requires_grad_(True)
+    te_ = dev(te, torch.float64).requires_grad_(True)
+    Mt, wt = dev(np.stack([M.real, M.imag], -1)), dev(w)
+    vis = ag.correct_correlate(c, dev(chan), gt_, tb_, bandpass=dev(bp), delays_end=te_)
+    loss = (wt * ((vis - Mt) ** 2).sum(-1)).sum()
+    loss.backward()
+    V = cplx(oracle.correlate(oracle.correct(chan, FS, centres, tb, te, bandpass=bp, gains=g)))
+    G = 2 * w * (V - M)
+    gg_ref, gb_ref, ge_ref = oracle.vjp_interp(chan, FS, centres, tb, te, np.stack([G.real, G.imag], -1),
+                                                bandpass=bp, gains=g)
+    assert relerr(gt_.grad.cpu().numpy().astype(np.float64), gg_ref) < 1e-4
+    assert relerr(tb_.grad.cpu().numpy(), gb_ref) < 1e-4
+    assert relerr(te_.grad.cpu().numpy(), ge_ref) < 1e-4
+    # equal ends: begin + end gradients = the constant-delay adjoint's delay gradient
+    V1, Gr1, gg0, gt0 = oracle_grad(chan, centres, g, tb, bp, M, w)
+    gg1, gb1, ge1 = c.backward_interp(dev(chan), dev(g), dev(tb, torch.float64), dev(tb, torch.float64), dev(Gr1),
+                                      bandpass=dev(bp))
+    assert relerr(gg1.cpu().numpy().astype(np.float64), gg0) < 1e-4
+    assert relerr((gb1 + ge1).cpu().numpy(), gt0) < 1e-4
+    c.close()
