@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 FS = synth.SAMPLE_RATE_HZ
 
 
-@pytest.mark.parametrize("precision,bound", [(0, 1e-5), (1, 5e-3)])
+@pytest.mark.parametrize("precision,bound", [(0, 1e-5), (1, 5e-3), (4, 1e-5)])
 @pytest.mark.parametrize("chunk", [2, 5, 7])
 def test_process_host_matches_device_path(precision, bound, chunk):
     import paper_1801_04834_gb300 as fxg
