@@ -488,15 +488,20 @@ def run_fx(args, w):
     if prec == 4:
         ex = executed_xflops(c, w, prec)
         tpk = peaks_run["tf32_tflops"]
-        roof = {"kernel": "xcorr_tf32_kernel", "bound": "tensor", "achieved": x_ach, "peak": tpk,
-                "unit": "TFLOP/s", "frac": x_ach / tpk,
+        split = 3.0 * xflops            # the method's TF32 work: hi hi' + hi lo' + lo hi' per complex MAC
+        s_ach = split / (ms_x * 1e-3) / 1e12
+        roof = {"kernel": "xcorr_tf32_kernel", "bound": "tensor", "achieved": s_ach, "peak": tpk,
+                "unit": "TFLOP/s", "frac": s_ach / tpk,
                 "traffic": recorded_traffic("xcorr_tf32_kernel", args.workload),
                 "peak_source": "dense TF32 tensor throughput measured in this run (torch TF32 matmul 8192^3, "
                                "burst); MEASURED_PEAKS.json holds no TF32 figure",
-                "algorithmic": f"{xflops:.4e} useful flop per launch (8 per complex MAC, upper triangle)",
+                "algorithmic": f"{split:.4e} TF32 flop per launch: 3 TF32 products (hi hi', hi lo', lo hi') "
+                               f"per complex MAC, 8 flop each, upper triangle incl. autos "
+                               f"(the split form's count, as for split FP16: 3 x {xflops:.4e} useful)",
+                "useful_fp32_equiv_TFLOPs": x_ach, "useful_frac": x_ach / tpk,
                 "executed_TFLOPs": ex / (ms_x * 1e-3) / 1e12, "executed_frac": ex / (ms_x * 1e-3) / 1e12 / tpk,
-                "executed_note": "the split form issues 3 TF32 products (hi hi', hi lo', lo hi') of whole "
-                                 "128-input tiles: %.2fx the useful flops" % (ex / xflops)}
+                "executed_note": "whole 128-input tiles (both triangles) are issued: %.2fx the split form's "
+                                 "algorithmic flops" % (ex / split)}
     elif prec == 0:
         fpk = fp32_alu_peak_tflops(sm_count)
         roof = {"kernel": "xcorr_f32_kernel", "bound": "alu", "achieved": x_ach, "peak": fpk,
