@@ -40,8 +40,13 @@
  *                            plane 0 real parts, plane 1 imaginary parts
  *         FX_F16_SPLIT:      [SB][C][4][I_pad][S_pad] half, planes hi.re,
  *                            hi.im, lo.re, lo.im (value = hi + lo)
+ *         FX_TF32_SPLIT:     [SB][C][2][I_pad][S_pad] float (FP32 planes,
+ *                            split into TF32 parts by the X-stage)
  *         I_pad = I rounded up to 16, S_pad = S rounded up to 64; the padding
- *         is written as zeros by fx_correct.
+ *         is written as zeros by fx_correct and fx_channelize_correct. A caller
+ *         that fills corr itself must zero spectra S .. S_pad-1 (the X-stage
+ *         sums them); padded inputs only reach visibilities that are not
+ *         written.
  *   vis   [SB][C][B][4]      complex float, B = N(N+1)/2 baselines,
  *                            b = j(j+1)/2 + i for stations i <= j, products
  *                            (p,q) in the order XX, XY, YX, YY (index 2p+q):
