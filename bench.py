@@ -951,7 +951,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--host-chunk", type=int, default=16,
+    ap.add_argument("--host-chunk", type=int, default=4,
                     help="subbands per chunk of the host pipeline (e2e)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batching, differentiation and beamformer measurements")
