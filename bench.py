@@ -52,7 +52,8 @@ FS = 195312.5
 WORKLOADS = {
     "lofar16_fp32": dict(N=64, SB=244, C=64, S=3072, T=16, fmt=0, precision=4, sigma=100.0,
                          ntones=3, ripple=True, seed_index=1,
-                         desc="LOFAR 16-bit, FP32-accurate path (hi/lo TF32 split X-stage on tensor cores): "
+                         desc="LOFAR 16-bit, FP32-accurate path (hi/lo split X-stage on tensor cores: hi hi' in TF32, "
+                              "hi lo' + lo hi' in BF16): "
                               "64 stations x 2 pols, 244 subbands, 16-tap PPF to 64 channels, "
                               "3072 spectra (1.00663 s) per block"),
     "lofar16_ffma": dict(N=64, SB=244, C=64, S=3072, T=16, fmt=0, precision=0, sigma=100.0,
@@ -78,7 +79,7 @@ WORKLOADS = {
 }
 
 PRECISION_NAMES = {0: "fp32_ffma", 1: "fp16", 2: "bf16", 3: "split_fp16", 4: "tf32_split"}
-DTYPE_NAMES = {0: "f32", 1: "f16", 2: "bf16", 3: "f16 hi+lo", 4: "f32 as tf32 hi+lo"}
+DTYPE_NAMES = {0: "f32", 1: "f16", 2: "bf16", 3: "f16 hi+lo", 4: "f32 as hi+lo: tf32 hi hi', bf16 cross terms"}
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 
@@ -94,22 +95,52 @@ def useful_xflops(w, n_subbands=None):
     return 8.0 * B * 4 * w["C"] * w["S"] * (n_subbands or w["SB"])
 
 
+def tf32_split_tiles(c):
+    """Sum of 128 x 2n over the TF32-split X-stage's items of one channel
+    (128-row blocks, diagonal and 64-input off-diagonal column tiles)."""
+    ip = c.I_pad
+    tiles = 0
+    for row0 in range(0, ip, 128):
+        tiles += 128 * 2 * min(128, ip - row0)
+        for c0 in range(row0 + 128, ip, 64):
+            tiles += 128 * 2 * min(64, ip - c0)
+    return tiles
+
+
+def executed_xflops_split(c, w):
+    """(TF32, BF16) tensor-core flops the TF32-split X-stage issues: per 16
+    spectra and item, 4 TF32 MMAs of 128 x 2n x 8 (hi hi') and 4 BF16 MMAs of
+    128 x 2n x 16 (hi lo' + lo hi'), 2 flop per multiply-add."""
+    per_sp = tf32_split_tiles(c) * c.S_pad * w["C"] * w["SB"]
+    return 4.0 * per_sp, 8.0 * per_sp
+
+
 def executed_xflops(c, w, precision):
-    """Tensor-core flops the X-stage issues: 2 x 128 x N x 8 per MMA. FP16/BF16:
+    """Tensor-core flops the X-stage issues: 2 x 128 x N x K per MMA. FP16/BF16:
     4 real products of the I_pad x I_pad tile per spectrum (both triangles);
-    split FP16: 12; TF32 split: 6 MMAs of 128 x 2n x 8 per 8 spectra per
-    128-row block x n-column tile of the upper block triangle."""
+    split FP16: 12; TF32 split: the TF32 and BF16 flops together."""
+    if precision == 4:
+        return sum(executed_xflops_split(c, w))
     ip, sp = c.I_pad, c.S_pad
     nch = w["C"] * w["SB"]
-    if precision == 4:
-        tiles = 0
-        for row0 in range(0, ip, 128):
-            tiles += 128 * 2 * min(128, ip - row0)
-            for c0 in range(row0 + 128, ip, 64):
-                tiles += 128 * 2 * min(64, ip - c0)
-        return 12.0 * tiles * sp * nch          # 6 MMAs x 2 x (128 x 2n) x 8 flop per 8 spectra
     mult = {1: 4, 2: 4, 3: 12}[precision]
     return 2.0 * mult * ip * ip * sp * nch
+
+
+def split_roofline(xflops, ex, ms, tpk, bpk):
+    """Tensor roofline of the TF32-split X-stage, whose work is in two dtypes.
+    Algorithmic work per complex MAC of the upper triangle: hi hi' in TF32
+    (8 flop) and hi lo' + lo hi' in BF16 (16 flop). The time floor is
+    F_tf32 / P_tf32 + F_bf16 / P_bf16; `achieved` is that work in TF32-
+    equivalent flops (BF16 flops x P_tf32 / P_bf16) per second, so
+    frac = floor / time against the TF32 peak."""
+    f_t, f_b = xflops, 2.0 * xflops
+    t = ms * 1e-3
+    ach = (f_t + f_b * tpk / bpk) / t / 1e12
+    ex_t, ex_b = ex
+    ex_ach = (ex_t + ex_b * tpk / bpk) / t / 1e12
+    return {"achieved": ach, "frac": ach / tpk, "executed_TFLOPs": ex_ach, "executed_frac": ex_ach / tpk,
+            "floor_ms": (f_t / tpk + f_b / bpk) / 1e9, "executed_floor_ms": (ex_t / tpk + ex_b / bpk) / 1e9}
 
 
 def samples(w):
@@ -486,22 +517,23 @@ def run_fx(args, w):
     sz = c.sizes
     x_ach = xflops / (ms_x * 1e-3) / 1e12
     if prec == 4:
-        ex = executed_xflops(c, w, prec)
-        tpk = peaks_run["tf32_tflops"]
-        split = 3.0 * xflops            # the method's TF32 work: hi hi' + hi lo' + lo hi' per complex MAC
-        s_ach = split / (ms_x * 1e-3) / 1e12
-        roof = {"kernel": "xcorr_tf32_kernel", "bound": "tensor", "achieved": s_ach, "peak": tpk,
-                "unit": "TFLOP/s", "frac": s_ach / tpk,
+        ex = executed_xflops_split(c, w)
+        tpk, bpk = peaks_run["tf32_tflops"], peaks_run["bf16_tflops"]
+        sr = split_roofline(xflops, ex, ms_x, tpk, bpk)
+        roof = {"kernel": "xcorr_tf32_kernel", "bound": "tensor", "achieved": sr["achieved"], "peak": tpk,
+                "unit": "TFLOP/s", "frac": sr["frac"],
                 "traffic": recorded_traffic("xcorr_tf32_kernel", args.workload),
                 "peak_source": "dense TF32 tensor throughput measured in this run (torch TF32 matmul 8192^3, "
-                               "burst); MEASURED_PEAKS.json holds no TF32 figure",
-                "algorithmic": f"{split:.4e} TF32 flop per launch: 3 TF32 products (hi hi', hi lo', lo hi') "
-                               f"per complex MAC, 8 flop each, upper triangle incl. autos "
-                               f"(the split form's count, as for split FP16: 3 x {xflops:.4e} useful)",
+                               "burst); MEASURED_PEAKS.json holds no TF32 figure; BF16 peak of the same run "
+                               f"({bpk:.0f} TFLOP/s) for the BF16 part",
+                "algorithmic": f"{xflops:.4e} TF32 flop (hi hi') + {2 * xflops:.4e} BF16 flop (hi lo' + lo hi') "
+                               f"per launch, 8 flop per complex MAC and product, upper triangle incl. autos; "
+                               f"achieved in TF32-equivalent flops (BF16 x P_tf32/P_bf16), frac = "
+                               f"floor {sr['floor_ms']:.2f} ms / measured {ms_x:.2f} ms",
                 "useful_fp32_equiv_TFLOPs": x_ach, "useful_frac": x_ach / tpk,
-                "executed_TFLOPs": ex / (ms_x * 1e-3) / 1e12, "executed_frac": ex / (ms_x * 1e-3) / 1e12 / tpk,
-                "executed_note": "whole 128-input tiles (both triangles) are issued: %.2fx the split form's "
-                                 "algorithmic flops" % (ex / split)}
+                "executed_TFLOPs": sr["executed_TFLOPs"], "executed_frac": sr["executed_frac"],
+                "executed_note": "whole 128-input tiles (both triangles) are issued: %.2fx the algorithmic work"
+                                 % (sr["executed_floor_ms"] / sr["floor_ms"])}
     elif prec == 0:
         fpk = fp32_alu_peak_tflops(sm_count)
         roof = {"kernel": "xcorr_f32_kernel", "bound": "alu", "achieved": x_ach, "peak": fpk,

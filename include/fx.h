@@ -82,8 +82,9 @@ typedef enum { FX_CI16 = 0, FX_CI8 = 1, FX_CI4 = 2 } fx_format;
 /* Arithmetic type of the corrected samples and of the X-stage operands. The
  * FIR and FFT always run in FP32; the X-stage always accumulates in FP32.
  * FX_TF32_SPLIT: FP32 corrected samples in the planar layout; the X-stage
- * splits each into hi + lo TF32 parts on the tensor cores (hi hi' + hi lo' +
- * lo hi', FP32 accumulation), which holds FP32's error bound; at most 512
+ * splits each into hi (the TF32 part) + lo on the tensor cores and forms
+ * hi hi' as TF32 MMAs and the cross terms hi lo' + lo hi' as BF16 MMAs, all
+ * with FP32 accumulation, which holds FP32's error bound; at most 512
  * stations, operand_scale must be 1. */
 typedef enum { FX_F32 = 0, FX_F16 = 1, FX_BF16 = 2, FX_F16_SPLIT = 3, FX_TF32_SPLIT = 4 } fx_precision;
 

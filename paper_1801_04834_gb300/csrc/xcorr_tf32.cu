@@ -1,15 +1,22 @@
 // xcorr_tf32.cu -- FP32-accurate X-stage on the tcgen05 tensor cores, any
-// station count: FP32 corrected samples split in the kernel into hi + lo TF32
-// parts, V ~ hi hi' + hi lo' + lo hi' (lo lo' dropped), FP32 accumulation in
-// TMEM, chunk sums added in IEEE FP32.
+// station count: FP32 corrected samples split in the kernel into hi + lo,
+// V ~ hi hi' + hi lo' + lo hi' (lo lo' dropped), the main term hi hi' as TF32
+// MMAs and the two cross terms as BF16 MMAs, FP32 accumulation in TMEM, chunk
+// sums added in IEEE FP32.
 //
 // Paper, Sec. "Signal processing with GPU kernels": the correlator forms
 // V[a][b] = sum_s Y[s][a] conj(Y[s][b]) for all input pairs and integrates over
 // the block, in single precision. TF32 keeps FP32's exponent range with an
 // 11-bit significand; hi = x with its 13 low mantissa bits cleared is exactly
-// a TF32 value and lo = x - hi is exact in FP32, so x = hi + lo and the
-// dropped lo lo' term is below 2^-20 of each product, which keeps the FP32
-// path's error bound while running on the tensor cores.
+// a TF32 value and lo = x - hi is exact in FP32 with |lo| < 2^-10 |x|. The
+// cross terms hi lo' and lo hi' are each below 2^-10 of the product, so they
+// tolerate BF16 operands: rounding hi and lo to BF16 (8-bit significand, FP32
+// exponent range, round to nearest) changes a cross term by at most 2^-8 of
+// itself, i.e. 2^-18 of the product in the worst case and about 2^-21 RMS,
+// with zero mean; the dropped lo lo' term is below 2^-20 of the product. BF16
+// MMAs run at twice the TF32 rate, so one K-step of 16 spectra costs the time
+// of 8 TF32 MMAs (4 TF32 + 4 BF16 of twice the depth) instead of 12 with all
+// three products in TF32, and reads two thirds of the shared-memory bytes.
 //
 // Complex product as one real MMA of twice the width. With planar operands
 // (re plane R, im plane J) and, for the column inputs, three consecutive
@@ -17,11 +24,11 @@
 //   D[a][0:n)  += R_a . R_b + J_a . J_b   = Re V[a][b]
 //   D[a][n:2n) += R_a . J_b - J_a . R_b   = -Im V[a][b]
 // come from two MMAs of N = 2n: A = R rows against B = [R; J] (planes 0-1),
-// and A = J rows against B = [J; -R] (planes 1-2). Each side is split into
-// hi and lo, so one K-step (8 spectra) is six MMAs of M = 128, N = 2n, K = 8:
-// hi.[hi], hi.[lo], lo.[hi] for the R rows and the J rows. At n = 128 each MMA
-// reads 4 KB of A and 8 KB of B from shared memory per 128 x 256 x 8 product,
-// three quarters of the shared-memory bytes per flop of two N = 128 MMAs.
+// and A = J rows against B = [J; -R] (planes 1-2). Per stage of 16 spectra:
+//   TF32 (K = 8, two K-steps):  hiR.[hiR; hiJ], hiJ.[hiJ; -hiR]
+//   BF16 (K = 16, one K-step):  hiR.[loR; loJ], hiJ.[loJ; -loR],
+//                               loR.[hiR; hiJ], loJ.[hiJ; -hiR]
+// At n = 128 each MMA reads 4 KB of A and 8 KB of B from shared memory.
 //
 // Work items. Rows come in blocks of 128 inputs (M = 128); an item is
 // (subband x channel, row block, column block) over the upper block
@@ -32,18 +39,24 @@
 // 128-column diagonal item, a 32-column off-diagonal item and a 32-row
 // diagonal item.
 //
-// Shared memory, one stage = 16 spectra (64-byte rows, 64-byte swizzle):
-//   B region: planes hi R, hi J, -hi R, lo R, lo J, -lo R of n rows each
-//             (plane pitch n x 64 bytes). On a diagonal item the A operands
-//             are planes 0, 1, 3, 4 of the same region read as 128-row tiles
-//             (rows past n are other planes' data and only reach
-//             accumulator rows the epilogue ignores; the region is sized so
-//             these reads stay inside the stage).
-//   A region (off-diagonal items): hi R, hi J, lo R, lo J of the 128 row
-//             inputs, 8 KB each, before the B region.
-// TMA writes the raw FP32 R and J rows into the hi planes; converter warps
-// split them in place (hi), write lo and the negated planes, fence the async
-// proxy and release the stage to the MMA thread.
+// Shared memory, one stage = 16 spectra:
+//   B region: TF32 planes hi R, hi J, -hi R of n rows each (64-byte rows,
+//             64-byte swizzle, plane pitch n x 64 bytes), then BF16 planes
+//             hi R, hi J, -hi R, lo R, lo J, -lo R (32-byte rows, 32-byte
+//             swizzle, pitch n x 32 bytes) from byte 3 n x 64. On a diagonal
+//             item the A operands are TF32 planes 0, 1 and BF16 planes 0, 1,
+//             3, 4 of the same region read as 128-row tiles (rows past n are
+//             other planes' data and only reach accumulator rows the
+//             epilogue ignores; the region is at least 48 KB, so these reads
+//             stay inside the stage).
+//   A region (off-diagonal items): TF32 hi R, hi J (8 KB each), then BF16
+//             hi R, hi J, lo R, lo J (4 KB each), before the B region.
+// TMA writes the raw FP32 R and J rows into the TF32 hi planes, where they
+// stay as they are: a kind::tf32 MMA reads the upper 19 bits of each 32-bit
+// operand and ignores the 13 low mantissa bits, so the raw value acts as hi
+// (the kernel tests on operands with non-zero low bits check this against an
+// FP64 reference). Converter warps write -hi R and the BF16 planes, fence the
+// async proxy and release the stage to the MMA thread.
 //
 // Accumulation. The tensor core's FP32 accumulator does not round each
 // addition to nearest, so a long chain of MMAs into one accumulator drifts
@@ -57,7 +70,8 @@
 //
 // Warp roles (persistent, one CTA per SM, 448 threads):
 //   warp 0      TMA producer
-//   warp 1      TMEM allocator + MMA issuer (tcgen05.mma kind::tf32)
+//   warp 1      TMEM allocator + MMA issuer (tcgen05.mma kind::tf32 and
+//               kind::f16 with BF16 operands, into the same accumulator)
 //   warps 2-9   epilogue: two warps per TMEM lane quadrant (warp % 4), each
 //               taking every other 32-column group of the upper triangle
 //   warps 10-13 converter
@@ -66,6 +80,7 @@
 // word, all roles leave, in-flight copies and MMAs are drained (bounded) and
 // TMEM is freed.
 #include <cuda.h>
+#include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cstring>
@@ -84,7 +99,10 @@ constexpr int kT3EpiWarps = 8;
 constexpr int kT3ConvWarp0 = 2 + kT3EpiWarps;
 constexpr int kT3K = 16;                              // spectra per stage (64-byte FP32 rows)
 constexpr unsigned kT3RowBytes = 64;
-constexpr unsigned kT3APlane = 128u * kT3RowBytes;    // one 128-row plane: 8 KB
+constexpr unsigned kT3APlane = 128u * kT3RowBytes;    // one 128-row TF32 plane: 8 KB
+constexpr unsigned kT3BfRowBytes = 32;                // one BF16 row: 16 spectra
+constexpr unsigned kT3ABfPlane = 128u * kT3BfRowBytes; // one 128-row BF16 plane: 4 KB
+constexpr unsigned kT3ABf = 2u * kT3APlane;           // BF16 planes of the A region
 constexpr unsigned kT3BRegionMin = 6u * kT3APlane;    // diagonal item at n = 128: 48 KB
 constexpr int kT3MaxStages = 6;
 constexpr int kT3MaxItems = 64;                       // items per channel
@@ -135,6 +153,14 @@ __device__ __forceinline__ unsigned long long sdesc64(unsigned addr)
            (1ull << 46) | (4ull << 61);
 }
 
+// The same for the BF16 planes: K-major, 32-byte swizzle (8-row atoms of 256
+// bytes, SBO = 256); one 32-byte row is the whole K = 16 of a stage.
+__device__ __forceinline__ unsigned long long sdesc32(unsigned addr)
+{
+    return (unsigned long long)((addr & 0x3FFFF) >> 4) | (1ull << 16) | ((unsigned long long)(256 >> 4) << 32) |
+           (1ull << 46) | (6ull << 61);
+}
+
 // Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, M = 128.
 __device__ __forceinline__ unsigned idesc_tf32(int n, bool neg_a)
 {
@@ -165,31 +191,62 @@ __device__ __forceinline__ unsigned lo_bits(unsigned x, unsigned h)
     return __float_as_uint(__uint_as_float(x) - __uint_as_float(h));
 }
 
-// Split one R plane and one J plane of `rows` rows in place into hi, writing
-// lo (and for the column operand the negated planes) at the given offsets.
-// All planes share the 64-byte swizzle phase, so equal byte offsets hold the
-// same logical element.
-__device__ __forceinline__ void convert_pair(unsigned char *r_plane, unsigned char *j_plane, unsigned char *r_lo,
-                                             unsigned char *j_lo, unsigned char *r_neg_hi, unsigned char *r_neg_lo,
-                                             int rows, int t)
+// Byte offset, in a 32-byte-swizzled BF16 plane, of the 4 elements that the
+// 16-byte chunk q of a 64-byte-swizzled FP32 plane holds. Both swizzles XOR
+// the 16-byte chunk index with address bits 7 and up (64-byte rows: chunk ^=
+// (row / 2) mod 4; 32-byte rows: chunk ^= (row / 4) mod 2) and both plane
+// bases are aligned to their atoms, so the logical position follows from q.
+__device__ __forceinline__ unsigned bf_chunk_off(int q)
+{
+    const int r = q >> 2;
+    const int lc = (q & 3) ^ ((r >> 1) & 3);          // logical chunk: spectra 4 lc .. 4 lc + 3
+    return (unsigned)(r * 32 + 16 * ((lc >> 1) ^ ((r >> 2) & 1)) + 8 * (lc & 1));
+}
+
+// 4 FP32 -> 4 BF16 (round to nearest even) in element order
+__device__ __forceinline__ uint2 bf16x4(uint4 v)
+{
+    const __nv_bfloat162 a = __floats2bfloat162_rn(__uint_as_float(v.x), __uint_as_float(v.y));
+    const __nv_bfloat162 b = __floats2bfloat162_rn(__uint_as_float(v.z), __uint_as_float(v.w));
+    return make_uint2(*reinterpret_cast<const unsigned *>(&a), *reinterpret_cast<const unsigned *>(&b));
+}
+
+__device__ __forceinline__ uint2 neg_bf16x4(uint2 v) { return make_uint2(v.x ^ 0x80008000u, v.y ^ 0x80008000u); }
+
+// Split one R plane and one J plane of `rows` rows (raw FP32 in the TF32
+// planes at tf, pitch tf_pitch, left unchanged: the TF32 MMA reads them as
+// hi) into hi and lo and write the BF16 planes at bf (pitch bf_pitch): for
+// the column operand (col) -hi R after the two TF32 planes and BF16 hi R,
+// hi J, -hi R, lo R, lo J, -lo R; for the row operand of an off-diagonal item
+// BF16 hi R, hi J, lo R, lo J.
+__device__ __forceinline__ void convert_split(unsigned char *tf, unsigned tf_pitch, unsigned char *bf,
+                                              unsigned bf_pitch, int rows, bool col, int t)
 {
     const int nq = rows * (int)(kT3RowBytes / 16);
     for (int q = t; q < nq; q += 128) {
-        const uint4 x = reinterpret_cast<const uint4 *>(r_plane)[q];
-        const uint4 y = reinterpret_cast<const uint4 *>(j_plane)[q];
+        const uint4 x = reinterpret_cast<const uint4 *>(tf)[q];
+        const uint4 y = reinterpret_cast<const uint4 *>(tf + tf_pitch)[q];
         uint4 xh, xl, yh, yl;
         xh.x = hi_bits(x.x); xh.y = hi_bits(x.y); xh.z = hi_bits(x.z); xh.w = hi_bits(x.w);
         yh.x = hi_bits(y.x); yh.y = hi_bits(y.y); yh.z = hi_bits(y.z); yh.w = hi_bits(y.w);
         xl.x = lo_bits(x.x, xh.x); xl.y = lo_bits(x.y, xh.y); xl.z = lo_bits(x.z, xh.z); xl.w = lo_bits(x.w, xh.w);
         yl.x = lo_bits(y.x, yh.x); yl.y = lo_bits(y.y, yh.y); yl.z = lo_bits(y.z, yh.z); yl.w = lo_bits(y.w, yh.w);
-        reinterpret_cast<uint4 *>(r_plane)[q] = xh;
-        reinterpret_cast<uint4 *>(j_plane)[q] = yh;
-        reinterpret_cast<uint4 *>(r_lo)[q] = xl;
-        reinterpret_cast<uint4 *>(j_lo)[q] = yl;
-        if (r_neg_hi) {
-            const unsigned s = 0x80000000u;
-            reinterpret_cast<uint4 *>(r_neg_hi)[q] = make_uint4(xh.x ^ s, xh.y ^ s, xh.z ^ s, xh.w ^ s);
-            reinterpret_cast<uint4 *>(r_neg_lo)[q] = make_uint4(xl.x ^ s, xl.y ^ s, xl.z ^ s, xl.w ^ s);
+        const uint2 xhb = bf16x4(xh), yhb = bf16x4(yh), xlb = bf16x4(xl), ylb = bf16x4(yl);
+        unsigned char *o = bf + bf_chunk_off(q);
+        if (col) {
+            const unsigned sg = 0x80000000u;
+            reinterpret_cast<uint4 *>(tf + 2 * tf_pitch)[q] = make_uint4(xh.x ^ sg, xh.y ^ sg, xh.z ^ sg, xh.w ^ sg);
+            *reinterpret_cast<uint2 *>(o) = xhb;
+            *reinterpret_cast<uint2 *>(o + bf_pitch) = yhb;
+            *reinterpret_cast<uint2 *>(o + 2 * bf_pitch) = neg_bf16x4(xhb);
+            *reinterpret_cast<uint2 *>(o + 3 * bf_pitch) = xlb;
+            *reinterpret_cast<uint2 *>(o + 4 * bf_pitch) = ylb;
+            *reinterpret_cast<uint2 *>(o + 5 * bf_pitch) = neg_bf16x4(xlb);
+        } else {
+            *reinterpret_cast<uint2 *>(o) = xhb;
+            *reinterpret_cast<uint2 *>(o + bf_pitch) = yhb;
+            *reinterpret_cast<uint2 *>(o + 2 * bf_pitch) = xlb;
+            *reinterpret_cast<uint2 *>(o + 3 * bf_pitch) = ylb;
         }
     }
 }
@@ -293,7 +350,9 @@ __global__ void __launch_bounds__(kT3Threads, 1) xcorr_tf32_kernel(const __grid_
                 const int n = itm.z;
                 const bool diag = itm.w != 0;
                 const unsigned pitch = (unsigned)n * kT3RowBytes;
+                const unsigned bpitch = (unsigned)n * kT3BfRowBytes;
                 const unsigned idesc = idesc_tf32(2 * n, false);
+                const unsigned idesc_bf = make_idesc(1u, 2 * n, false);
                 for (int ch = 0; ch < n_chunks && ok; ++ch, ++acc_it) {
                     const int ab = (int)(acc_it & 1);
                     if (!t3wait(acce_bar(ab), (unsigned)((acc_it >> 1) & 1) ^ 1u, abort_flag, P, 2)) {
@@ -310,27 +369,27 @@ __global__ void __launch_bounds__(kT3Threads, 1) xcorr_tf32_kernel(const __grid_
                         }
                         tc_fence_after();
                         const unsigned st = tiles_u32 + (unsigned)s * P.stage_bytes;
-                        const unsigned bb = diag ? st : st + P.a_off;
-                        // A planes: hi R, hi J, lo R, lo J
+                        const unsigned bb = diag ? st : st + P.a_off;      // TF32 hi R, hi J, -hi R
+                        const unsigned bf = bb + 3 * pitch;                 // BF16 hi R, hi J, -hi R, lo R, lo J, -lo R
+                        // A planes: TF32 hi R, hi J; BF16 hi R, hi J, lo R, lo J
                         const unsigned a_hr = diag ? bb : st;
                         const unsigned a_hj = diag ? bb + pitch : st + kT3APlane;
-                        const unsigned a_lr = diag ? bb + 3 * pitch : st + 2 * kT3APlane;
-                        const unsigned a_lj = diag ? bb + 4 * pitch : st + 3 * kT3APlane;
+                        const unsigned a_bhr = diag ? bf : st + kT3ABf;
+                        const unsigned a_bhj = diag ? bf + bpitch : st + kT3ABf + kT3ABfPlane;
+                        const unsigned a_blr = diag ? bf + 3 * bpitch : st + kT3ABf + 2 * kT3ABfPlane;
+                        const unsigned a_blj = diag ? bf + 4 * bpitch : st + kT3ABf + 3 * kT3ABfPlane;
 #pragma unroll
-                        for (int kk = 0; kk < kT3K / 8; ++kk) {    // 8 FP32 = 32 bytes per K-step
+                        for (int kk = 0; kk < kT3K / 8; ++kk) {    // 8 FP32 = 32 bytes per TF32 K-step
                             const unsigned acc = (kc | kk) ? 1u : 0u;
                             const unsigned o = (unsigned)kk * 32u;
-                            const unsigned long long b_h0 = sdesc64(bb + o);               // [hi R; hi J]
-                            const unsigned long long b_h1 = sdesc64(bb + pitch + o);       // [hi J; -hi R]
-                            const unsigned long long b_l0 = sdesc64(bb + 3 * pitch + o);   // [lo R; lo J]
-                            const unsigned long long b_l1 = sdesc64(bb + 4 * pitch + o);   // [lo J; -lo R]
-                            mma_tf32(d, sdesc64(a_hr + o), b_h0, idesc, acc);
-                            mma_tf32(d, sdesc64(a_hj + o), b_h1, idesc, 1u);
-                            mma_tf32(d, sdesc64(a_hr + o), b_l0, idesc, 1u);
-                            mma_tf32(d, sdesc64(a_hj + o), b_l1, idesc, 1u);
-                            mma_tf32(d, sdesc64(a_lr + o), b_h0, idesc, 1u);
-                            mma_tf32(d, sdesc64(a_lj + o), b_h1, idesc, 1u);
+                            mma_tf32(d, sdesc64(a_hr + o), sdesc64(bb + o), idesc, acc);           // [hi R; hi J]
+                            mma_tf32(d, sdesc64(a_hj + o), sdesc64(bb + pitch + o), idesc, 1u);    // [hi J; -hi R]
                         }
+                        // cross terms, K = 16 spectra in one BF16 MMA each
+                        mma_f16(d, sdesc32(a_bhr), sdesc32(bf + 3 * bpitch), idesc_bf, 1u);    // [lo R; lo J]
+                        mma_f16(d, sdesc32(a_bhj), sdesc32(bf + 4 * bpitch), idesc_bf, 1u);    // [lo J; -lo R]
+                        mma_f16(d, sdesc32(a_blr), sdesc32(bf), idesc_bf, 1u);                 // [hi R; hi J]
+                        mma_f16(d, sdesc32(a_blj), sdesc32(bf + bpitch), idesc_bf, 1u);        // [hi J; -hi R]
                         issued = true;
                         mma_commit(empty_bar(s));
                     }
@@ -363,10 +422,9 @@ __global__ void __launch_bounds__(kT3Threads, 1) xcorr_tf32_kernel(const __grid_
                 }
                 unsigned char *st = tiles + (size_t)s * P.stage_bytes;
                 unsigned char *bb = diag ? st : st + P.a_off;
-                if (!diag)   // row inputs: hi in place, lo into planes 2 and 3 of the A region
-                    convert_pair(st, st + kT3APlane, st + 2 * kT3APlane, st + 3 * kT3APlane, nullptr, nullptr, 128,
-                                 ct);
-                convert_pair(bb, bb + pitch, bb + 3 * pitch, bb + 4 * pitch, bb + 2 * pitch, bb + 5 * pitch, n, ct);
+                if (!diag)   // row inputs: BF16 planes after the two TF32 planes of the A region
+                    convert_split(st, kT3APlane, st + kT3ABf, kT3ABfPlane, 128, false, ct);
+                convert_split(bb, pitch, bb + 3 * pitch, (unsigned)n * kT3BfRowBytes, n, true, ct);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(conv_bar(s));

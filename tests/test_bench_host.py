@@ -54,10 +54,17 @@ def test_workload_counts():
     assert bench.fp32_alu_peak_tflops(152) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
     # both arms print the same config dict
     assert bench.config_of(w, 1) == bench.config_of(w, 1) and bench.config_of(w, 1)["x_stage"] == "tf32_split"
-    # executed tensor work of the TF32 split at 64 stations: 6 MMAs of 128 x 256 x 8 per 8 spectra per channel
+    # executed tensor work of the TF32 split at 64 stations, per 16 spectra per channel: 4 TF32 MMAs of
+    # 128 x 256 x 8 and 4 BF16 MMAs of 128 x 256 x 16
     class _C:
         I_pad, S_pad = 128, 3072
-    assert bench.executed_xflops(_C, w, 4) == pytest.approx(6 * 2 * 128 * 256 * 8 * 384 * 64 * 244)
+    ex_t, ex_b = bench.executed_xflops_split(_C, w)
+    assert ex_t == pytest.approx(4 * 2 * 128 * 256 * 8 * 192 * 64 * 244)
+    assert ex_b == pytest.approx(4 * 2 * 128 * 256 * 16 * 192 * 64 * 244)
+    # the mixed roofline: at equal peaks the floor is the total flops over the peak
+    r = bench.split_roofline(1e12, (2e12, 4e12), 10.0, 1000.0, 1000.0)
+    assert r["floor_ms"] == pytest.approx(3.0) and r["frac"] == pytest.approx(0.3)
+    assert r["executed_floor_ms"] == pytest.approx(6.0)
     assert bench.aggregate_value(10.0, 1, 2.0) == 5.0
 
 

@@ -61,9 +61,9 @@ def test_xstage_fp16_full_shape_sampled():
 
 
 def test_xstage_tf32_split_full_shape_sampled():
-    """The FP32-accurate tensor-core X-stage (hi/lo TF32 split) on FP32 planar
-    operands: 48 accumulator chains of 64 spectra summed in IEEE FP32 per
-    channel; held to the FP32 path's bound (1e-5)."""
+    """The FP32-accurate tensor-core X-stage (hi hi' in TF32, hi lo' + lo hi'
+    in BF16) on FP32 planar operands: 48 accumulator chains of 64 spectra
+    summed in IEEE FP32 per channel; held to the FP32 path's bound (1e-5)."""
     c = _correlator(4)
     I = 2 * N
     g = torch.Generator(device="cuda").manual_seed(180104836)

@@ -2,11 +2,13 @@
 
 Each FP32 corrected sample x is split in the kernel into hi = x with the 13
 low mantissa bits cleared (exactly a TF32 value) and lo = x - hi (exact in
-FP32); the MMAs form hi hi' + hi lo' + lo hi' with FP32 accumulation. The
-dropped lo lo' term and the TF32 rounding of lo are each below 2^-20 of a
-product, so the visibilities must meet the FP32 path's bound: normwise
-relative error per subband below 1e-5 against the oracle, and agreement with
-the FFMA X-stage on the same corrected block to the same level.
+FP32, |lo| < 2^-10 |x|); the MMAs form hi hi' in TF32 and the cross terms
+hi lo' + lo hi' in BF16, all with FP32 accumulation. The BF16 rounding of
+the cross terms' operands moves each product by at most 2^-18 of itself
+(about 2^-21 RMS, zero mean) and the dropped lo lo' term is below 2^-20, so
+the visibilities must meet the FP32 path's bound: normwise relative error
+per subband below 1e-5 against the oracle, and agreement with the FFMA
+X-stage on the same corrected block to the same level.
 """
 import numpy as np
 import pytest
@@ -120,11 +122,16 @@ def _einsum_vis(y):
 def test_tf32_split_kernel_on_given_operands(exact, N):
     """fx_correlate alone on planar FP32 operands written here: values with
     13 zero low mantissa bits (hi only, lo = 0) and arbitrary FP32 values
-    (lo carries the low bits) against an FP64 einsum. Bound: each TMEM
-    accumulator chain spans 64 spectra = 48 MMAs, and the tensor core's
-    accumulation may lose up to 2^-24 of the running sum per MMA (48 x 2^-24 =
-    2.9e-6), plus the dropped lo lo' term (below 2^-20); chains are summed in
-    IEEE FP32. So 4e-6 normwise, against 1e-5 for the FP32 path end to end.
+    (lo carries the low bits) against an FP64 einsum. The second kind also
+    checks that the TF32 MMAs read a raw FP32 operand as its hi part (the
+    kernel leaves the low bits in place): a TF32 MMA that used the low bits
+    or rounded them would be off by up to 2^-11 per product. Bound: each TMEM
+    accumulator chain spans 64 spectra = 32 MMAs (4 TF32 + 4 BF16 per 16
+    spectra), and the tensor core's accumulation may lose up to 2^-24 of the
+    running sum per MMA (32 x 2^-24 = 1.9e-6), plus the BF16 rounding of the
+    cross terms (zero mean) and the dropped lo lo' term (below 2^-20); chains
+    are summed in IEEE FP32. So 4e-6 normwise, against 1e-5 for the FP32 path
+    end to end.
     Station counts above 64 exercise off-diagonal column tiles (A and B from
     different inputs) and ragged diagonal tiles of the last row block.
     Per baseline, max |dV_ij| / sqrt(|V_ii| |V_jj|) (so cross terms are not
