@@ -210,11 +210,12 @@ fx_status fx_channelize_correct(fx_handle *h, const void *d_raw, const double *d
  *   vis[sb][k][b(i,j)][2p+q] = sum_{s<S} Y[i,p] conj(Y[j,q])  for i <= j.
  * d_corr: corr layout of the handle's precision; d_vis: vis layout. FP32
  * operands run on the CUDA cores; FP16/BF16/split operands on the tcgen05
- * tensor cores with FP32 accumulation (split: hi*hi' + hi*lo' + lo*hi');
+ * tensor cores with FP32 accumulation (split: hi*hi' + hi*lo' + lo*hi',
+ * accumulator chains restarted every 256 spectra and summed in IEEE FP32);
  * FX_TF32_SPLIT operands (FP32 planar) on the tcgen05 tensor cores as hi/lo
- * TF32 parts with FP32 accumulation, accumulator chains restarted every 64
- * spectra and summed in IEEE FP32 (FP32 accuracy, any station count up to
- * 512; results reproducible run to run). */
+ * parts (hi*hi' in TF32, the cross terms in BF16) with FP32 accumulation,
+ * accumulator chains restarted every 64 spectra and summed in IEEE FP32 (FP32
+ * accuracy, any station count up to 512; results reproducible run to run). */
 fx_status fx_correlate(fx_handle *h, const void *d_corr, float *d_vis, fx_stream stream);
 
 /* End to end from host memory: raw samples in, visibilities out, for all

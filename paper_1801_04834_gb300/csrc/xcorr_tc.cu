@@ -34,6 +34,14 @@
 //   warps 2-5  epilogue: tcgen05.ld of their 32-lane TMEM quadrant, scale by
 //              1/operand_scale^2, store the upper-triangle baselines only
 //
+// Accumulator chains. FP16/BF16 accumulate an item's whole block in one TMEM
+// accumulator. Split FP16 restarts it every 4 stages (256 spectra): the tensor
+// core's FP32 accumulation truncates each addition, so a long chain drifts by
+// about 2^-24 of the running value per MMA, more than the lo planes win back.
+// The epilogue stores an item's first chain and adds the later ones with
+// vector FP32 reductions in L2 (red.global.add.v4.f32, round to nearest);
+// each entry has one owner lane, which issues its chains in order.
+//
 // Every mbarrier wait is bounded (clock64 budget). On expiry the thread
 // records a code in the status word and raises a shared abort flag; all roles
 // leave their loops, the producer waits (bounded) for the loads it still has
@@ -90,6 +98,7 @@ struct TcCommon {
     long long timeout_cycles;
     int no_tma;                       // failure-detection test: issue no loads
     int accumulate;                   // add to the visibilities instead of writing them
+    int chunk;                        // stages per accumulator chain (0: the whole item)
 };
 
 template <int MAXJ>
@@ -119,6 +128,14 @@ __device__ __forceinline__ bool wait_bounded(unsigned bar, unsigned parity, vola
     }
     return true;
 }
+// Vector FP32 reduction into global memory (performed in L2, round to nearest).
+__device__ __forceinline__ void red_add4(float2 *addr, float4 v)
+{
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
 // ---- work-item decoding --------------------------------------------------------
 template <int MAXJ>
 __device__ __forceinline__ Item decode(const TcParams<MAXJ> &P, long long w)
@@ -261,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1) xcorr_tc_kernel(const __grid_cons
         if (lane == 0) {
             long long it = 0, acc_it = 0;
             bool ok = true, issued = false;
-            for (long long w = blockIdx.x; w < a.n_items && ok; w += gridDim.x, ++acc_it) {
+            for (long long w = blockIdx.x; w < a.n_items && ok; w += gridDim.x) {
                 const Item itm = decode(P, w);
                 const TcJob &J = P.jobs[itm.job];
                 int row0, col0, ncols;
@@ -269,60 +286,64 @@ __global__ void __launch_bounds__(kThreads, 1) xcorr_tc_kernel(const __grid_cons
                 const bool diag = (col0 == row0);
                 const unsigned idesc = make_idesc(a.bf16, ncols, false);
                 const unsigned idesc_neg = make_idesc(a.bf16, ncols, true);
-                const int ab = (int)(acc_it % a.nacc);
-                const unsigned aph = (unsigned)((acc_it / a.nacc) & 1);
-                if (!wait_bounded(acce_bar(ab), aph ^ 1u, abort_flag, a, 2)) { ok = false; break; }
-                tc_fence_after();
-                const unsigned d_re = tmem_base + (unsigned)(ab * a.acc_stride);
-                const unsigned d_im = d_re + (unsigned)a.ncm;
-                for (int kc = 0; kc < J.nk; ++kc, ++it) {
-                    const int s = (int)(it % a.stages);
-                    const unsigned ph = (unsigned)((it / a.stages) & 1);
-                    if (!wait_bounded(full_bar(s), ph, abort_flag, a, 2)) { ok = false; break; }
+                const int clen = a.chunk > 0 ? a.chunk : J.nk;   // stages per accumulator chain
+                for (int k0 = 0; k0 < J.nk && ok; k0 += clen, ++acc_it) {
+                    const int ab = (int)(acc_it % a.nacc);
+                    const unsigned aph = (unsigned)((acc_it / a.nacc) & 1);
+                    if (!wait_bounded(acce_bar(ab), aph ^ 1u, abort_flag, a, 2)) { ok = false; break; }
                     tc_fence_after();
-                    const unsigned tile = tiles_u32 + (unsigned)s * a.stage_bytes;
-                    const unsigned btile = diag ? tile : tile + a_region;
-                    const unsigned bpl = diag ? a_plane : b_plane;
+                    const unsigned d_re = tmem_base + (unsigned)(ab * a.acc_stride);
+                    const unsigned d_im = d_re + (unsigned)a.ncm;
+                    const int k1 = min(J.nk, k0 + clen);
+                    for (int kc = k0; kc < k1; ++kc, ++it) {
+                        const int s = (int)(it % a.stages);
+                        const unsigned ph = (unsigned)((it / a.stages) & 1);
+                        if (!wait_bounded(full_bar(s), ph, abort_flag, a, 2)) { ok = false; break; }
+                        tc_fence_after();
+                        const unsigned tile = tiles_u32 + (unsigned)s * a.stage_bytes;
+                        const unsigned btile = diag ? tile : tile + a_region;
+                        const unsigned bpl = diag ? a_plane : b_plane;
 #pragma unroll
-                    for (int kk = 0; kk < kBK / 16; ++kk) {
-                        const unsigned acc = (kc | kk) ? 1u : 0u;
-                        // A operand rows = the row block, B operand rows = the column block
-                        const unsigned long long ar0 = smem_desc(tile + 0 * a_plane + kk * 32);
-                        const unsigned long long aj0 = smem_desc(tile + 1 * a_plane + kk * 32);
-                        const unsigned long long br0 = smem_desc(btile + 0 * bpl + kk * 32);
-                        const unsigned long long bj0 = smem_desc(btile + 1 * bpl + kk * 32);
-                        if (a.planes == 2) {
-                            mma_f16(d_re, ar0, br0, idesc, acc);
-                            mma_f16(d_re, aj0, bj0, idesc, 1u);
-                            mma_f16(d_im, aj0, br0, idesc, acc);
-                            mma_f16(d_im, ar0, bj0, idesc_neg, 1u);
-                        } else {
-                            const unsigned long long ar1 = smem_desc(tile + 2 * a_plane + kk * 32);
-                            const unsigned long long aj1 = smem_desc(tile + 3 * a_plane + kk * 32);
-                            const unsigned long long br1 = smem_desc(btile + 2 * bpl + kk * 32);
-                            const unsigned long long bj1 = smem_desc(btile + 3 * bpl + kk * 32);
-                            // (hi, hi)
-                            mma_f16(d_re, ar0, br0, idesc, acc);
-                            mma_f16(d_re, aj0, bj0, idesc, 1u);
-                            mma_f16(d_im, aj0, br0, idesc, acc);
-                            mma_f16(d_im, ar0, bj0, idesc_neg, 1u);
-                            // (hi, lo)
-                            mma_f16(d_re, ar0, br1, idesc, 1u);
-                            mma_f16(d_re, aj0, bj1, idesc, 1u);
-                            mma_f16(d_im, aj0, br1, idesc, 1u);
-                            mma_f16(d_im, ar0, bj1, idesc_neg, 1u);
-                            // (lo, hi)
-                            mma_f16(d_re, ar1, br0, idesc, 1u);
-                            mma_f16(d_re, aj1, bj0, idesc, 1u);
-                            mma_f16(d_im, aj1, br0, idesc, 1u);
-                            mma_f16(d_im, ar1, bj0, idesc_neg, 1u);
+                        for (int kk = 0; kk < kBK / 16; ++kk) {
+                            const unsigned acc = (kc != k0 || kk) ? 1u : 0u;
+                            // A operand rows = the row block, B operand rows = the column block
+                            const unsigned long long ar0 = smem_desc(tile + 0 * a_plane + kk * 32);
+                            const unsigned long long aj0 = smem_desc(tile + 1 * a_plane + kk * 32);
+                            const unsigned long long br0 = smem_desc(btile + 0 * bpl + kk * 32);
+                            const unsigned long long bj0 = smem_desc(btile + 1 * bpl + kk * 32);
+                            if (a.planes == 2) {
+                                mma_f16(d_re, ar0, br0, idesc, acc);
+                                mma_f16(d_re, aj0, bj0, idesc, 1u);
+                                mma_f16(d_im, aj0, br0, idesc, acc);
+                                mma_f16(d_im, ar0, bj0, idesc_neg, 1u);
+                            } else {
+                                const unsigned long long ar1 = smem_desc(tile + 2 * a_plane + kk * 32);
+                                const unsigned long long aj1 = smem_desc(tile + 3 * a_plane + kk * 32);
+                                const unsigned long long br1 = smem_desc(btile + 2 * bpl + kk * 32);
+                                const unsigned long long bj1 = smem_desc(btile + 3 * bpl + kk * 32);
+                                // (hi, hi)
+                                mma_f16(d_re, ar0, br0, idesc, acc);
+                                mma_f16(d_re, aj0, bj0, idesc, 1u);
+                                mma_f16(d_im, aj0, br0, idesc, acc);
+                                mma_f16(d_im, ar0, bj0, idesc_neg, 1u);
+                                // (hi, lo)
+                                mma_f16(d_re, ar0, br1, idesc, 1u);
+                                mma_f16(d_re, aj0, bj1, idesc, 1u);
+                                mma_f16(d_im, aj0, br1, idesc, 1u);
+                                mma_f16(d_im, ar0, bj1, idesc_neg, 1u);
+                                // (lo, hi)
+                                mma_f16(d_re, ar1, br0, idesc, 1u);
+                                mma_f16(d_re, aj1, bj0, idesc, 1u);
+                                mma_f16(d_im, aj1, br0, idesc, 1u);
+                                mma_f16(d_im, ar1, bj0, idesc_neg, 1u);
+                            }
                         }
+                        issued = true;
+                        mma_commit(empty_bar(s));          // stage free once these MMAs have read it
                     }
-                    issued = true;
-                    mma_commit(empty_bar(s));          // stage free once these MMAs have read it
+                    if (!ok) break;
+                    mma_commit(accf_bar(ab));              // accumulator ready for the epilogue
                 }
-                if (!ok) break;
-                mma_commit(accf_bar(ab));              // accumulator ready for the epilogue
             }
             if (!ok && issued) {
                 mma_commit(drain_bar);
@@ -334,62 +355,78 @@ __global__ void __launch_bounds__(kThreads, 1) xcorr_tc_kernel(const __grid_cons
         // ================= epilogue (warps 2..5) =================
         const int qd = warp & 3;                      // TMEM lane quadrant of this warp
         long long acc_it = 0;
-        for (long long w = blockIdx.x; w < a.n_items; w += gridDim.x, ++acc_it) {
+        bool live = true;
+        for (long long w = blockIdx.x; w < a.n_items && live; w += gridDim.x) {
             const Item itm = decode(P, w);
             const TcJob &J = P.jobs[itm.job];
             int row0, col0, ncols;
             item_cols(P, J, itm, row0, col0, ncols);
-            const int ab = (int)(acc_it % a.nacc);
-            const unsigned aph = (unsigned)((acc_it / a.nacc) & 1);
-            const bool got = wait_bounded(accf_bar(ab), aph, abort_flag, a, 3);
-            if (!__all_sync(0xffffffffu, got)) break;   // warp-uniform exit
-            tc_fence_after();
+            const int clen = a.chunk > 0 ? a.chunk : J.nk;
             const int ia = row0 + 32 * qd + lane;       // this lane's row input
             const int i = ia >> 1, p = ia & 1;
             const int i_warp_min = (row0 + 32 * qd) >> 1;
             const unsigned lane_off = (unsigned)(32 * qd) << 16;
-            const unsigned t_re = tmem_base + lane_off + (unsigned)(ab * a.acc_stride);
-            const unsigned t_im = t_re + (unsigned)a.ncm;
             float2 *vrow = J.vis + itm.gch * J.B * 4;
-            for (int cc = 0; cc < ncols / 16; ++cc) {
-                const int j0 = (col0 >> 1) + 8 * cc;   // first station of this 16-column chunk
-                if (j0 >= J.N) break;
-                if (j0 + 7 < i_warp_min) continue;    // whole chunk below the diagonal for this warp
-                float re[16], im[16];
-                tmem_ld16(t_re + 16 * cc, re);
-                tmem_ld16(t_im + 16 * cc, im);
-                // accumulating: the sums of earlier time chunks, loaded while TMEM is read
-                float4 old[8];
-                if (a.accumulate) {
+            for (int k0 = 0; k0 < J.nk; k0 += clen, ++acc_it) {
+                const int ab = (int)(acc_it % a.nacc);
+                const unsigned aph = (unsigned)((acc_it / a.nacc) & 1);
+                const bool got = wait_bounded(accf_bar(ab), aph, abort_flag, a, 3);
+                if (!__all_sync(0xffffffffu, got)) {   // warp-uniform exit
+                    live = false;
+                    break;
+                }
+                tc_fence_after();
+                // the first chain of an item is written (or, accumulating, added by
+                // load + add + store); later chains are added by FP32 reductions in L2
+                const bool first = (k0 == 0);
+                const unsigned t_re = tmem_base + lane_off + (unsigned)(ab * a.acc_stride);
+                const unsigned t_im = t_re + (unsigned)a.ncm;
+                for (int cc = 0; cc < ncols / 16; ++cc) {
+                    const int j0 = (col0 >> 1) + 8 * cc;   // first station of this 16-column chunk
+                    if (j0 >= J.N) break;
+                    if (j0 + 7 < i_warp_min) continue;    // whole chunk below the diagonal for this warp
+                    float re[16], im[16];
+                    tmem_ld16(t_re + 16 * cc, re);
+                    tmem_ld16(t_im + 16 * cc, im);
+                    // accumulating: the sums of earlier time pieces, loaded while TMEM is read
+                    float4 old[8];
+                    if (a.accumulate && first) {
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) {
+                            const int j = j0 + jj;
+                            old[jj] = (i <= j && j < J.N) ? *reinterpret_cast<const float4 *>(
+                                                                vrow + ((long long)j * (j + 1) / 2 + i) * 4 + 2 * p)
+                                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                    }
+                    tmem_ld_wait();
 #pragma unroll
                     for (int jj = 0; jj < 8; ++jj) {
                         const int j = j0 + jj;
-                        old[jj] = (i <= j && j < J.N)
-                                      ? *reinterpret_cast<const float4 *>(vrow + ((long long)j * (j + 1) / 2 + i) * 4 + 2 * p)
-                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                }
-                tmem_ld_wait();
-#pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    const int j = j0 + jj;
-                    if (i <= j && j < J.N) {
-                        const long long b = (long long)j * (j + 1) / 2 + i;
-                        const float s = a.inv_scale2;
-                        float4 v = make_float4(re[2 * jj] * s, im[2 * jj] * s, re[2 * jj + 1] * s, im[2 * jj + 1] * s);
-                        if (a.accumulate) {
-                            v.x += old[jj].x;
-                            v.y += old[jj].y;
-                            v.z += old[jj].z;
-                            v.w += old[jj].w;
+                        if (i <= j && j < J.N) {
+                            const long long b = (long long)j * (j + 1) / 2 + i;
+                            const float s = a.inv_scale2;
+                            float4 v = make_float4(re[2 * jj] * s, im[2 * jj] * s, re[2 * jj + 1] * s,
+                                                   im[2 * jj + 1] * s);
+                            float2 *dst = vrow + b * 4 + 2 * p;
+                            if (!first) {
+                                red_add4(dst, v);
+                                continue;
+                            }
+                            if (a.accumulate) {
+                                v.x += old[jj].x;
+                                v.y += old[jj].y;
+                                v.z += old[jj].z;
+                                v.w += old[jj].w;
+                            }
+                            *reinterpret_cast<float4 *>(dst) = v;
                         }
-                        *reinterpret_cast<float4 *>(vrow + b * 4 + 2 * p) = v;
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce_bar(ab));
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acce_bar(ab));
         }
     }
 
@@ -465,6 +502,15 @@ bool geometry(const TcConfig &cfg, int precision, const std::vector<JobShape> &j
     c.ncm = (ncm + 31) / 32 * 32;
     c.acc_stride = 2 * c.ncm;
     c.nacc = (2 * c.acc_stride <= kTmemCols) ? 2 : 1;
+    // Split FP16: the tensor core's FP32 accumulation truncates each addition
+    // (about 2^-24 of the running value per MMA, 24 MMAs per accumulator and
+    // 64-spectrum stage), which would undo what the lo planes win back over a
+    // long integration (3.8e-5 over 3072 spectra in one chain); chains of 4
+    // stages (256 spectra) are added in IEEE FP32 instead (3.1e-6, 6% more
+    // time for the L2 reductions; 128-spectrum chains 1.5e-6 at 13% more).
+    // Plain FP16/BF16 keep one chain per item: they are the fast forms, well
+    // inside their bounds.
+    c.chunk = (planes == 4 && c.nacc == 2) ? 4 : 0;
     c.bf16 = precision == FX_BF16 ? 1u : 0u;
     return true;
 }

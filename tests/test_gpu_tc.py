@@ -72,6 +72,35 @@ def test_tc_correlate_operand_exact(kind, N, C, S, SB):
     assert np.max(np.abs(auto[..., 0, 1])) <= 1e-5 * np.max(np.abs(auto[..., 0, 0]))
 
 
+def test_split_fp16_wins_back_accuracy_over_a_long_block():
+    """Split FP16 (hi + lo planes) against plain FP16 over a 3072-spectrum
+    block (the LOFAR 16-bit integration), operands from the same FP32 noise.
+    The split kernel restarts its accumulators every 256 spectra and adds the
+    chains in IEEE FP32 (the tensor core truncates each accumulation, about
+    2^-24 of the running value per MMA, 24 MMAs per 64 spectra: at most
+    96 x 2^-24 = 5.7e-6 per chain), so against the exact FP64 correlation of
+    the FP32 values it stays below 6e-6 normwise (operands hold 2^-22), while
+    plain FP16 (operand rounding 2^-12 and one chain over the whole block) is
+    at least three times further off."""
+    N, C, S, SB = 32, 16, 3072, 1
+    corr64 = synth.noise(4242, (SB, C, S, N, 2, 2), sigma=30.0)
+    corr32 = corr64.astype(np.float32).astype(np.float64)
+    ref = oracle.correlate(corr32)
+    blk = synth.Block(0, SB, N, 2, C, 16, S, None, synth.kaiser_sinc_taps(16, C), synth.subband_centres(SB))
+    err = {}
+    for kind in ("f16", "split"):
+        c = make_corr(blk, precision=PREC[kind])
+        ops, held = planar(corr32, c.I_pad, c.S_pad, kind)
+        got = c.correlate(ops.cuda().contiguous()).cpu().numpy().astype(np.float64)
+        err[kind] = float(np.max(per_subband_rel(got, ref)))
+        # against the values the operands hold, only the accumulation is left
+        err[kind + "_held"] = float(np.max(per_subband_rel(got, oracle.correlate(held))))
+        c.close()
+    print(err)
+    assert err["split"] < 6e-6 and err["split_held"] < 6e-6, err
+    assert err["split"] * 3 < err["f16"], err
+
+
 def test_tc_operand_scale():
     """operand_scale multiplies the operands and is divided out of vis."""
     N, C, S, SB = 16, 16, 64, 1
