@@ -280,11 +280,13 @@ ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const f
 //  * pass 2 runs with lane = row: a warp takes (group of 32 rows, k1) items,
 //    so each output store of a warp is one station's 16 spectra x 2 pols of
 //    one channel, 256 contiguous bytes of the spectrum-blocked layout;
-//  * the FIR threads, which have the lighter share of the work, tabulate
-//    exp(i phi) x flag per (station, channel, spectrum) of their round into a
-//    double-buffered table (one __sincosf per owner and round, then rotations
-//    by exp(2 i step)); the FFT threads multiply in bandpass x gain (a
-//    per-CTA table) and the phase factor.
+//  * the FIR threads, which have the lighter share of the work, multiply
+//    their FIR output by the input's complex gain x operand scale (the FFT is
+//    linear, so this equals multiplying its output) and tabulate
+//    bandpass x exp(i phi) x flag per (station, channel, spectrum) of their
+//    round into a double-buffered table (one __sincosf per owner and round,
+//    then rotations by exp(2 i step)); the FFT threads multiply each output
+//    by that one factor.
 template <int C>
 struct FusedWsCfg {
     static constexpr int R = PpfCfg<C>::R;
@@ -309,7 +311,7 @@ constexpr size_t fused_ws_smem_bytes()
 {
     using W = FusedWsCfg<C>;
     return (size_t)C * sizeof(float2) + 2ull * kRound * W::NPC * C * kPols * sizeof(TIn) +
-           (2ull * W::USZ + 2ull * W::ESZ + (size_t)W::IC * C) * sizeof(float2) + 16;   // + 2 mbarriers
+           (2ull * W::USZ + 2ull * W::ESZ) * sizeof(float2) + 16;   // + 2 mbarriers
 }
 
 // CTAs per SM the shared memory allows: 3 at C = 64, 2 at C = 16 (four stations' rows)
@@ -344,9 +346,8 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
     unsigned char *inbuf = smem + C * sizeof(float2);
     float2 *u = reinterpret_cast<float2 *>(inbuf + 2 * BUF_BYTES);   // [2][USZ]
     float2 *et = u + 2 * USZ;                                         // [2][NPC][C][EJ]
-    float2 *bgt = et + 2 * ESZ;                                       // [IC][C] bandpass x gain
     // raw-row mbarriers (one station per CTA: its rows arrive by bulk copy)
-    const unsigned rbar = tc::smem_u32(bgt + IC * C);
+    const unsigned rbar = tc::smem_u32(et + 2 * ESZ);
 
     const int tid = threadIdx.x;
     const int sb = blockIdx.z;
@@ -358,13 +359,6 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
     auto rowp = [&](float2 *uq, int r) { return uq + r * ROW + (r / kRound) * PADG; };
 
     for (int i = tid; i < C; i += ALL) tw[i] = twiddle[i];
-    for (int e = tid; e < IC * C; e += ALL) {
-        const int il = e / C, k = e % C;
-        const int n = min(n0 + il / kPols, N - 1);
-        const float b = bandpass ? bandpass[(long long)n * C + k] : 1.f;
-        const float2 g = gains ? gains[n * kPols + il % kPols] : make_float2(1.f, 0.f);
-        bgt[e] = make_float2(b * g.x * scale, b * g.y * scale);
-    }
     if constexpr (NPC == 1) {
         if (tid == 0) {
             tc::mbar_init(rbar, 1);
@@ -412,6 +406,10 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
         const float2 pst = phase[((long long)sb * N + own_n) * C + own_nc % C];   // (phi0, step)
         float sn2, cs2;
         sincosf(2.f * pst.y, &sn2, &cs2);           // exp(2 i step): this owner's spectra are 2 apart
+        const float bpo = bandpass ? bandpass[(long long)own_n * C + own_nc % C] : 1.f;
+        const int n_fir = min(n0 + nl, N - 1);
+        const float2 gg = gains ? gains[n_fir * kPols + p] : make_float2(1.f, 0.f);
+        const float2 gsc = make_float2(gg.x * scale, gg.y * scale);
         const float2 rot2 = make_float2(cs2, sn2);
         float2 h[T];
 #pragma unroll
@@ -462,7 +460,7 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
                 float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int k = 0; k < T; ++k) acc = __ffma2_rn(h[k], win[(j + k) % T], acc);
-                fo[j * ROW] = acc;                  // row (input, spectrum j)
+                fo[j * ROW] = cmul(acc, gsc);       // row (input, spectrum j), times gain x scale
             }
             // exp(i phi) x flag of this round: phi = phi0 + s step reduced to
             // [-pi, pi] (two-constant Cody-Waite split of 2 pi), then __sincosf
@@ -476,6 +474,8 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
                 float r = fmaf(-kq, 6.28125f, phi);
                 r = fmaf(-kq, 1.9353071795864769e-3f, r);
                 __sincosf(r, &e.y, &e.x);
+                e.x *= bpo;
+                e.y *= bpo;
             }
 #pragma unroll
             for (int qq = 0; qq < kRound / 2; ++qq) {
@@ -542,12 +542,11 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
 #pragma unroll
                 for (int m = 0; m < R; ++m) v[m] = uq[(k1 * R + m) * RS + r];
                 fft_reg<R>(v);
-                const float2 *bg = bgt + il * C;
                 const float2 *e = eq + ((il / kPols) * C) * EJ + j;
 #pragma unroll
                 for (int k2 = 0; k2 < R; ++k2) {
                     const int kout = k1 + R * ((k2 + R / 2) % R);
-                    v[k2] = cmul(v[k2], cmul(bg[kout], e[kout * EJ]));
+                    v[k2] = cmul(v[k2], e[kout * EJ]);
                 }
                 if (it == W::ITEMS / 4 - 1 && b + 2 < nrounds) named_bar_arrive(kBarEmpty + q, ALL);
                 const int s = sr + j, i = 2 * n0 + il;
@@ -617,18 +616,21 @@ __global__ void planar_pad_kernel(unsigned short *__restrict__ corr, long long n
 // ---------------------------------------------------------------------------
 // Warp-specialised fused kernel for C = 256 with planar outputs (OUT = 2..5):
 // one CTA per (station, pol), 256 FIR threads (one channel each) and 256 FFT
-// threads, one CTA per SM. A round's rows (16 spectra of one input) fit twice
-// in shared memory at this channel count only per input; the CTAs of a
-// station's two pols are neighbours in the grid and read the same raw rows
-// (the second read mostly from L2). FIR round b -> u[b & 1] and the whole
-// per-sample factor bandpass x gain x flag x exp(i phi) of its 16 spectra
-// (one __sincosf per channel and round, multiplied once by bandpass x gain,
-// then rotations by exp(i step) computed in FP32 from the FP64-derived step;
-// bandpass x gain is constant per channel within a CTA, which serves one
-// input) -> FULL; FFT round b:
-// pass 1 (row = 16 lanes), transposed into
-// P1[k1][n2][row] over u[b & 1] after barrier FFT, pass 2 with lane = spectrum
-// (a half-warp per k1), so a warp store is 2 x 32 bytes of planar rows.
+// threads in two groups of 128, one CTA per SM. A round's rows (16 spectra
+// of one input) fit twice in shared memory at this channel count only per
+// input; the CTAs of a station's two pols are neighbours in the grid and read
+// the same raw rows (the second read mostly from L2). FIR round b -> u[b & 1]
+// and the whole per-sample factor bandpass x gain x flag x exp(i phi) of its
+// 16 spectra (one __sincosf per channel and round, multiplied once by
+// bandpass x gain, then rotations by exp(i step) computed in FP32 from the
+// FP64-derived step; bandpass x gain is constant per channel within a CTA,
+// which serves one input) -> FULL[b & 1]. FFT group g takes the rounds
+// b = g mod 2 (row buffer g) with its own named barrier, so two rounds are in
+// FFT at once and each FFT thread has two transforms in flight per pass
+// (36.6 against 39.5 ms at the 8-bit workload with one group of 256): pass 1
+// (row = 16 lanes), transposed into P1[k1][n2][row] over u[g] after the
+// group's barrier, pass 2 with lane = spectrum (a half-warp per k1), so a
+// warp store is 2 x 32 bytes of planar rows.
 struct Ws256 {
     static constexpr int C = 256, R = 16, NF = 256;
     static constexpr int ROW = C + 16;                  // FIR row stride (float2)
@@ -660,6 +662,8 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
     constexpr int ROW_BYTES = C * kPols * (int)sizeof(TIn);     // one raw time row of the station (both pols)
     constexpr int BUF_BYTES = kRound * ROW_BYTES;
     constexpr int ALL = 2 * NF;
+    constexpr int NG = NF / 2;                  // FFT threads per group: group g takes rounds b = g mod 2
+    constexpr int HAND = NF + NG;               // FULL / EMPTY: the FIR threads and one FFT group
     static_assert(OUT >= 2 && OUT <= 5, "planar outputs");
     static_assert(ROW_BYTES % 16 == 0, "rows must be whole 16-byte chunks");
     static_assert(ws256_smem_bytes<TIn>() <= 227 * 1024, "one CTA per SM");
@@ -734,7 +738,7 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
             const int q = b & 1;
             const int sr = s0 + b * kRound;
             raw_wait(rbar + 8u * q, (unsigned)(((b + q) / 2) & 1), status, budget);   // round b's rows
-            if (b >= 2) named_bar_sync(kBarEmpty + q, ALL);
+            if (b >= 2) named_bar_sync(kBarEmpty + q, HAND);
             const TIn *in = reinterpret_cast<const TIn *>(inbuf + q * BUF_BYTES);
             float2 *uq = u + q * USZ;
 #pragma unroll
@@ -771,69 +775,100 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
                     e = cmul(e, rot);
                 }
             }
-            named_bar_arrive(kBarFull + q, ALL);
+            named_bar_arrive(kBarFull + q, HAND);
             named_bar_sync(kBarRaw, NF);                // every FIR thread has read raw buffer q
             if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             if (b + 2 < nrounds) issue(q, s0 + T - 1 + (b + 2) * kRound, kRound);
         }
     } else {
-        // ---------------- FFT threads ----------------
+        // ---------------- FFT threads: two groups of NG, group g = buffer g ----------------
         const int t = tid - NF;
+        const int g = t / NG, tg = t % NG;
+        const int bar_fft = g ? kBarFft2 : kBarFft;
         constexpr int planes = OUT == 4 ? 4 : 2;
         const long long pstride = (long long)I_pad * s_out;
         const int i = n * kPols + p;
-        for (int b = 0; b < nrounds; ++b) {
+        for (int b = g; b < nrounds; b += 2) {
             const int q = b & 1;
             const int sr = s0 + b * kRound;
             float2 *uq = u + q * USZ;
             const float2 *eq = et + q * ESZ;
-            named_bar_sync(kBarFull + q, ALL);
-            // pass 1: row tr = t / 16 (spectrum), column n2 = t mod 16
-            const int tr = t / R, n2 = t % R;
-            float2 v[R];
+            named_bar_sync(kBarFull + q, HAND);
+            // pass 1: two (row tr = spectrum, column n2) tasks per thread
+            float2 v[2][R];
 #pragma unroll
-            for (int n1 = 0; n1 < R; ++n1) v[n1] = uq[tr * ROW + R * n1 + n2];
-            fft_reg<R>(v);
+            for (int it = 0; it < 2; ++it) {
+                const int task = it * NG + tg;
+                const int tr = task / R, n2 = task % R;
 #pragma unroll
-            for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], tw2[k1 * R + n2]);
-            named_bar_sync(kBarFft, NF);                // every FFT thread has read u[q]
-#pragma unroll
-            for (int k1 = 0; k1 < R; ++k1) uq[(k1 * R + n2) * RS + tr] = v[k1];
-            named_bar_sync(kBarFft, NF);                // P1 complete
-            // pass 2: half-warp per k1, lane = spectrum j
-            const int k1 = t / 16, j = t % 16;
-#pragma unroll
-            for (int m = 0; m < R; ++m) v[m] = uq[(k1 * R + m) * RS + j];
-            fft_reg<R>(v);
-#pragma unroll
-            for (int k2 = 0; k2 < R; ++k2) {
-                const int kout = k1 + R * ((k2 + R / 2) % R);
-                v[k2] = cmul(v[k2], eq[kout * EJ + j]);
+                for (int n1 = 0; n1 < R; ++n1) v[it][n1] = uq[tr * ROW + R * n1 + n2];
             }
-            if (b + 2 < nrounds) named_bar_arrive(kBarEmpty + q, ALL);
-            const int s = sr + j;
-            if (sr + kRound > s_end && s >= s_end) {       // only in the block's last round
 #pragma unroll
-                for (int k2 = 0; k2 < R; ++k2) v[k2] = make_float2(0.f, 0.f);
+            for (int it = 0; it < 2; ++it) {
+                const int n2 = (it * NG + tg) % R;
+                fft_reg<R>(v[it]);
+#pragma unroll
+                for (int k1 = 1; k1 < R; ++k1) v[it][k1] = cmul(v[it][k1], tw2[k1 * R + n2]);
             }
-            const long long base = (long long)sb * C * planes * pstride + (long long)i * s_out + (s - s_base);
+            named_bar_sync(bar_fft, NG);                // every thread of the group has read u[q]
 #pragma unroll
-            for (int k2 = 0; k2 < R; ++k2) {
-                const int kout = k1 + R * ((k2 + R / 2) % R);
-                const float2 y = v[k2];
-                const long long o = base + (long long)kout * planes * pstride;
-                if constexpr (OUT == 5) {
-                    float *out = reinterpret_cast<float *>(corr);
-                    out[o] = y.x;
-                    out[o + pstride] = y.y;
-                } else {
-                    unsigned short *out = reinterpret_cast<unsigned short *>(corr);
-                    const unsigned short hr = to_bits(y.x, OUT), hi = to_bits(y.y, OUT);
-                    out[o] = hr;
-                    out[o + pstride] = hi;
-                    if constexpr (OUT == 4) {
-                        out[o + 2 * pstride] = __half_as_ushort(__float2half_rn(y.x - __half2float(__ushort_as_half(hr))));
-                        out[o + 3 * pstride] = __half_as_ushort(__float2half_rn(y.y - __half2float(__ushort_as_half(hi))));
+            for (int it = 0; it < 2; ++it) {
+                const int task = it * NG + tg;
+                const int tr = task / R, n2 = task % R;
+#pragma unroll
+                for (int k1 = 0; k1 < R; ++k1) uq[(k1 * R + n2) * RS + tr] = v[it][k1];
+            }
+            named_bar_sync(bar_fft, NG);                // P1 complete
+            // pass 2: two (k1, spectrum j) items per thread, a half-warp per k1
+#pragma unroll
+            for (int it = 0; it < 2; ++it) {
+                const int item = it * NG + tg;
+                const int k1 = item / 16, j = item % 16;
+#pragma unroll
+                for (int m = 0; m < R; ++m) v[it][m] = uq[(k1 * R + m) * RS + j];
+            }
+#pragma unroll
+            for (int it = 0; it < 2; ++it) {
+                const int item = it * NG + tg;
+                const int k1 = item / 16, j = item % 16;
+                fft_reg<R>(v[it]);
+#pragma unroll
+                for (int k2 = 0; k2 < R; ++k2) {
+                    const int kout = k1 + R * ((k2 + R / 2) % R);
+                    v[it][k2] = cmul(v[it][k2], eq[kout * EJ + j]);
+                }
+            }
+            if (b + 2 < nrounds) named_bar_arrive(kBarEmpty + q, HAND);
+#pragma unroll
+            for (int it = 0; it < 2; ++it) {
+                const int item = it * NG + tg;
+                const int k1 = item / 16, j = item % 16;
+                const int s = sr + j;
+                if (sr + kRound > s_end && s >= s_end) {       // only in the block's last round
+#pragma unroll
+                    for (int k2 = 0; k2 < R; ++k2) v[it][k2] = make_float2(0.f, 0.f);
+                }
+                const long long base = (long long)sb * C * planes * pstride + (long long)i * s_out + (s - s_base);
+#pragma unroll
+                for (int k2 = 0; k2 < R; ++k2) {
+                    const int kout = k1 + R * ((k2 + R / 2) % R);
+                    const float2 y = v[it][k2];
+                    const long long o = base + (long long)kout * planes * pstride;
+                    if constexpr (OUT == 5) {
+                        float *out = reinterpret_cast<float *>(corr);
+                        out[o] = y.x;
+                        out[o + pstride] = y.y;
+                    } else {
+                        unsigned short *out = reinterpret_cast<unsigned short *>(corr);
+                        const unsigned short hr = to_bits(y.x, OUT), hi = to_bits(y.y, OUT);
+                        out[o] = hr;
+                        out[o + pstride] = hi;
+                        if constexpr (OUT == 4) {
+                            out[o + 2 * pstride] =
+                                __half_as_ushort(__float2half_rn(y.x - __half2float(__ushort_as_half(hr))));
+                            out[o + 3 * pstride] =
+                                __half_as_ushort(__float2half_rn(y.y - __half2float(__ushort_as_half(hi))));
+                        }
                     }
                 }
             }

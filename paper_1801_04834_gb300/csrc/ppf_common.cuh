@@ -82,6 +82,7 @@ enum {
     kBarFft = 2,     // FFT threads among themselves
     kBarFull = 3,    // FULL[0], FULL[1]: FIR round in the row buffer (ids 3, 4)
     kBarEmpty = 5,   // EMPTY[0], EMPTY[1]: FFT threads done with it (ids 5, 6)
+    kBarFft2 = 7,    // the second FFT group of the 256-channel kernel among itself
 };
 __device__ __forceinline__ void named_bar_sync(int id, int n)
 {
