@@ -69,6 +69,12 @@ __device__ __forceinline__ unsigned short to_bits(float x, int out)
     return __half_as_ushort(__float2half_rn(x));
 }
 
+// lo part of split FP16: x - hi rounded to FP16, hi = the FP16 bits of x
+__device__ __forceinline__ unsigned short lo_bits16(float x, unsigned short hi)
+{
+    return __half_as_ushort(__float2half_rn(x - __half2float(__ushort_as_half(hi))));
+}
+
 template <int C, int T, typename TIn, int OUT>
 __global__ void __launch_bounds__(PpfCfg<C>::NT, PpfCfg<C>::NT >= 512 ? 1 : 2)
 ppf_correct_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, const float *__restrict__ taps,
@@ -298,9 +304,9 @@ struct FusedWsCfg {
     static constexpr int PADG = 8;                       // float2 offset per input (16 rows)
     static constexpr int USZ = NTR * ROW + IC * PADG;    // one row buffer
     static constexpr int RS = NTR + 16 / R;              // P1 row stride
-    static constexpr int EJ = kRound + 1;                // phase table: 16 spectra + pad
+    static constexpr int EJ = kRound + 2;                // phase table: 16 spectra + pad (even: 16-byte pairs)
     static constexpr int ESZ = NPC * C * EJ;             // one phase-table buffer
-    static constexpr int ITEMS = (NTR / 32) * R;         // pass-2 items (row group, k1)
+    static constexpr int ITEMS = (NTR / 32) * (R / 2);   // pass-2 items (row group, pair of k1)
     static_assert(C == 16 || C == 64, "warp-specialised fused kernel: C = 16 or 64");
     static_assert(R * R * RS <= USZ, "P1 fits over the row buffer");
     static_assert(ITEMS % 4 == 0 && NTR % 32 == 0, "four FFT warps share the pass-2 items");
@@ -531,32 +537,44 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
                 for (int k1 = 0; k1 < R; ++k1) uq[(k1 * R + task % R) * RS + task / R] = v1[it][k1];
             }
             named_bar_sync(kBarFft, NF);                // P1 complete
-            // pass 2: lane = row (input il, spectrum j), item = (row group, k1)
+            // pass 2: a half-warp per k1 (two k1 per item), each lane two adjacent
+            // rows (input il, spectra j and j + 1), so the rows and the phase
+            // factors come in 16-byte loads and the planar stores go out in pairs
 #pragma unroll
             for (int it = 0; it < W::ITEMS / 4; ++it) {
                 const int item = warp + 4 * it;
-                const int g = item / R, k1 = item % R;
-                const int r = 32 * g + lane;
+                const int g = item / (R / 2), k1 = 2 * (item % (R / 2)) + lane / 16;
+                const int r = 32 * g + 2 * (lane % 16);
                 const int il = r / kRound, j = r % kRound;
-                float2 v[R];
+                float2 va[R], vb[R];
 #pragma unroll
-                for (int m = 0; m < R; ++m) v[m] = uq[(k1 * R + m) * RS + r];
-                fft_reg<R>(v);
+                for (int m = 0; m < R; ++m) {
+                    const float4 w = *reinterpret_cast<const float4 *>(uq + (k1 * R + m) * RS + r);
+                    va[m] = make_float2(w.x, w.y);
+                    vb[m] = make_float2(w.z, w.w);
+                }
+                fft_reg<R>(va);
+                fft_reg<R>(vb);
                 const float2 *e = eq + ((il / kPols) * C) * EJ + j;
 #pragma unroll
                 for (int k2 = 0; k2 < R; ++k2) {
                     const int kout = k1 + R * ((k2 + R / 2) % R);
-                    v[k2] = cmul(v[k2], e[kout * EJ]);
+                    const float4 f = *reinterpret_cast<const float4 *>(e + kout * EJ);
+                    va[k2] = cmul(va[k2], make_float2(f.x, f.y));
+                    vb[k2] = cmul(vb[k2], make_float2(f.z, f.w));
                 }
                 if (it == W::ITEMS / 4 - 1 && b + 2 < nrounds) named_bar_arrive(kBarEmpty + q, ALL);
                 const int s = sr + j, i = 2 * n0 + il;
-                if (sr + kRound > s_end && s >= s_end) {   // only in the block's last round
+                if (sr + kRound > s_end) {                  // only in the block's last round
 #pragma unroll
-                    for (int k2 = 0; k2 < R; ++k2) v[k2] = make_float2(0.f, 0.f);
+                    for (int k2 = 0; k2 < R; ++k2) {
+                        if (s >= s_end) va[k2] = make_float2(0.f, 0.f);
+                        if (s + 1 >= s_end) vb[k2] = make_float2(0.f, 0.f);
+                    }
                 }
                 if (i < I) {
                     if constexpr (OUT == 1) {
-                        // one warp store = one station's 16 spectra x 2 pols of a channel (256 B)
+                        // one warp store = one station's 16 spectra x 2 pols of two channels
                         float2 *out = reinterpret_cast<float2 *>(corr) +
                                       ((((long long)sb * C) * NB + (sr - s_base) / kRound) * N + (i >> 1)) *
                                           (2 * kRound) + j * 2 + (i & 1);
@@ -564,32 +582,36 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
 #pragma unroll
                         for (int k2 = 0; k2 < R; ++k2) {
                             const int kout = k1 + R * ((k2 + R / 2) % R);
-                            out[kout * kstride] = v[k2];
+                            out[kout * kstride] = va[k2];
+                            out[kout * kstride + 2] = vb[k2];
                         }
                     } else {
-                        // planar: one warp store = 2 inputs x 16 spectra of one (channel, plane)
+                        // planar: one warp store = 2 inputs x 16 spectra of two (channel, plane)
                         constexpr int planes = OUT == 4 ? 4 : 2;
                         const long long pstride = (long long)I_pad * s_out;
                         const long long base = (long long)sb * C * planes * pstride + (long long)i * s_out + (s - s_base);
 #pragma unroll
                         for (int k2 = 0; k2 < R; ++k2) {
                             const int kout = k1 + R * ((k2 + R / 2) % R);
-                            const float2 y = v[k2];
+                            const float2 ya = va[k2], yb = vb[k2];
                             const long long o = base + (long long)kout * planes * pstride;
                             if constexpr (OUT == 5) {
                                 float *out = reinterpret_cast<float *>(corr);
-                                out[o] = y.x;
-                                out[o + pstride] = y.y;
+                                *reinterpret_cast<float2 *>(out + o) = make_float2(ya.x, yb.x);
+                                *reinterpret_cast<float2 *>(out + o + pstride) = make_float2(ya.y, yb.y);
                             } else {
                                 unsigned short *out = reinterpret_cast<unsigned short *>(corr);
-                                const unsigned short hr = to_bits(y.x, OUT), hi = to_bits(y.y, OUT);
-                                out[o] = hr;
-                                out[o + pstride] = hi;
+                                const unsigned short ra = to_bits(ya.x, OUT), ia = to_bits(ya.y, OUT);
+                                const unsigned short rb = to_bits(yb.x, OUT), ib = to_bits(yb.y, OUT);
+                                *reinterpret_cast<unsigned *>(out + o) = (unsigned)ra | ((unsigned)rb << 16);
+                                *reinterpret_cast<unsigned *>(out + o + pstride) = (unsigned)ia | ((unsigned)ib << 16);
                                 if constexpr (OUT == 4) {
-                                    out[o + 2 * pstride] =
-                                        __half_as_ushort(__float2half_rn(y.x - __half2float(__ushort_as_half(hr))));
-                                    out[o + 3 * pstride] =
-                                        __half_as_ushort(__float2half_rn(y.y - __half2float(__ushort_as_half(hi))));
+                                    const unsigned short lra = lo_bits16(ya.x, ra), lia = lo_bits16(ya.y, ia);
+                                    const unsigned short lrb = lo_bits16(yb.x, rb), lib = lo_bits16(yb.y, ib);
+                                    *reinterpret_cast<unsigned *>(out + o + 2 * pstride) =
+                                        (unsigned)lra | ((unsigned)lrb << 16);
+                                    *reinterpret_cast<unsigned *>(out + o + 3 * pstride) =
+                                        (unsigned)lia | ((unsigned)lib << 16);
                                 }
                             }
                         }
