@@ -10,7 +10,8 @@ Default workload (the headline): 64 stations x 2 pols, 244 subbands, complex
 int16 noise (sigma 100) + 3 point sources with seeded delays (+-5 us) and
 per-station bandpass ripple, 16-tap PPF to 64 channels, 3072 spectra per block
 (1.00663 s of sky), FP32-accurate path: the X-stage runs on the tcgen05 tensor
-cores with each FP32 operand split into hi + lo TF32 parts (FX_TF32_SPLIT).
+cores with each FP32 operand split into hi + lo, hi hi' as TF32 MMAs and the
+cross terms hi lo' + lo hi' as BF16 MMAs (FX_TF32_SPLIT).
 The CUDA-core FFMA FP32 X-stage and the FP16 / BF16 / split-FP16 tensor-core
 X-stages are timed on the same block, and the 8-bit precision workload (64
 stations, 488 subbands, 256 channels, 768 spectra) is timed at its own shape;
