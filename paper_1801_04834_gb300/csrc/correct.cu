@@ -15,7 +15,8 @@
 //                phi0 = 2 pi f_k tau_begin reduced mod 2 pi, and the
 //                per-spectrum step 2 pi f_k (tau_end - tau_begin) / S; both
 //                stored as FP32. FP64 work is SB*N*C, not per sample.
-//   correct_*    FP32 per sample: phi = phi0 + s * step, sincos, rotate,
+//   correct_*    FP32 per sample: phi = phi0 + s * step reduced to [-pi, pi]
+//                (two-constant Cody-Waite split of 2 pi), __sincosf, rotate,
 //                times bandpass * gain, transpose. Memory bound.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -43,15 +44,6 @@ __global__ void phase_table_kernel(const double *__restrict__ centres, const dou
     const double red = phi0 - two_pi * rint(phi0 / two_pi);
     const double step = two_pi * f * (tau_e[n] - tau_b[n]) / (double)S;
     table[idx] = make_float2((float)red, (float)step);
-}
-
-// Y = X * bandpass * gain * exp(i (phi0 + s * step))
-__device__ __forceinline__ float2 correct_one(float2 x, float2 ph, int s, float bp, float2 g)
-{
-    float sn, cs;
-    sincosf(fmaf((float)s, ph.y, ph.x), &sn, &cs);
-    const float2 xg = make_float2(fmaf(x.x, g.x, -x.y * g.y), fmaf(x.x, g.y, x.y * g.x));
-    return make_float2(bp * fmaf(xg.x, cs, -xg.y * sn), bp * fmaf(xg.x, sn, xg.y * cs));
 }
 
 // ---- FP32 output, spectrum-blocked [SB][C][ceil16(S)/16][N][16][2] ---------
@@ -98,18 +90,35 @@ correct_f32_kernel(const float2 *__restrict__ chan, const float2 *__restrict__ t
             ph[e] = make_float2(cs, sn);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < kPols * kBS * C; e += kNT) {
-            const int k = e % C, j = (e / C) % kBS, p = e / (C * kBS);
-            const int s = blk * kBS + j;
-            float2 y = make_float2(0.f, 0.f);
-            if (s < S) {
-                const float2 x = chan[((((long long)sb * N + n) * kPols + p) * S + s) * C + k];
-                const float bp = bandpass ? bandpass[(long long)n * C + k] : 1.f;
-                const float2 xg = make_float2(fmaf(x.x, g[p].x, -x.y * g[p].y), fmaf(x.x, g[p].y, x.y * g[p].x));
-                const float2 w = ph[j * C + k];
-                y = make_float2(bp * fmaf(xg.x, w.x, -xg.y * w.y), bp * fmaf(xg.x, w.y, xg.y * w.x));
+        // eight samples per thread in flight before any is used
+        constexpr int U = 8;
+        for (int e0 = threadIdx.x; e0 < kPols * kBS * C; e0 += U * kNT) {
+            float2 xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * kNT;
+                const int k = e % C, j = (e / C) % kBS, p = e / (C * kBS);
+                const int s = blk * kBS + j;
+                xv[u] = make_float2(0.f, 0.f);
+                if (e < kPols * kBS * C && s < S) xv[u] = chan[((((long long)sb * N + n) * kPols + p) * S + s) * C + k];
             }
-            tile[k * TW + j * kPols + p] = y;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * kNT;
+                if (e >= kPols * kBS * C) break;
+                const int k = e % C, j = (e / C) % kBS, p = e / (C * kBS);
+                const int s = blk * kBS + j;
+                float2 y = make_float2(0.f, 0.f);
+                if (s < S) {
+                    const float2 x = xv[u];
+                    const float bp = bandpass ? bandpass[(long long)n * C + k] : 1.f;
+                    const float2 xg =
+                        make_float2(fmaf(x.x, g[p].x, -x.y * g[p].y), fmaf(x.x, g[p].y, x.y * g[p].x));
+                    const float2 w = ph[j * C + k];
+                    y = make_float2(bp * fmaf(xg.x, w.x, -xg.y * w.y), bp * fmaf(xg.x, w.y, xg.y * w.x));
+                }
+                tile[k * TW + j * kPols + p] = y;
+            }
         }
         __syncthreads();
         float2 *out = corr + (((long long)sb * C * NB + blk) * N + n) * (2 * kBS);
@@ -133,55 +142,83 @@ static cudaError_t launch_correct_f32(const float2 *chan, const float2 *table, c
     return cudaGetLastError();
 }
 
-// ---- planar 16-bit output [SB][C][planes][I_pad][S_pad] -----------------
-// CTA tile = 8 channels x 64 spectra x 8 inputs. Reads are 8-channel runs
-// (64 B); writes are 64-spectrum rows (128 B) of one (channel, plane, input).
-constexpr int kPT_C = 8, kPT_S = 64, kPT_I = 8;
-constexpr int kPT_ROW = kPT_S + 2;   // float2 pad per (input, channel) row
+// ---- planar output [SB][C][planes][I_pad][S_pad] (16-bit, hi/lo or FP32) ----
+// CTA tile = one station (both pols) x CC channels (CC = min(C, 64)) x ST =
+// 2048 / CC spectra. Reads are whole channel runs of one (pol, spectrum)
+// (CC x 8 bytes: all of a 64-channel row), so a CTA reads contiguous memory
+// and DRAM pages are not reopened by sibling CTAs; writes are ST-spectrum
+// runs of one (channel, plane, input). The tile [pol][channel][ST + 1] turns
+// the corner in shared memory without bank conflicts. CTAs past the last
+// station (inputs I .. I_pad) and spectra S .. S_pad write zeros.
+// All of a thread's samples are loaded before any is used (memory-level
+// parallelism). The phase is reduced to [-pi, pi] by a two-constant
+// Cody-Waite split of 2 pi, then __sincosf (absolute error about 4e-7, as in
+// the fused F-stage).
+constexpr int kPT_E = 4096;                 // samples per CTA tile
 
-template <int MODE>  // 1: F16, 2: BF16, 3: F16 split, 4: FP32 (TF32 split X-stage)
+template <int CC>
+constexpr int pt_st() { return kPT_E / (kPols * CC); }
+
+template <int MODE, int CC>  // MODE 1: F16, 2: BF16, 3: F16 split, 4: FP32 (TF32 split X-stage)
 __global__ void __launch_bounds__(kNT)
 correct_planar_kernel(const float2 *__restrict__ chan, const float2 *__restrict__ table,
                       const float *__restrict__ bandpass, const float2 *__restrict__ gains,
                       void *__restrict__ corr, int N, int C, int S, int I_pad, int S_pad, float scale)
 {
-    __shared__ float2 tile[kPT_I * kPT_C * kPT_ROW];
-    const int I = N * kPols;
-    const int s0 = blockIdx.x * kPT_S;
-    const int i0 = blockIdx.y * kPT_I;
-    const int cblocks = C / kPT_C;
-    const int c0 = (blockIdx.z % cblocks) * kPT_C;
+    constexpr int ST = pt_st<CC>();          // spectra per tile: 32 (CC = 64) or 128 (CC = 16)
+    constexpr int TR = ST + 1;               // tile row (float2)
+    constexpr int PER = kPT_E / kNT;
+    __shared__ float2 tile[kPols * CC * TR];
+    const int s0 = blockIdx.x * ST;
+    const int n = blockIdx.y;                // station; n >= N: padding inputs (zeros)
+    const int cblocks = C / CC;
+    const int c0 = (blockIdx.z % cblocks) * CC;
     const int sb = blockIdx.z / cblocks;
 
-    for (int e = threadIdx.x; e < kPT_I * kPT_S * kPT_C; e += kNT) {
-        const int c = e % kPT_C;
-        const int s = (e / kPT_C) % kPT_S;
-        const int il = e / (kPT_C * kPT_S);
-        const int i = i0 + il, ss = s0 + s, k = c0 + c;
+    float2 xv[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * kNT;
+        const int c = e % CC, s = (e / CC) % ST, p = e / (CC * ST);
+        const int ss = s0 + s;
+        xv[u] = make_float2(0.f, 0.f);
+        if (n < N && ss < S) xv[u] = chan[((((long long)sb * N + n) * kPols + p) * S + ss) * C + c0 + c];
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * kNT;
+        const int c = e % CC, s = (e / CC) % ST, p = e / (CC * ST);
+        const int ss = s0 + s, k = c0 + c;
         float2 y = make_float2(0.f, 0.f);
-        if (i < I && ss < S) {
-            const int n = i / kPols, p = i % kPols;
-            const float2 x = chan[((((long long)sb * N + n) * kPols + p) * S + ss) * C + k];
+        if (n < N && ss < S) {
             const float2 ph = table[((long long)sb * N + n) * C + k];
-            const float bp = bandpass ? bandpass[(long long)n * C + k] : 1.f;
-            const float2 g = gains ? gains[i] : make_float2(1.f, 0.f);
-            y = correct_one(x, ph, ss, bp, g);
-            y.x *= scale;
-            y.y *= scale;
+            const float bp = (bandpass ? bandpass[(long long)n * C + k] : 1.f) * scale;
+            const float2 g = gains ? gains[n * kPols + p] : make_float2(1.f, 0.f);
+            const float phi = fmaf((float)ss, ph.y, ph.x);
+            const float kq = rintf(phi * 0.15915494309189535f);            // phi / (2 pi)
+            float r = fmaf(-kq, 6.28125f, phi);                             // 2 pi = 6.28125 + 1.9353...e-3
+            r = fmaf(-kq, 1.9353071795864769e-3f, r);
+            float sn, cs;
+            __sincosf(r, &sn, &cs);
+            const float2 x = xv[u];
+            const float2 xg = make_float2(fmaf(x.x, g.x, -x.y * g.y), fmaf(x.x, g.y, x.y * g.x));
+            y = make_float2(bp * fmaf(xg.x, cs, -xg.y * sn), bp * fmaf(xg.x, sn, xg.y * cs));
         }
-        tile[(il * kPT_C + c) * kPT_ROW + s] = y;
+        tile[(p * CC + c) * TR + s] = y;
     }
     __syncthreads();
     constexpr int planes = (MODE == 3) ? 4 : 2;
     const long long plane_stride = (long long)I_pad * S_pad;
-    // task = (input il, channel c, group of 8 spectra)
-    for (int t = threadIdx.x; t < kPT_I * kPT_C * (kPT_S / 8); t += kNT) {
-        const int g8 = t % (kPT_S / 8);
-        const int c = (t / (kPT_S / 8)) % kPT_C;
-        const int il = t / ((kPT_S / 8) * kPT_C);
-        const float2 *src = tile + (il * kPT_C + c) * kPT_ROW + g8 * 8;
+    // task = (pol p, channel c, group of 8 spectra)
+    for (int task = threadIdx.x; task < kPols * CC * (ST / 8); task += kNT) {
+        const int g8 = task % (ST / 8);
+        const int c = (task / (ST / 8)) % CC;
+        const int p = task / ((ST / 8) * CC);
+        const int sg = s0 + g8 * 8;
+        if (sg >= S_pad) continue;
+        const float2 *src = tile + (p * CC + c) * TR + g8 * 8;
         const long long base = (((long long)sb * C + c0 + c) * planes) * plane_stride +
-                               (long long)(i0 + il) * S_pad + s0 + g8 * 8;
+                               (long long)(n * kPols + p) * S_pad + sg;
         if constexpr (MODE == 4) {
             float4 *re = reinterpret_cast<float4 *>(reinterpret_cast<float *>(corr) + base);
             float4 *im = reinterpret_cast<float4 *>(reinterpret_cast<float *>(corr) + base + plane_stride);
@@ -189,39 +226,39 @@ correct_planar_kernel(const float2 *__restrict__ chan, const float2 *__restrict_
             re[1] = make_float4(src[4].x, src[5].x, src[6].x, src[7].x);
             im[0] = make_float4(src[0].y, src[1].y, src[2].y, src[3].y);
             im[1] = make_float4(src[4].y, src[5].y, src[6].y, src[7].y);
-            continue;
-        }
-        unsigned short re_hi[8], im_hi[8], re_lo[8], im_lo[8];
+        } else {
+            unsigned short re_hi[8], im_hi[8], re_lo[8], im_lo[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const float2 y = src[q];
-            if constexpr (MODE == 2) {
-                re_hi[q] = __bfloat16_as_ushort(__float2bfloat16_rn(y.x));
-                im_hi[q] = __bfloat16_as_ushort(__float2bfloat16_rn(y.y));
-            } else {
-                const __half hr = __float2half_rn(y.x), hi = __float2half_rn(y.y);
-                re_hi[q] = __half_as_ushort(hr);
-                im_hi[q] = __half_as_ushort(hi);
-                if constexpr (MODE == 3) {
-                    re_lo[q] = __half_as_ushort(__float2half_rn(y.x - __half2float(hr)));
-                    im_lo[q] = __half_as_ushort(__float2half_rn(y.y - __half2float(hi)));
+            for (int q = 0; q < 8; ++q) {
+                const float2 y = src[q];
+                if constexpr (MODE == 2) {
+                    re_hi[q] = __bfloat16_as_ushort(__float2bfloat16_rn(y.x));
+                    im_hi[q] = __bfloat16_as_ushort(__float2bfloat16_rn(y.y));
+                } else {
+                    const __half hr = __float2half_rn(y.x), hi = __float2half_rn(y.y);
+                    re_hi[q] = __half_as_ushort(hr);
+                    im_hi[q] = __half_as_ushort(hi);
+                    if constexpr (MODE == 3) {
+                        re_lo[q] = __half_as_ushort(__float2half_rn(y.x - __half2float(hr)));
+                        im_lo[q] = __half_as_ushort(__float2half_rn(y.y - __half2float(hi)));
+                    }
                 }
             }
-        }
-        unsigned short *out = reinterpret_cast<unsigned short *>(corr);
-        auto store8 = [&](long long off, const unsigned short (&v)[8]) {
-            uint4 w;
-            w.x = v[0] | ((unsigned)v[1] << 16);
-            w.y = v[2] | ((unsigned)v[3] << 16);
-            w.z = v[4] | ((unsigned)v[5] << 16);
-            w.w = v[6] | ((unsigned)v[7] << 16);
-            *reinterpret_cast<uint4 *>(out + off) = w;
-        };
-        store8(base, re_hi);
-        store8(base + plane_stride, im_hi);
-        if constexpr (MODE == 3) {
-            store8(base + 2 * plane_stride, re_lo);
-            store8(base + 3 * plane_stride, im_lo);
+            unsigned short *out = reinterpret_cast<unsigned short *>(corr);
+            auto store8 = [&](long long off, const unsigned short (&v)[8]) {
+                uint4 w;
+                w.x = v[0] | ((unsigned)v[1] << 16);
+                w.y = v[2] | ((unsigned)v[3] << 16);
+                w.z = v[4] | ((unsigned)v[5] << 16);
+                w.w = v[6] | ((unsigned)v[7] << 16);
+                *reinterpret_cast<uint4 *>(out + off) = w;
+            };
+            store8(base, re_hi);
+            store8(base + plane_stride, im_hi);
+            if constexpr (MODE == 3) {
+                store8(base + 2 * plane_stride, re_lo);
+                store8(base + 3 * plane_stride, im_lo);
+            }
         }
     }
 }
@@ -308,6 +345,35 @@ cudaError_t launch_correct_f32_noalloc(int N, int SB, int C, int S, double fs, c
     return launch_correct_f32(chan, table, bandpass, gains, corr, SB, N, C, S, st);
 }
 
+template <int CC>
+static cudaError_t launch_planar(const Handle &h, const float2 *chan, const float *bandpass, const float2 *gains,
+                                 void *corr, cudaStream_t st)
+{
+    const int N = h.p.n_stations, C = h.p.n_channels, S = h.p.n_spectra, SB = h.p.n_subbands;
+    constexpr int ST = pt_st<CC>();
+    dim3 grid((h.S_pad + ST - 1) / ST, h.I_pad / kPols, SB * (C / CC));
+    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+    switch (h.p.precision) {
+    case FX_F16:
+        correct_planar_kernel<1, CC><<<grid, kNT, 0, st>>>(chan, h.d_phase, bandpass, gains, corr, N, C, S, h.I_pad,
+                                                           h.S_pad, h.operand_scale);
+        break;
+    case FX_BF16:
+        correct_planar_kernel<2, CC><<<grid, kNT, 0, st>>>(chan, h.d_phase, bandpass, gains, corr, N, C, S, h.I_pad,
+                                                           h.S_pad, h.operand_scale);
+        break;
+    case FX_TF32_SPLIT:
+        correct_planar_kernel<4, CC><<<grid, kNT, 0, st>>>(chan, h.d_phase, bandpass, gains, corr, N, C, S, h.I_pad,
+                                                           h.S_pad, 1.f);
+        break;
+    default:
+        correct_planar_kernel<3, CC><<<grid, kNT, 0, st>>>(chan, h.d_phase, bandpass, gains, corr, N, C, S, h.I_pad,
+                                                           h.S_pad, h.operand_scale);
+        break;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_correct(const Handle &h, const float2 *chan, const float *bandpass,
                            const float2 *gains, void *corr, cudaStream_t st)
 {
@@ -315,27 +381,8 @@ cudaError_t launch_correct(const Handle &h, const float2 *chan, const float *ban
     if (h.p.precision == FX_F32)
         return launch_correct_f32(chan, h.d_phase, bandpass, gains, reinterpret_cast<float2 *>(corr), SB, N, C, S,
                                   st);
-    dim3 grid(h.S_pad / kPT_S, h.I_pad / kPT_I, SB * (C / kPT_C));
-    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-    switch (h.p.precision) {
-    case FX_F16:
-        correct_planar_kernel<1><<<grid, kNT, 0, st>>>(chan, h.d_phase, bandpass, gains, corr, N, C, S,
-                                                       h.I_pad, h.S_pad, h.operand_scale);
-        break;
-    case FX_BF16:
-        correct_planar_kernel<2><<<grid, kNT, 0, st>>>(chan, h.d_phase, bandpass, gains, corr, N, C, S,
-                                                       h.I_pad, h.S_pad, h.operand_scale);
-        break;
-    case FX_TF32_SPLIT:
-        correct_planar_kernel<4><<<grid, kNT, 0, st>>>(chan, h.d_phase, bandpass, gains, corr, N, C, S,
-                                                       h.I_pad, h.S_pad, 1.f);
-        break;
-    default:
-        correct_planar_kernel<3><<<grid, kNT, 0, st>>>(chan, h.d_phase, bandpass, gains, corr, N, C, S,
-                                                       h.I_pad, h.S_pad, h.operand_scale);
-        break;
-    }
-    return cudaGetLastError();
+    if (C >= 64) return launch_planar<64>(h, chan, bandpass, gains, corr, st);
+    return launch_planar<16>(h, chan, bandpass, gains, corr, st);
 }
 
 }  // namespace fxi
