@@ -874,7 +874,10 @@ def measure_adjoint(args, dev):
     import synth
     N, SB, C, S = 76, 32, 64, 768
     rng = np.random.default_rng(synth.BASE_SEED + 4)
-    c = fxg.Correlator(N, SB, C, S, taps=synth.kaiser_sinc_taps(16, C), centres=synth.subband_centres(SB))
+    # FP32 accuracy on the tensor cores (the headline's X-stage: hi hi' in TF32,
+    # the cross terms in BF16) for the forward pass, R and the backward passes
+    c = fxg.Correlator(N, SB, C, S, taps=synth.kaiser_sinc_taps(16, C), centres=synth.subband_centres(SB),
+                       precision=4)
     chan = torch.empty(c.chan_shape(), dtype=torch.float32, device=dev)
     chan.normal_(generator=torch.Generator(device=dev).manual_seed(synth.BASE_SEED + 4))
     g = torch.as_tensor(synth.random_gains(rng, N), dtype=torch.float32, device=dev)
@@ -905,7 +908,8 @@ def measure_adjoint(args, dev):
     peaks, _ = measured_peaks()
     vb = c.sizes.vis_bytes
     c.close()
-    return {"workload": "76 stations x 2 pols, 32 subbands, 64 channels, 768 spectra, FP32",
+    return {"workload": "76 stations x 2 pols, 32 subbands, 64 channels, 768 spectra, FP32 accuracy "
+                        "(split X-stage on tcgen05: hi hi' TF32, cross terms BF16)",
             "forward_ms": fwd_ms, "raw_vis_recompute_ms": raw_ms, "backward_ms": bwd_ms,
             "apply_gains_ms": app_ms, "backward_moving_delays_ms": interp_ms,
             "backward_hbm_frac": 2 * vb / (bwd_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
