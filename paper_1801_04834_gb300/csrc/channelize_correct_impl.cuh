@@ -460,13 +460,28 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
             const TIn *in = reinterpret_cast<const TIn *>(inbuf + q * BUF_BYTES);
             float2 *uq = u + q * USZ;
             float2 *fo = rowp(uq, (nl * kPols + p) * kRound) + c;
+            // four outputs at a time (four independent FMA chains); tap k of
+            // output j takes the sample loaded at output j + k - (T - 1), so the
+            // group's new samples stay in t[] until its outputs are formed
 #pragma unroll
-            for (int j = 0; j < kRound; ++j) {
-                win[(T - 1 + j) % T] = to_f2(in[j * NF + tid]);
-                float2 acc = make_float2(0.f, 0.f);
+            for (int j0 = 0; j0 < kRound; j0 += 4) {
+                float2 t[4], acc[4];
 #pragma unroll
-                for (int k = 0; k < T; ++k) acc = __ffma2_rn(h[k], win[(j + k) % T], acc);
-                fo[j * ROW] = cmul(acc, gsc);       // row (input, spectrum j), times gain x scale
+                for (int qq = 0; qq < 4; ++qq) {
+                    t[qq] = to_f2(in[(j0 + qq) * NF + tid]);
+                    acc[qq] = make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int k = 0; k < T; ++k)
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq)
+                        acc[qq] = __ffma2_rn(h[k], k >= T - 1 - qq ? t[qq + k - (T - 1)] : win[(j0 + qq + k) % T],
+                                             acc[qq]);
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    fo[(j0 + qq) * ROW] = cmul(acc[qq], gsc);   // row (input, spectrum), times gain x scale
+                    win[(T - 1 + j0 + qq) % T] = t[qq];
+                }
             }
             // exp(i phi) x flag of this round: phi = phi0 + s step reduced to
             // [-pi, pi] (two-constant Cody-Waite split of 2 pi), then __sincosf
@@ -763,13 +778,26 @@ ppf_correct_ws256_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, c
             if (b >= 2) named_bar_sync(kBarEmpty + q, HAND);
             const TIn *in = reinterpret_cast<const TIn *>(inbuf + q * BUF_BYTES);
             float2 *uq = u + q * USZ;
+            // four outputs at a time (see the 16/64-channel kernel)
 #pragma unroll
-            for (int j = 0; j < kRound; ++j) {
-                win[(T - 1 + j) % T] = to_f2(in[j * C * kPols + c * kPols + p]);
-                float2 acc = make_float2(0.f, 0.f);
+            for (int j0 = 0; j0 < kRound; j0 += 4) {
+                float2 t[4], acc[4];
 #pragma unroll
-                for (int k = 0; k < T; ++k) acc = __ffma2_rn(h[k], win[(j + k) % T], acc);
-                uq[j * ROW + c] = acc;
+                for (int qq = 0; qq < 4; ++qq) {
+                    t[qq] = to_f2(in[(j0 + qq) * C * kPols + c * kPols + p]);
+                    acc[qq] = make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int k = 0; k < T; ++k)
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq)
+                        acc[qq] = __ffma2_rn(h[k], k >= T - 1 - qq ? t[qq + k - (T - 1)] : win[(j0 + qq + k) % T],
+                                             acc[qq]);
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    uq[(j0 + qq) * ROW + c] = acc[qq];
+                    win[(T - 1 + j0 + qq) % T] = t[qq];
+                }
             }
             // phasors of this round: phi(sr) reduced to [-pi, pi] (two-constant
             // Cody-Waite split of 2 pi) and __sincosf, then rotations by exp(i step)
