@@ -339,7 +339,7 @@ ppf_correct_ws_kernel(const TIn *__restrict__ raw, void *__restrict__ corr, cons
                       int s_end, int *__restrict__ status, long long budget, int no_loads)
 {
     using W = FusedWsCfg<C>;
-    constexpr int R = W::R, NPC = W::NPC, NF = W::NF, IC = W::IC, ROW = W::ROW, PADG = W::PADG, USZ = W::USZ;
+    constexpr int R = W::R, NPC = W::NPC, NF = W::NF, ROW = W::ROW, PADG = W::PADG, USZ = W::USZ;
     constexpr int RS = W::RS, EJ = W::EJ, ESZ = W::ESZ;
     constexpr int ROW_BYTES = C * kPols * (int)sizeof(TIn);
     constexpr int BUF_BYTES = kRound * NPC * ROW_BYTES;
